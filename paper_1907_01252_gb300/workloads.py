@@ -1,0 +1,117 @@
+"""Seeded synthetic workloads for the channel-with-elastic-bar FSI problem.
+
+This module describes INPUTS only: geometry break points, cells per segment,
+material constants, time windows and seeded random states. It holds none of
+the method's arithmetic and imports nothing from the rest of the package, so
+both the CUDA path and the FP64 oracle may take their inputs from it.
+
+Geometry (reference configuration, Sec. 4 setting re-sized to the workloads
+used here): channel [0, 2] x [0, 0.41], an elastic bar x in [0.6, 0.7],
+y in [0, 0.2] attached to the bottom wall. Break points at the bar edges make
+the tensor mesh interface-fitted (Sec. 2.2, the mesh resolves the interface).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+X_BREAKS = (0.0, 0.6, 0.7, 2.0)
+Y_BREAKS = (0.0, 0.2, 0.41)
+SOLID_BOX = ((0.6, 0.7), (0.0, 0.2))
+
+
+def cells_per_segment(breaks, n_cells):
+    """Split n_cells over the segments of `breaks` in proportion to length.
+
+    Each segment gets round(n * len / total) cells, at least one; the longest
+    segment absorbs the difference so that the counts sum to n_cells.
+    (16 -> 5/1/10 and 128 -> 38/6/84 in x; 4 -> 2/2 and 32 -> 16/16 in y.)
+    """
+    lengths = [b - a for a, b in zip(breaks[:-1], breaks[1:])]
+    total = breaks[-1] - breaks[0]
+    counts = [max(1, int(math.floor(n_cells * L / total + 0.5))) for L in lengths]
+    longest = int(np.argmax(lengths))
+    counts[longest] += n_cells - sum(counts)
+    if counts[longest] < 1:
+        raise ValueError("too few cells for the break points")
+    return tuple(counts)
+
+
+@dataclasses.dataclass(frozen=True)
+class Material:
+    rho_f: float = 1000.0     # fluid density
+    nu_f: float = 1e-3        # kinematic viscosity
+    rho_s: float = 1000.0     # solid density
+    mu_s: float = 5e5         # shear modulus
+    lambda_s: float = 2e6     # first Lame parameter (Poisson ratio 0.4)
+    vbar: float = 1.0         # mean inflow velocity
+    ramp_t: float = 0.2       # inflow ramp duration
+    theta0: float = 1.0       # shifted CN: theta = 1/2 + theta0 * k
+    alpha0: float = 0.1       # local-projection stabilisation constant
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    T: float
+    n_slices: int
+    m_fine: int
+    m_coarse: int = 1
+    newton_tol: float = 1e-10
+    newton_maxit: int = 20
+    gmres_restart: int = 50
+    gmres_maxit: int = 2000
+    gmres_rtol: float = 1e-12
+    parareal_tol: float = 1e-8
+    material: Material = Material()
+    with_solid: bool = True
+
+    @property
+    def nx_seg(self):
+        return cells_per_segment(X_BREAKS, self.nx)
+
+    @property
+    def ny_seg(self):
+        return cells_per_segment(Y_BREAKS, self.ny)
+
+    @property
+    def n_nodes(self):
+        return (2 * self.nx + 1) * (2 * self.ny + 1)
+
+    @property
+    def n_dofs(self):
+        return 5 * self.n_nodes
+
+    @property
+    def k_fine(self):
+        return self.T / self.n_slices / self.m_fine
+
+    @property
+    def k_coarse(self):
+        return self.T / self.n_slices / self.m_coarse
+
+
+# 2D monolithic ALE FSI, FP64, 16 x 4 Q2 cells, T = 1, 8 slices x 16 fine CN steps.
+SMALL_16x4 = Workload("fsi2d_q2_16x4_T1_8x16", nx=16, ny=4, T=1.0, n_slices=8, m_fine=16)
+# Same problem at scale: 128 x 32 Q2 cells (83,525 dofs), T = 2, 64 slices x 32 fine CN steps.
+LARGE_128x32 = Workload("fsi2d_q2_128x32_T2_64x32", nx=128, ny=32, T=2.0, n_slices=64, m_fine=32)
+
+WORKLOADS = {w.name: w for w in (SMALL_16x4, LARGE_128x32)}
+
+
+def random_state(n_nodes, seed, v_scale=1.0, u_scale=2e-3, p_scale=100.0):
+    """Seeded random nodal state [n_nodes, 5] = (v_x, v_y, u_x, u_y, p).
+
+    The displacement amplitude is kept small so that the ALE map stays
+    invertible (J > 0) on the meshes used in the tests.
+    """
+    rng = np.random.default_rng(seed)
+    U = np.empty((n_nodes, 5))
+    U[:, 0:2] = v_scale * rng.uniform(-1.0, 1.0, (n_nodes, 2))
+    U[:, 2:4] = u_scale * rng.uniform(-1.0, 1.0, (n_nodes, 2))
+    U[:, 4] = p_scale * rng.uniform(-1.0, 1.0, n_nodes)
+    return U
