@@ -1,0 +1,170 @@
+/*
+ * fsi.h -- C ABI of the GB300 library for Parareal time stepping of monolithic
+ * ALE fluid-structure interaction (Margenberg & Richter, "Parallel
+ * time-stepping for fluid-structure interactions").
+ *
+ * The library advances the fully discrete ALE-FSI system of Sec. 2
+ * (equal-order Q2 elements, shifted Crank-Nicolson step of Sec. 2.3 with the
+ * forms of Eq. (semiforms)) for many time slices at once on one GPU, and runs
+ * the Parareal iteration of Sec. 3, Eq. (parareal:iteration).
+ *
+ * Conventions shared by every entry point
+ *   - State layout: one state is n_dofs = 5 * n_nodes doubles, node-major,
+ *     components (v_x, v_y, u_x, u_y, p). Node (i, j) of the Q2 node grid
+ *     (2nx+1) x (2ny+1) has id j * (2nx+1) + i (x fastest). A batch of S
+ *     states is S contiguous states.
+ *   - Pointers documented "device" are CUDA device pointers owned by the
+ *     caller; "host" pointers are ordinary host memory owned by the caller.
+ *     The library never frees caller memory and never keeps a caller pointer
+ *     after a call returns.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every kernel of a call runs on that stream. Calls that report
+ *     iteration statistics synchronise the stream before they return.
+ *   - Return value: FSI_OK (0) on success, a negative FSI_E* code otherwise;
+ *     fsi_last_error() then returns a message (thread-local). No entry point
+ *     aborts, exits, traps on the device or leaves a kernel waiting without
+ *     an iteration limit.
+ *   - The context owns all workspace (allocated in fsi_setup for batches of
+ *     up to params->max_batch slices). A context must not be used by two
+ *     host threads at the same time.
+ */
+#ifndef FSI_H
+#define FSI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FSI_OK = 0,
+  FSI_EINVAL = -1,    /* invalid argument or size */
+  FSI_ENOMEM = -2,    /* device allocation failed */
+  FSI_ECUDA = -3,     /* CUDA runtime error */
+  FSI_ENEWTON = -4,   /* Newton did not reach its tolerance within newton_maxit */
+  FSI_EGMRES = -5,    /* FGMRES did not reach its tolerance within gmres_maxit */
+  FSI_EJAC = -6,      /* singular local block (Vanka or coarsest solve) or J <= 0 */
+  FSI_ENAN = -7,      /* non-finite residual */
+  FSI_EDIVERGE = -8   /* Parareal increment grew for three iterations in a row */
+};
+
+/* Interface-fitted tensor-product mesh of the reference domain (Sec. 2.2:
+ * the interface is resolved by cell faces). Break points split each axis into
+ * segments with nx_seg[i] (ny_seg[j]) uniform cells. Cells whose centre lies
+ * in the solid box are solid. Host pointers, read during fsi_setup only. */
+typedef struct fsi_mesh {
+  int n_xseg;
+  const double* x_breaks; /* [n_xseg + 1], increasing */
+  const int* nx_seg;      /* [n_xseg], each >= 1 */
+  int n_yseg;
+  const double* y_breaks; /* [n_yseg + 1], increasing */
+  const int* ny_seg;      /* [n_yseg], each >= 1 */
+  int has_solid;
+  double solid_x0, solid_x1, solid_y0, solid_y1;
+} fsi_mesh;
+
+/* Material, time and solver parameters. Materials: Eq. (stress) (Newtonian
+ * fluid, St. Venant-Kirchhoff solid). theta = 1/2 + theta0 * k for the fine
+ * step (Sec. 2.3); the coarse step uses theta = 1. alpha0 scales the local
+ * projection stabilisation (Sec. 2.2 requires one; its form is a reading).
+ * The Parareal interval [0, T] is cut into n_slices slices of m_fine fine and
+ * m_coarse coarse steps (Sec. 3, T/L = m k = M K). */
+typedef struct fsi_params {
+  double rho_f, nu_f, rho_s, mu_s, lambda_s;
+  double vbar, ramp_t;     /* mean inflow velocity, inflow ramp duration */
+  double theta0, alpha0;
+  double T;
+  int n_slices, m_fine, m_coarse;
+  double newton_tol;       /* stop when ||R||_2 <= newton_tol * max(||R_0||_2, 1) */
+  int newton_maxit;
+  int gmres_restart;       /* FGMRES restart length m */
+  int gmres_maxit;         /* total FGMRES iterations per linear solve */
+  double gmres_rtol;       /* relative residual reduction per linear solve */
+  int mg_coarsest_max_dofs;/* coarsen the multigrid hierarchy until <= this */
+  int mg_smooth;           /* Vanka sweeps before and after the coarse correction */
+  double mg_omega;         /* Vanka damping */
+  int max_batch;           /* most slices advanced in one call */
+} fsi_params;
+
+/* Iteration statistics of one call (filled when the pointer is non-NULL). */
+typedef struct fsi_stats {
+  long long newton_iters;  /* Newton iterations summed over slices and steps */
+  long long gmres_iters;   /* FGMRES iterations summed over slices and solves */
+  int max_newton;          /* most Newton iterations of one slice in one step */
+  int max_gmres;           /* most FGMRES iterations of one slice in one solve */
+  int status;              /* same code as the return value */
+} fsi_stats;
+
+typedef struct fsi_parareal_stats {
+  int iterations;          /* Parareal iterations done (the predictor sweep is 0) */
+  double increment_v, increment_u, increment_p; /* last relative increments */
+  long long fine_steps;    /* fine theta steps run (slices x steps) */
+  long long coarse_steps;  /* coarse theta steps run */
+  fsi_stats fine, coarse;  /* summed solver statistics */
+} fsi_parareal_stats;
+
+typedef struct fsi_ctx fsi_ctx;
+
+/* Build the mesh hierarchy, the dof tables and all device workspace.
+ * Errors: FSI_EINVAL (bad mesh/params), FSI_ENOMEM, FSI_ECUDA. */
+int fsi_setup(const fsi_mesh* mesh, const fsi_params* params, fsi_ctx** out);
+void fsi_destroy(fsi_ctx* ctx);
+const char* fsi_last_error(void);
+int fsi_n_nodes(const fsi_ctx* ctx);
+int fsi_n_dofs(const fsi_ctx* ctx);
+int fsi_n_levels(const fsi_ctx* ctx);   /* multigrid levels of the linear solver */
+
+/* Residual of one theta step t_{n-1} -> t_n = t_new (Sec. 2.3, the step
+ * equation with the forms of Eq. (semiforms)) for S slices at once.
+ * U, U_old, R: device [S][n_dofs]; t_new: host [S]. Rows with Dirichlet data
+ * carry U - g(t_new); pressure rows of nodes that touch no fluid cell carry p.
+ * Errors: FSI_EINVAL (S outside 1..max_batch). */
+int fsi_residual(fsi_ctx* ctx, int S, const double* U, const double* U_old,
+                 const double* t_new, double k, double theta, double* R, void* stream);
+
+/* Jacobian dR/dU of the same residual, assembled as a block-sparse matrix with
+ * 5x5 node blocks: vals device [S][nnzb][5][5] (row-major blocks), pattern
+ * from fsi_bsr_pattern. Errors: FSI_EINVAL. */
+int fsi_jacobian(fsi_ctx* ctx, int S, const double* U, const double* U_old,
+                 double k, double theta, double* vals, void* stream);
+int fsi_nnzb(const fsi_ctx* ctx);
+/* Host copy of the block pattern: rowptr [n_nodes + 1], colidx [nnzb]. */
+int fsi_bsr_pattern(const fsi_ctx* ctx, int* rowptr, int* colidx);
+
+/* y = A x for S slices sharing the pattern: vals device [S][nnzb][25],
+ * x, y device [S][n_dofs]. Errors: FSI_EINVAL. */
+int fsi_bsr_spmv(fsi_ctx* ctx, int S, const double* vals, const double* x,
+                 double* y, void* stream);
+
+/* One theta step for S slices: Newton's method (exact Jacobian, no damping;
+ * Sec. 1 and 4 solve each step's nonlinear system by Newton) with FGMRES
+ * preconditioned by a geometric multigrid V-cycle with Vanka smoothing.
+ * U_old, U_new: device [S][n_dofs] (may alias); t_old: host [S].
+ * Errors: FSI_ENEWTON, FSI_EGMRES, FSI_EJAC, FSI_ENAN, FSI_EINVAL. */
+int fsi_theta_step(fsi_ctx* ctx, int S, const double* U_old, const double* t_old,
+                   double k, double theta, double* U_new, fsi_stats* stats, void* stream);
+
+/* Fine propagator F of Sec. 3 for S slices at once: m_fine shifted
+ * Crank-Nicolson steps of k = T / n_slices / m_fine from t0[s].
+ * U0, U1: device [S][n_dofs] (may alias); t0: host [S]. */
+int fsi_fine(fsi_ctx* ctx, int S, const double* U0, const double* t0, double* U1,
+             fsi_stats* stats, void* stream);
+
+/* Coarse propagator C of Sec. 3: m_coarse theta = 1 steps of
+ * K = T / n_slices / m_coarse. Same arguments as fsi_fine. */
+int fsi_coarse(fsi_ctx* ctx, int S, const double* U0, const double* t0, double* U1,
+               fsi_stats* stats, void* stream);
+
+/* Parareal, Eq. (parareal:iteration): predictor sweep with C, then iterations
+ * U_{n+1}^{i+1} = F(U_n^i) + (C(U_n^{i+1}) - C(U_n^i)); fine solves of all
+ * slices not yet exact run batched. U: device [n_slices + 1][n_dofs]; on entry
+ * U[0] is the initial state, on return U holds the last iterate at all slice
+ * boundaries. Stops when the largest relative boundary increment of v, u and
+ * p is <= tol, or after max_iter iterations (max_iter >= n_slices gives the
+ * serial fine solution). Errors: as fsi_theta_step, FSI_EDIVERGE. */
+int parareal_iterate(fsi_ctx* ctx, double* U, int max_iter, double tol,
+                     fsi_parareal_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_H */

@@ -1,0 +1,966 @@
+// GB300 library for Parareal time stepping of monolithic ALE fluid-structure
+// interaction: host side (mesh hierarchy, tables, workspace, drivers, C ABI).
+//
+// The method follows Margenberg & Richter, "Parallel time-stepping for
+// fluid-structure interactions": the ALE-FSI system of Sec. 2 discretised with
+// equal-order Q2 elements and the shifted Crank-Nicolson step of Sec. 2.3; the
+// Parareal iteration of Sec. 3. The paper leaves the linear solver open (it
+// cites monolithic multigrid solvers); here every Newton step is solved by
+// FGMRES preconditioned with a geometric multigrid V-cycle whose smoother is
+// the cell-wise Vanka (local 45 x 45 solves) block smoother, coarse operators
+// by rediscretisation on interface-fitted coarsened meshes.
+//
+// All slices of a batch advance together; every kernel works per slice with
+// fixed reduction orders, so the result of a slice does not depend on the
+// batch it ran in.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fsi.h"
+#include "fsi_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(FSI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+#define TRY(call)                 \
+  do {                            \
+    int rc_ = (call);             \
+    if (rc_ != FSI_OK) return rc_; \
+  } while (0)
+
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// Host mesh of one multigrid level.
+// ---------------------------------------------------------------------------
+struct HostMesh {
+  std::vector<double> xv, yv;   // vertices
+  std::vector<int> xseg, yseg;  // cells per segment
+  int nx = 0, ny = 0, nnx = 0, nny = 0, n_nodes = 0, n_cells = 0, nnzb = 0;
+  std::vector<double> xn, yn;
+  std::vector<int> cell_nodes;
+  std::vector<double> cell_h;
+  std::vector<uint8_t> cell_flags, node_flags;
+  std::vector<double> node_y;
+  std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk;
+};
+
+std::vector<double> axis_vertices(const std::vector<double>& breaks, const std::vector<int>& counts) {
+  std::vector<double> v{breaks[0]};
+  for (size_t s = 0; s < counts.size(); ++s)
+    for (int i = 1; i <= counts[s]; ++i)
+      v.push_back(i == counts[s] ? breaks[s + 1] : breaks[s] + (breaks[s + 1] - breaks[s]) * i / counts[s]);
+  return v;
+}
+
+void build_mesh(HostMesh& m, bool has_solid, const double box[4]) {
+  m.nx = (int)m.xv.size() - 1;
+  m.ny = (int)m.yv.size() - 1;
+  m.nnx = 2 * m.nx + 1;
+  m.nny = 2 * m.ny + 1;
+  m.n_nodes = m.nnx * m.nny;
+  m.n_cells = m.nx * m.ny;
+  m.xn.assign(m.nnx, 0.0);
+  m.yn.assign(m.nny, 0.0);
+  for (int i = 0; i <= m.nx; ++i) m.xn[2 * i] = m.xv[i];
+  for (int i = 0; i < m.nx; ++i) m.xn[2 * i + 1] = 0.5 * (m.xv[i] + m.xv[i + 1]);
+  for (int j = 0; j <= m.ny; ++j) m.yn[2 * j] = m.yv[j];
+  for (int j = 0; j < m.ny; ++j) m.yn[2 * j + 1] = 0.5 * (m.yv[j] + m.yv[j + 1]);
+  m.cell_nodes.assign(m.n_cells * 9, 0);
+  m.cell_h.assign(m.n_cells * 2, 0.0);
+  m.cell_flags.assign(m.n_cells, 0);
+  std::vector<char> in_solid(m.n_nodes, 0), in_fluid(m.n_nodes, 0);
+  for (int cy = 0; cy < m.ny; ++cy)
+    for (int cx = 0; cx < m.nx; ++cx) {
+      const int c = cy * m.nx + cx;
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) m.cell_nodes[c * 9 + b * 3 + a] = (2 * cy + b) * m.nnx + 2 * cx + a;
+      m.cell_h[c * 2] = m.xv[cx + 1] - m.xv[cx];
+      m.cell_h[c * 2 + 1] = m.yv[cy + 1] - m.yv[cy];
+      const double xc = 0.5 * (m.xv[cx] + m.xv[cx + 1]), yc = 0.5 * (m.yv[cy] + m.yv[cy + 1]);
+      const bool solid = has_solid && xc > box[0] && xc < box[1] && yc > box[2] && yc < box[3];
+      m.cell_flags[c] = (solid ? CF_SOLID : 0) | (cx == m.nx - 1 ? CF_OUTFLOW : 0);
+      for (int l = 0; l < 9; ++l) (solid ? in_solid : in_fluid)[m.cell_nodes[c * 9 + l]] = 1;
+    }
+  m.node_flags.assign(m.n_nodes, 0);
+  m.node_y.assign(m.n_nodes, 0.0);
+  for (int j = 0; j < m.nny; ++j)
+    for (int i = 0; i < m.nnx; ++i) {
+      const int n = j * m.nnx + i;
+      uint8_t f = 0;
+      const bool wall = (j == 0 || j == m.nny - 1);
+      if (i == 0 || wall) f |= NF_DIR_V;
+      if (i == 0 || i == m.nnx - 1 || wall) f |= NF_DIR_U;
+      if (i == 0) f |= NF_INFLOW;
+      if (in_solid[n]) f |= NF_IN_SOLID;
+      if (!in_fluid[n]) f |= NF_P_ID;
+      m.node_flags[n] = f;
+      m.node_y[n] = m.yn[j];
+    }
+  // node -> (cell, local) in ascending cell order
+  m.node_cells.assign(m.n_nodes * 4, -1);
+  std::vector<int> cnt(m.n_nodes, 0);
+  for (int c = 0; c < m.n_cells; ++c)
+    for (int l = 0; l < 9; ++l) {
+      const int n = m.cell_nodes[c * 9 + l];
+      m.node_cells[n * 4 + cnt[n]++] = c * 9 + l;
+    }
+  // block pattern: nodes sharing a cell
+  std::vector<std::vector<int>> rows(m.n_nodes);
+  for (int c = 0; c < m.n_cells; ++c)
+    for (int li = 0; li < 9; ++li)
+      for (int lj = 0; lj < 9; ++lj) rows[m.cell_nodes[c * 9 + li]].push_back(m.cell_nodes[c * 9 + lj]);
+  m.rowptr.assign(m.n_nodes + 1, 0);
+  m.colidx.clear();
+  m.blk_row.clear();
+  for (int n = 0; n < m.n_nodes; ++n) {
+    auto& r = rows[n];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    for (int j : r) {
+      m.colidx.push_back(j);
+      m.blk_row.push_back(n);
+    }
+    m.rowptr[n + 1] = (int)m.colidx.size();
+  }
+  m.nnzb = (int)m.colidx.size();
+  m.blk_src.assign((size_t)m.nnzb * 4, -1);
+  m.cell_blk.assign(m.n_cells * 81, -1);
+  std::vector<int> bcnt(m.nnzb, 0);
+  for (int c = 0; c < m.n_cells; ++c)
+    for (int li = 0; li < 9; ++li)
+      for (int lj = 0; lj < 9; ++lj) {
+        const int i = m.cell_nodes[c * 9 + li], j = m.cell_nodes[c * 9 + lj];
+        auto beg = m.colidx.begin() + m.rowptr[i], end = m.colidx.begin() + m.rowptr[i + 1];
+        const int b = (int)(std::lower_bound(beg, end, j) - m.colidx.begin());
+        m.cell_blk[c * 81 + li * 9 + lj] = b;
+        m.blk_src[(size_t)b * 4 + bcnt[b]++] = c * 81 + li * 9 + lj;
+      }
+}
+
+// Coarsen one axis: pair cells inside each segment, keep the break points.
+void coarsen_axis(const std::vector<double>& v, const std::vector<int>& seg, std::vector<double>& vc,
+                  std::vector<int>& segc) {
+  vc.assign(1, v[0]);
+  segc.clear();
+  int off = 0;
+  for (int n : seg) {
+    for (int j = 2; j <= n; j += 2) vc.push_back(v[off + j]);
+    if (n % 2) vc.push_back(v[off + n]);
+    segc.push_back((n + 1) / 2);
+    off += n;
+  }
+}
+
+double lag2(int a, double s) {
+  if (a == 0) return (1 - s) * (1 - 2 * s);
+  if (a == 1) return 4 * s * (1 - s);
+  return s * (2 * s - 1);
+}
+
+// 1D Q2 interpolation from coarse vertices vc to the Q2 nodes of fine vertices vf.
+void prolong_1d(const std::vector<double>& vc, const std::vector<double>& xf, std::vector<int>& pidx,
+                std::vector<double>& pw, std::vector<int>& ridx, std::vector<double>& rw) {
+  const int nf = (int)xf.size(), nc = 2 * ((int)vc.size() - 1) + 1;
+  pidx.assign(nf * 3, -1);
+  pw.assign(nf * 3, 0.0);
+  std::vector<std::vector<std::pair<int, double>>> cols(nc);
+  for (int i = 0; i < nf; ++i) {
+    const double x = xf[i];
+    int cc = (int)(std::upper_bound(vc.begin(), vc.end(), x) - vc.begin()) - 1;
+    cc = std::max(0, std::min(cc, (int)vc.size() - 2));
+    const double s = (x - vc[cc]) / (vc[cc + 1] - vc[cc]);
+    int e = 0;
+    for (int a = 0; a < 3; ++a) {
+      double w = lag2(a, s);
+      if (std::fabs(w) < 1e-13) continue;
+      if (std::fabs(w - 1.0) < 1e-13) w = 1.0;
+      pidx[i * 3 + e] = 2 * cc + a;
+      pw[i * 3 + e] = w;
+      cols[2 * cc + a].push_back({i, w});
+      ++e;
+    }
+  }
+  ridx.assign(nc * 7, -1);
+  rw.assign(nc * 7, 0.0);
+  for (int I = 0; I < nc; ++I)
+    for (size_t e = 0; e < cols[I].size() && e < 7; ++e) {
+      ridx[I * 7 + e] = cols[I][e].first;
+      rw[I * 7 + e] = cols[I][e].second;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device level: tables, transfer from the next finer level, workspace.
+// ---------------------------------------------------------------------------
+struct Level {
+  HostMesh h;
+  DevMesh dm{};
+  Transfer T{};          // coarse = this level, fine = previous level (level >= 1)
+  size_t n = 0;          // dofs
+  std::vector<void*> owned;
+  double *U = nullptr, *Uold = nullptr;       // injected states (level >= 1)
+  double *KV = nullptr;                       // element matrices, then Vanka inverses
+  double *A = nullptr;                        // block-sparse values
+  double *cellbuf = nullptr, *r = nullptr, *x = nullptr, *b = nullptr;
+  double *D = nullptr, *Dinv = nullptr;       // coarsest only
+  int* perm = nullptr;
+  bool coarsest = false;
+};
+
+}  // namespace
+
+struct fsi_ctx {
+  fsi_params prm{};
+  Phys P{};
+  std::vector<Level> lev;
+  int S = 0;            // max batch
+  size_t n = 0;         // fine dofs
+  int m = 0;            // FGMRES restart
+  std::vector<void*> owned;
+  double *Uit = nullptr, *Uold = nullptr, *R = nullptr, *dU = nullptr, *w = nullptr;
+  double *V = nullptr, *Z = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *hcol = nullptr, *hcol2 = nullptr, *scal = nullptr, *resid = nullptr, *partial = nullptr;
+  int *nv = nullptr, *status = nullptr;
+  uint8_t *active = nullptr, *active2 = nullptr;
+  double* t_dev = nullptr;
+  // Parareal workspace
+  double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
+  int red_blocks = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(std::vector<void*>& own, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return fail(FSI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  own.push_back(q);
+  *p = (T*)q;
+  return FSI_OK;
+}
+
+template <typename T>
+int upload(std::vector<void*>& own, const T** p, const std::vector<T>& v) {
+  T* q;
+  TRY(dalloc(own, &q, v.size()));
+  if (!v.empty()) CK(cudaMemcpy(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *p = q;
+  return FSI_OK;
+}
+
+int setup_level(Level& L, int S, bool coarsest, bool need_state) {
+  HostMesh& h = L.h;
+  DevMesh& d = L.dm;
+  d.nnx = h.nnx;
+  d.nny = h.nny;
+  d.n_nodes = h.n_nodes;
+  d.n_cells = h.n_cells;
+  d.nnzb = h.nnzb;
+  TRY(upload(L.owned, &d.cell_nodes, h.cell_nodes));
+  TRY(upload(L.owned, &d.cell_h, h.cell_h));
+  TRY(upload(L.owned, &d.cell_flags, h.cell_flags));
+  TRY(upload(L.owned, &d.node_flags, h.node_flags));
+  TRY(upload(L.owned, &d.node_y, h.node_y));
+  TRY(upload(L.owned, &d.node_cells, h.node_cells));
+  TRY(upload(L.owned, &d.rowptr, h.rowptr));
+  TRY(upload(L.owned, &d.colidx, h.colidx));
+  TRY(upload(L.owned, &d.blk_row, h.blk_row));
+  TRY(upload(L.owned, &d.blk_src, h.blk_src));
+  TRY(upload(L.owned, &d.cell_blk, h.cell_blk));
+  L.n = (size_t)h.n_nodes * 5;
+  L.coarsest = coarsest;
+  if (need_state) {
+    TRY(dalloc(L.owned, &L.U, S * L.n));
+    TRY(dalloc(L.owned, &L.Uold, S * L.n));
+  }
+  TRY(dalloc(L.owned, &L.KV, (size_t)S * h.n_cells * 2025));
+  TRY(dalloc(L.owned, &L.A, (size_t)S * h.nnzb * 25));
+  TRY(dalloc(L.owned, &L.cellbuf, (size_t)S * h.n_cells * 45));
+  TRY(dalloc(L.owned, &L.r, S * L.n));
+  TRY(dalloc(L.owned, &L.x, S * L.n));
+  TRY(dalloc(L.owned, &L.b, S * L.n));
+  if (coarsest) {
+    TRY(dalloc(L.owned, &L.D, (size_t)S * L.n * L.n));
+    TRY(dalloc(L.owned, &L.Dinv, (size_t)S * L.n * L.n));
+    TRY(dalloc(L.owned, &L.perm, (size_t)S * L.n));
+  }
+  return FSI_OK;
+}
+
+int setup_transfer(Level& C, const Level& F) {
+  std::vector<int> pxi, pyi, rxi, ryi;
+  std::vector<double> pxw, pyw, rxw, ryw;
+  prolong_1d(C.h.xv, F.h.xn, pxi, pxw, rxi, rxw);
+  prolong_1d(C.h.yv, F.h.yn, pyi, pyw, ryi, ryw);
+  std::vector<int> inj(C.h.n_nodes);
+  for (int J = 0; J < C.h.nny; ++J)
+    for (int I = 0; I < C.h.nnx; ++I) {
+      int fi = -1, fj = -1;
+      for (int i = 0; i < F.h.nnx; ++i)
+        if (std::fabs(F.h.xn[i] - C.h.xn[I]) < 1e-12) { fi = i; break; }
+      for (int j = 0; j < F.h.nny; ++j)
+        if (std::fabs(F.h.yn[j] - C.h.yn[J]) < 1e-12) { fj = j; break; }
+      if (fi < 0 || fj < 0) return fail(FSI_EINVAL, "coarse node not on the fine grid");
+      inj[J * C.h.nnx + I] = fj * F.h.nnx + fi;
+    }
+  Transfer& T = C.T;
+  T.nnx_f = F.h.nnx;
+  T.nny_f = F.h.nny;
+  T.nnx_c = C.h.nnx;
+  T.nny_c = C.h.nny;
+  TRY(upload(C.owned, &T.px_idx, pxi));
+  TRY(upload(C.owned, &T.px_w, pxw));
+  TRY(upload(C.owned, &T.py_idx, pyi));
+  TRY(upload(C.owned, &T.py_w, pyw));
+  TRY(upload(C.owned, &T.rx_idx, rxi));
+  TRY(upload(C.owned, &T.rx_w, rxw));
+  TRY(upload(C.owned, &T.ry_idx, ryi));
+  TRY(upload(C.owned, &T.ry_w, ryw));
+  TRY(upload(C.owned, &T.inject, inj));
+  return FSI_OK;
+}
+
+// Reference-cell tables: 3-point Gauss rule on [0, 1], Q2 basis, Q1 vertex
+// projection for the local projection stabilisation.
+int upload_tables() {
+  const double gp[3] = {0.5 - std::sqrt(0.15), 0.5, 0.5 + std::sqrt(0.15)};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  auto L = [](int a, double s) { return lag2(a, s); };
+  auto dL = [](int a, double s) { return a == 0 ? 4 * s - 3 : (a == 1 ? 4 - 8 * s : 4 * s - 1); };
+  double phi[9][9], dps[9][9], dpt[9][9], wq[9], phie[3][9], dpse[3][9], dpte[3][9];
+  for (int q2 = 0; q2 < 3; ++q2)
+    for (int q1 = 0; q1 < 3; ++q1) {
+      const int q = q2 * 3 + q1;
+      wq[q] = gw[q1] * gw[q2];
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          const int l = b * 3 + a;
+          phi[q][l] = L(a, gp[q1]) * L(b, gp[q2]);
+          dps[q][l] = dL(a, gp[q1]) * L(b, gp[q2]);
+          dpt[q][l] = L(a, gp[q1]) * dL(b, gp[q2]);
+        }
+    }
+  for (int q = 0; q < 3; ++q)
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) {
+        const int l = b * 3 + a;
+        phie[q][l] = L(a, 1.0) * L(b, gp[q]);
+        dpse[q][l] = dL(a, 1.0) * L(b, gp[q]);
+        dpte[q][l] = L(a, 1.0) * dL(b, gp[q]);
+      }
+  // kappa(phi_l) = phi_l - pi1(phi_l); pi1 phi_l = Q1 vertex function for vertex nodes
+  double kss[9][9] = {}, ktt[9][9] = {};
+  for (int q = 0; q < 9; ++q) {
+    const double s = gp[q % 3], t = gp[q / 3];
+    double gs[9], gt[9];
+    for (int l = 0; l < 9; ++l) {
+      const int a = l % 3, b = l / 3;
+      gs[l] = dps[q][l];
+      gt[l] = dpt[q][l];
+      if (a != 1 && b != 1) {
+        const double Ns = a == 0 ? 1 - s : s, Nt = b == 0 ? 1 - t : t;
+        const double dNs = a == 0 ? -1.0 : 1.0, dNt = b == 0 ? -1.0 : 1.0;
+        gs[l] -= dNs * Nt;
+        gt[l] -= Ns * dNt;
+      }
+    }
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j < 9; ++j) {
+        kss[i][j] += wq[q] * gs[i] * gs[j];
+        ktt[i][j] += wq[q] * gt[i] * gt[j];
+      }
+  }
+  CK(cudaMemcpyToSymbol(c_phi, phi, sizeof(phi)));
+  CK(cudaMemcpyToSymbol(c_dps, dps, sizeof(dps)));
+  CK(cudaMemcpyToSymbol(c_dpt, dpt, sizeof(dpt)));
+  CK(cudaMemcpyToSymbol(c_wq, wq, sizeof(wq)));
+  CK(cudaMemcpyToSymbol(c_phie, phie, sizeof(phie)));
+  CK(cudaMemcpyToSymbol(c_dpse, dpse, sizeof(dpse)));
+  CK(cudaMemcpyToSymbol(c_dpte, dpte, sizeof(dpte)));
+  CK(cudaMemcpyToSymbol(c_we, gw, sizeof(gw)));
+  CK(cudaMemcpyToSymbol(c_lps_ss, kss, sizeof(kss)));
+  CK(cudaMemcpyToSymbol(c_lps_tt, ktt, sizeof(ktt)));
+  return FSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched building blocks
+// ---------------------------------------------------------------------------
+int launch_check() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(FSI_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return FSI_OK;
+}
+
+int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
+             const uint8_t* act, double* R, cudaStream_t st) {
+  k_cell_residual<<<dim3(nblk(L.h.n_cells, 128), S), 128, 0, st>>>(L.dm, c->P, U, Uold, L.n, k, theta, act,
+                                                                     L.cellbuf);
+  k_gather_residual<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, c->P, L.cellbuf, U, L.n, c->t_dev, act, R);
+  return launch_check();
+}
+
+int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
+             const uint8_t* act, double* A, cudaStream_t st) {
+  k_cell_jacobian<<<dim3(L.h.n_cells, S), JAC_THREADS, 0, st>>>(L.dm, c->P, U, Uold, L.n, k, theta, act, L.KV);
+  k_assemble_bsr<<<dim3(nblk((size_t)L.h.nnzb * 5, 128), S), 128, 0, st>>>(L.dm, L.KV, act, A);
+  return launch_check();
+}
+
+template <bool RES>
+int spmv(Level& L, int S, const double* A, const double* x, const double* b, const uint8_t* act, double* y,
+         cudaStream_t st) {
+  k_bsr_spmv<RES><<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.dm, A, x, b, L.n, act, y);
+  return launch_check();
+}
+
+// Norms or dot products with fixed reduction order: out[s*ostride + i] = V_i . w
+int dots(fsi_ctx* c, int S, size_t n, int nv, const double* V, size_t vstride, size_t vslice, const double* w,
+         size_t wstride, const uint8_t* act, double* out, int ostride, bool take_sqrt, cudaStream_t st) {
+  const int nb = (int)nblk(n, RED_CHUNK);
+  k_dots_partial<<<dim3(nb, S), RED_THREADS, 0, st>>>((int)n, nv, V, vstride, vslice, w, wstride, act, c->partial, 64);
+  k_dots_finish<<<S, 64, 0, st>>>(nb, nv, c->partial, 64, act, out, ostride, take_sqrt, false);
+  return launch_check();
+}
+
+// Multigrid setup for the Newton iterate U (level 0) and old state Uold.
+int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
+             cudaStream_t st) {
+  const int NL = (int)c->lev.size();
+  const double* Ul = U;
+  const double* Uol = Uold;
+  for (int l = 0; l < NL; ++l) {
+    Level& L = c->lev[l];
+    if (l > 0) {
+      const Level& F = c->lev[l - 1];
+      k_inject<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T.inject, L.h.n_nodes, Ul, F.n, L.n, act, L.U);
+      k_inject<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T.inject, L.h.n_nodes, Uol, F.n, L.n, act, L.Uold);
+      Ul = L.U;
+      Uol = L.Uold;
+    }
+    TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st));
+    if (L.coarsest) {
+      const int n = (int)L.n;
+      k_dense_from_bsr<<<dim3(nblk((size_t)n * n, 256), S), 256, 0, st>>>(L.dm, L.A, act, L.D);
+      k_dense_invert<<<S, GJ_THREADS, n * sizeof(double), st>>>(n, L.D, L.perm, act, L.Dinv, c->status);
+    } else {
+      k_vanka_setup<<<dim3(L.h.n_cells, S), VK_THREADS, 0, st>>>(L.dm, L.A, act, L.KV, c->status);
+    }
+    TRY(launch_check());
+  }
+  return FSI_OK;
+}
+
+// x = M_l^{-1} b : one V-cycle with Vanka smoothing, x is overwritten.
+int vcycle(fsi_ctx* c, int l, int S, const double* b, double* x, const uint8_t* act, cudaStream_t st) {
+  Level& L = c->lev[l];
+  if (L.coarsest) {
+    k_dense_apply<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>((int)L.n, L.Dinv, b, L.n, act, x);
+    return launch_check();
+  }
+  const int nu = c->prm.mg_smooth;
+  const double om = c->prm.mg_omega;
+  k_fill<<<dim3(nblk(L.n, 256), S), 256, 0, st>>>((int)L.n, 0.0, act, x, L.n);
+  auto smooth = [&](bool first) -> int {
+    const double* r = b;
+    if (!first) {
+      TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
+      r = L.r;
+    }
+    k_vanka_cell<<<dim3(nblk((size_t)L.h.n_cells * 45, 128), S), 128, 0, st>>>(L.dm, L.KV, r, L.n, act, L.cellbuf);
+    k_vanka_gather<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, L.cellbuf, om, L.n, act, x);
+    return launch_check();
+  };
+  for (int i = 0; i < nu; ++i) TRY(smooth(i == 0));
+  Level& C = c->lev[l + 1];
+  TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
+  k_restrict<<<dim3(nblk(C.n, 128), S), 128, 0, st>>>(C.T, L.dm.node_flags, C.dm.node_flags, L.r, L.n, C.n, act, C.b);
+  TRY(launch_check());
+  TRY(vcycle(c, l + 1, S, C.b, C.x, act, st));
+  k_prolong_add<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(C.T, L.dm.node_flags, C.x, L.n, C.n, act, x);
+  TRY(launch_check());
+  for (int i = 0; i < nu; ++i) TRY(smooth(false));
+  return FSI_OK;
+}
+
+// FGMRES(m) with multigrid right preconditioning: solve A x = b per active
+// slice to ||b - A x|| <= rtol ||b||. x is overwritten.
+int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in, fsi_stats* stats, cudaStream_t st) {
+  Level& L = c->lev[0];
+  const size_t n = L.n;
+  const int m = c->m;
+  const size_t vsl = (size_t)(m + 1) * n, zsl = (size_t)m * n;
+  std::vector<uint8_t> act(S), act2(S);
+  std::vector<double> bnorm(S), res(S);
+  std::vector<int> its(S, 0), nvh(S, 0);
+  CK(cudaMemcpyAsync(act.data(), act_in, S, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->active, act_in, S, cudaMemcpyDeviceToDevice, st));
+  k_fill<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, 0.0, c->active, x, n);
+  TRY(dots(c, S, n, 1, b, 0, n, b, n, c->active, c->scal, 1, true, st));
+  CK(cudaMemcpyAsync(bnorm.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double rtol = c->prm.gmres_rtol;
+  int status = FSI_OK;
+  for (int s = 0; s < S; ++s)
+    if (act[s] && !(bnorm[s] > 0.0)) {
+      if (!std::isfinite(bnorm[s])) status = FSI_ENAN;
+      act[s] = 0;
+    }
+  auto any = [&]() { return std::any_of(act.begin(), act.end(), [](uint8_t a) { return a != 0; }); };
+  bool first_cycle = true;
+  while (any()) {
+    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    // r = b - A x  (x = 0 in the first cycle)
+    if (first_cycle) {
+      CK(cudaMemcpy2DAsync(c->V, vsl * sizeof(double), b, n * sizeof(double), n * sizeof(double), S,
+                           cudaMemcpyDeviceToDevice, st));
+    } else {
+      // V[s][0] = b - A x for active slices (strided output through w)
+      TRY(spmv<true>(L, S, L.A, x, b, c->active, c->w, st));
+      CK(cudaMemcpy2DAsync(c->V, vsl * sizeof(double), c->w, n * sizeof(double), n * sizeof(double), S,
+                           cudaMemcpyDeviceToDevice, st));
+    }
+    first_cycle = false;
+    TRY(dots(c, S, n, 1, c->V, 0, vsl, c->V, vsl, c->active, c->scal, 1, true, st));
+    k_init_g<<<nblk(S, 64), 64, 0, st>>>(S, m, c->scal, c->active, c->g);
+    k_scale<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->V, vsl, c->scal, 1, true, c->active, c->V, vsl);
+    TRY(launch_check());
+    std::vector<uint8_t> cyc = act;   // slices still inside this cycle
+    for (int j = 0; j < m; ++j) {
+      CK(cudaMemcpyAsync(c->active, cyc.data(), S, cudaMemcpyHostToDevice, st));
+      double* Vj = c->V + (size_t)j * n;
+      double* Zj = c->Z + (size_t)j * n;
+      // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
+      CK(cudaMemcpy2DAsync(c->dU, n * sizeof(double), Vj, vsl * sizeof(double), n * sizeof(double), S,
+                           cudaMemcpyDeviceToDevice, st));
+      TRY(vcycle(c, 0, S, c->dU, c->R, c->active, st));
+      CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(double), c->R, n * sizeof(double), n * sizeof(double), S,
+                           cudaMemcpyDeviceToDevice, st));
+      // w = A Z_j
+      TRY(spmv<false>(L, S, L.A, c->R, nullptr, c->active, c->w, st));
+      // classical Gram-Schmidt, twice
+      TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol, m + 1, false, st));
+      k_sub_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->hcol, m + 1, c->active, c->w, n);
+      TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol2, m + 1, false, st));
+      k_sub_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->hcol2, m + 1, c->active, c->w, n);
+      k_axpby<<<dim3(1, S), 64, 0, st>>>(j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
+      TRY(dots(c, S, n, 1, c->w, 0, n, c->w, n, c->active, c->scal, 1, true, st));
+      k_scale<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->w, n, c->scal, 1, true, c->active, c->V + (size_t)(j + 1) * n, vsl);
+      k_givens<<<nblk(S, 64), 64, 0, st>>>(S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
+      TRY(launch_check());
+      CK(cudaMemcpyAsync(res.data(), c->resid, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<uint8_t> fin(S, 0);
+      bool any_fin = false, any_left = false;
+      for (int s = 0; s < S; ++s) {
+        if (!cyc[s]) continue;
+        ++its[s];
+        const bool conv = res[s] <= rtol * bnorm[s];
+        const bool bad = !std::isfinite(res[s]);
+        if (conv || bad || j == m - 1 || its[s] >= c->prm.gmres_maxit) {
+          fin[s] = 1;
+          nvh[s] = j + 1;
+          cyc[s] = 0;
+          any_fin = true;
+          if (conv || bad || its[s] >= c->prm.gmres_maxit) {
+            act[s] = 0;
+            if (bad) status = FSI_ENAN;
+            else if (!conv) status = FSI_EGMRES;
+          }
+        } else {
+          any_left = true;
+        }
+      }
+      if (any_fin) {
+        CK(cudaMemcpyAsync(c->active2, fin.data(), S, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->nv, nvh.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_backsolve<<<nblk(S, 64), 64, 0, st>>>(S, m, c->nv, c->H, c->g, c->active2, c->y);
+        k_add_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->nv, c->Z, n, zsl, c->y, m, c->active2, x, n);
+        TRY(launch_check());
+      }
+      if (!any_left) break;
+    }
+  }
+  if (stats) {
+    for (int s = 0; s < S; ++s) {
+      stats->gmres_iters += its[s];
+      stats->max_gmres = std::max(stats->max_gmres, its[s]);
+    }
+  }
+  return status;
+}
+
+// One theta step for S slices (Newton + FGMRES/multigrid).
+int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, double k, double theta, double* U_new,
+               fsi_stats* stats, cudaStream_t st) {
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  Level& L = c->lev[0];
+  const size_t n = L.n;
+  std::vector<double> tn(S);
+  for (int s = 0; s < S; ++s) tn[s] = t_old[s] + k;
+  CK(cudaMemcpyAsync(c->t_dev, tn.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->Uold, U_old, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(c->Uit, U_old, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  std::vector<uint8_t> act(S, 1);
+  std::vector<int> st_h(S, 0);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->status, st_h.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_apply_dirichlet<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, c->P, c->Uit, n, c->t_dev, c->active);
+  TRY(launch_check());
+  std::vector<double> r0(S, 0.0), nr(S);
+  std::vector<int> nit(S, 0);
+  int status = FSI_OK;
+  for (int it = 0;; ++it) {
+    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+    TRY(dots(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
+    CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int s = 0; s < S; ++s) {
+      if (!act[s]) continue;
+      if (!std::isfinite(nr[s])) {
+        status = FSI_ENAN;
+        act[s] = 0;
+        continue;
+      }
+      if (it == 0) r0[s] = nr[s];
+      if (it >= 1 && nr[s] <= c->prm.newton_tol * std::max(r0[s], 1.0)) {
+        act[s] = 0;
+        continue;
+      }
+      if (it >= c->prm.newton_maxit) {
+        status = FSI_ENEWTON;
+        act[s] = 0;
+        continue;
+      }
+      nit[s] = it + 1;
+      any = true;
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    // right-hand side -R
+    k_axpby<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
+    TRY(launch_check());
+    TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st));
+    // FGMRES needs R (rhs) and writes the correction; R is reused as scratch
+    // inside, so copy the rhs first.
+    CK(cudaMemcpyAsync(c->lev[0].b, c->R, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int rc = fgmres(c, S, c->lev[0].b, c->lev[0].x, c->active, stats, st);
+    CK(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int s = 0; s < S; ++s)
+      if (act[s] && st_h[s] != 0) {
+        status = FSI_EJAC;
+        act[s] = 0;
+      }
+    if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed");
+    if (rc == FSI_EGMRES) status = FSI_EGMRES;
+    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    k_axpby<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, 1.0, c->lev[0].x, n, 1.0, c->active, c->Uit, n);
+    TRY(launch_check());
+  }
+  CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    for (int s = 0; s < S; ++s) {
+      stats->newton_iters += nit[s];
+      stats->max_newton = std::max(stats->max_newton, nit[s]);
+    }
+    stats->status = status;
+  }
+  if (status != FSI_OK) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "theta step failed with status %d", status);
+    return fail(status, buf);
+  }
+  return FSI_OK;
+}
+
+int propagate(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, int m, bool fine, fsi_stats* stats,
+              cudaStream_t st) {
+  const double dt = c->prm.T / c->prm.n_slices;
+  const double k = dt / m;
+  const double theta = fine ? 0.5 + c->prm.theta0 * k : 1.0;
+  std::vector<double> t(t0, t0 + S);
+  const double* src = U0;
+  for (int j = 0; j < m; ++j) {
+    TRY(theta_step(c, S, src, t.data(), k, theta, U1, stats, st));
+    for (double& x : t) x += k;
+    src = U1;
+  }
+  if (m == 0 && U1 != U0)
+    CK(cudaMemcpyAsync(U1, U0, S * c->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return FSI_OK;
+}
+
+// Batches of at most max_batch slices.
+int propagate_chunked(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, bool fine, fsi_stats* stats,
+                      cudaStream_t st) {
+  const int m = fine ? c->prm.m_fine : c->prm.m_coarse;
+  for (int s0 = 0; s0 < S; s0 += c->S) {
+    const int b = std::min(c->S, S - s0);
+    TRY(propagate(c, b, U0 + (size_t)s0 * c->n, t0 + s0, U1 + (size_t)s0 * c->n, m, fine, stats, st));
+  }
+  return FSI_OK;
+}
+
+int validate(const fsi_mesh* mesh, const fsi_params* p) {
+  if (!mesh || !p) return fail(FSI_EINVAL, "null mesh or params");
+  if (mesh->n_xseg < 1 || mesh->n_yseg < 1 || !mesh->x_breaks || !mesh->y_breaks || !mesh->nx_seg || !mesh->ny_seg)
+    return fail(FSI_EINVAL, "empty mesh");
+  for (int i = 0; i < mesh->n_xseg; ++i)
+    if (mesh->nx_seg[i] < 1 || !(mesh->x_breaks[i + 1] > mesh->x_breaks[i])) return fail(FSI_EINVAL, "bad x segments");
+  for (int i = 0; i < mesh->n_yseg; ++i)
+    if (mesh->ny_seg[i] < 1 || !(mesh->y_breaks[i + 1] > mesh->y_breaks[i])) return fail(FSI_EINVAL, "bad y segments");
+  if (p->max_batch < 1 || p->n_slices < 1 || p->m_fine < 1 || p->m_coarse < 1 || !(p->T > 0))
+    return fail(FSI_EINVAL, "bad time or batch parameters");
+  if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
+    return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
+  if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5)
+    return fail(FSI_EINVAL, "bad multigrid parameters");
+  return FSI_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* fsi_last_error(void) { return g_err.c_str(); }
+
+void fsi_destroy(fsi_ctx* c) {
+  if (!c) return;
+  for (auto& L : c->lev)
+    for (void* p : L.owned) cudaFree(p);
+  for (void* p : c->owned) cudaFree(p);
+  delete c;
+}
+
+int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
+  if (!out) return fail(FSI_EINVAL, "null output pointer");
+  *out = nullptr;
+  TRY(validate(mesh, p));
+  fsi_ctx* c = new fsi_ctx();
+  auto cleanup = [&](int rc) {
+    fsi_destroy(c);
+    return rc;
+  };
+  c->prm = *p;
+  c->S = p->max_batch;
+  c->m = p->gmres_restart;
+  c->P = Phys{p->rho_f, p->nu_f, p->rho_s, p->mu_s, p->lambda_s, p->vbar, p->ramp_t,
+              mesh->y_breaks[mesh->n_yseg] - mesh->y_breaks[0], mesh->y_breaks[0], p->alpha0};
+  const double box[4] = {mesh->solid_x0, mesh->solid_x1, mesh->solid_y0, mesh->solid_y1};
+  // level hierarchy
+  std::vector<double> xb(mesh->x_breaks, mesh->x_breaks + mesh->n_xseg + 1);
+  std::vector<double> yb(mesh->y_breaks, mesh->y_breaks + mesh->n_yseg + 1);
+  HostMesh h0;
+  h0.xseg.assign(mesh->nx_seg, mesh->nx_seg + mesh->n_xseg);
+  h0.yseg.assign(mesh->ny_seg, mesh->ny_seg + mesh->n_yseg);
+  h0.xv = axis_vertices(xb, h0.xseg);
+  h0.yv = axis_vertices(yb, h0.yseg);
+  build_mesh(h0, mesh->has_solid != 0, box);
+  std::vector<HostMesh> hs{h0};
+  while ((size_t)hs.back().n_nodes * 5 > (size_t)p->mg_coarsest_max_dofs) {
+    const HostMesh& f = hs.back();
+    HostMesh hc;
+    coarsen_axis(f.xv, f.xseg, hc.xv, hc.xseg);
+    coarsen_axis(f.yv, f.yseg, hc.yv, hc.yseg);
+    if (hc.xv.size() == f.xv.size() && hc.yv.size() == f.yv.size()) break;
+    build_mesh(hc, mesh->has_solid != 0, box);
+    hs.push_back(hc);
+  }
+  if ((size_t)hs.back().n_nodes * 5 > 4096) return cleanup(fail(FSI_EINVAL, "coarsest level too large"));
+  c->lev.resize(hs.size());
+  int rc = upload_tables();
+  if (rc) return cleanup(rc);
+  for (size_t l = 0; l < hs.size(); ++l) {
+    c->lev[l].h = hs[l];
+    rc = setup_level(c->lev[l], c->S, l + 1 == hs.size(), l > 0);
+    if (rc) return cleanup(rc);
+    if (l > 0 && (rc = setup_transfer(c->lev[l], c->lev[l - 1]))) return cleanup(rc);
+  }
+  c->n = c->lev[0].n;
+  const size_t S = c->S, n = c->n, m = c->m;
+  auto A = [&](auto** ptr, size_t cnt) { return dalloc(c->owned, ptr, cnt); };
+  if ((rc = A(&c->Uit, S * n)) || (rc = A(&c->Uold, S * n)) || (rc = A(&c->R, S * n)) || (rc = A(&c->dU, S * n)) ||
+      (rc = A(&c->w, S * n)) || (rc = A(&c->V, S * (m + 1) * n)) || (rc = A(&c->Z, S * m * n)) ||
+      (rc = A(&c->H, S * (m + 1) * m)) || (rc = A(&c->cs, S * m)) || (rc = A(&c->sn, S * m)) ||
+      (rc = A(&c->g, S * (m + 1))) || (rc = A(&c->y, S * m)) || (rc = A(&c->hcol, S * (m + 1))) ||
+      (rc = A(&c->hcol2, S * (m + 1))) || (rc = A(&c->scal, S)) || (rc = A(&c->resid, S)) ||
+      (rc = A(&c->partial, S * nblk(n, RED_CHUNK) * 64)) || (rc = A(&c->nv, S)) || (rc = A(&c->status, S)) ||
+      (rc = A(&c->active, S)) || (rc = A(&c->active2, S)) || (rc = A(&c->t_dev, S)))
+    return cleanup(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
+  *out = c;
+  return FSI_OK;
+}
+
+int fsi_n_nodes(const fsi_ctx* c) { return c ? c->lev[0].h.n_nodes : FSI_EINVAL; }
+int fsi_n_dofs(const fsi_ctx* c) { return c ? (int)c->n : FSI_EINVAL; }
+int fsi_n_levels(const fsi_ctx* c) { return c ? (int)c->lev.size() : FSI_EINVAL; }
+int fsi_nnzb(const fsi_ctx* c) { return c ? c->lev[0].h.nnzb : FSI_EINVAL; }
+
+int fsi_bsr_pattern(const fsi_ctx* c, int* rowptr, int* colidx) {
+  if (!c || !rowptr || !colidx) return fail(FSI_EINVAL, "null argument");
+  const HostMesh& h = c->lev[0].h;
+  std::memcpy(rowptr, h.rowptr.data(), h.rowptr.size() * sizeof(int));
+  std::memcpy(colidx, h.colidx.data(), h.colidx.size() * sizeof(int));
+  return FSI_OK;
+}
+
+int fsi_residual(fsi_ctx* c, int S, const double* U, const double* U_old, const double* t_new, double k,
+                 double theta, double* R, void* stream) {
+  if (!c || !U || !U_old || !t_new || !R) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->t_dev, t_new, S * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  TRY(residual(c, c->lev[0], S, U, U_old, k, theta, c->active, R, st));
+  CK(cudaStreamSynchronize(st));
+  return FSI_OK;
+}
+
+int fsi_jacobian(fsi_ctx* c, int S, const double* U, const double* U_old, double k, double theta, double* vals,
+                 void* stream) {
+  if (!c || !U || !U_old || !vals) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  TRY(jacobian(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
+  CK(cudaStreamSynchronize(st));
+  return FSI_OK;
+}
+
+int fsi_bsr_spmv(fsi_ctx* c, int S, const double* vals, const double* x, double* y, void* stream) {
+  if (!c || !vals || !x || !y) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  TRY(spmv<false>(c->lev[0], S, vals, x, nullptr, c->active, y, st));
+  return FSI_OK;
+}
+
+int fsi_theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, double k, double theta,
+                   double* U_new, fsi_stats* stats, void* stream) {
+  if (!c || !U_old || !t_old || !U_new) return fail(FSI_EINVAL, "null argument");
+  if (stats) *stats = fsi_stats{};
+  int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream);
+  if (stats) stats->status = rc;
+  return rc;
+}
+
+int fsi_fine(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, fsi_stats* stats, void* stream) {
+  if (!c || !U0 || !t0 || !U1) return fail(FSI_EINVAL, "null argument");
+  if (S < 1) return fail(FSI_EINVAL, "empty batch");
+  if (stats) *stats = fsi_stats{};
+  int rc = propagate_chunked(c, S, U0, t0, U1, true, stats, (cudaStream_t)stream);
+  if (stats) stats->status = rc;
+  return rc;
+}
+
+int fsi_coarse(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, fsi_stats* stats, void* stream) {
+  if (!c || !U0 || !t0 || !U1) return fail(FSI_EINVAL, "null argument");
+  if (S < 1) return fail(FSI_EINVAL, "empty batch");
+  if (stats) *stats = fsi_stats{};
+  int rc = propagate_chunked(c, S, U0, t0, U1, false, stats, (cudaStream_t)stream);
+  if (stats) stats->status = rc;
+  return rc;
+}
+
+int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parareal_stats* stats, void* stream) {
+  if (!c || !U) return fail(FSI_EINVAL, "null argument");
+  if (max_iter < 0) return fail(FSI_EINVAL, "negative iteration count");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = c->prm.n_slices;
+  const size_t n = c->n;
+  const double dt = c->prm.T / N;
+  fsi_parareal_stats loc{};
+  if (!c->Cold) {
+    c->red_blocks = 152;
+    if (dalloc(c->owned, &c->Cold, (size_t)N * n) || dalloc(c->owned, &c->Fv, (size_t)N * n) ||
+        dalloc(c->owned, &c->Cnew, n) || dalloc(c->owned, &c->ppart, (size_t)c->red_blocks * 6))
+      return FSI_ENOMEM;
+  }
+  std::vector<double> t(N);
+  for (int i = 0; i < N; ++i) t[i] = i * dt;
+  // predictor sweep (iteration 0)
+  for (int i = 0; i < N; ++i) {
+    TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cold + (size_t)i * n, false, &loc.coarse, st));
+    CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    loc.coarse_steps += c->prm.m_coarse;
+  }
+  std::vector<double> part(c->red_blocks * 6);
+  int it = 0;
+  for (it = 1; it <= max_iter && it <= N; ++it) {
+    const int first = it - 1;
+    const int S = N - first;
+    // fine solves of every slice that is not yet exact, batched
+    TRY(propagate_chunked(c, S, U + (size_t)first * n, &t[first], c->Fv + (size_t)first * n, true, &loc.fine, st));
+    loc.fine_steps += (long long)S * c->prm.m_fine;
+    double inc[3] = {0, 0, 0};
+    for (int i = first; i < N; ++i) {
+      const double* Cn;
+      if (i == first) {
+        Cn = c->Cold + (size_t)i * n;   // unchanged input: C(U_i^it) - C(U_i^(it-1)) = 0 exactly
+      } else {
+        TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cnew, false, &loc.coarse, st));
+        loc.coarse_steps += c->prm.m_coarse;
+        Cn = c->Cnew;
+      }
+      k_parareal_correct<<<c->red_blocks, RED_THREADS, 0, st>>>((int)n, c->Fv + (size_t)i * n, Cn,
+                                                                c->Cold + (size_t)i * n, U + (size_t)(i + 1) * n,
+                                                                c->ppart);
+      TRY(launch_check());
+      if (i != first)
+        CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(part.data(), c->ppart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      double a[6] = {0, 0, 0, 0, 0, 0};
+      for (int b = 0; b < c->red_blocks; ++b)
+        for (int f = 0; f < 6; ++f) a[f] += part[b * 6 + f];
+      for (int f = 0; f < 3; ++f) {
+        const double rel = a[3 + f] > 0 ? std::sqrt(a[f] / a[3 + f]) : std::sqrt(a[f]);
+        if (!std::isfinite(rel)) return fail(FSI_EDIVERGE, "Parareal increment is not finite");
+        inc[f] = std::max(inc[f], rel);
+      }
+    }
+    loc.increment_v = inc[0];
+    loc.increment_u = inc[1];
+    loc.increment_p = inc[2];
+    loc.iterations = it;
+    if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
+  }
+  if (stats) *stats = loc;
+  return FSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// Quadrature-point physics of the monolithic ALE fluid-structure step.
+//
+// Sec. 2 of Margenberg & Richter: ALE fluid, Eq. (ALE) with the stress of
+// Eq. (ALE:stress); St. Venant-Kirchhoff solid, Eq. (stress); the shifted
+// Crank-Nicolson step of Sec. 2.3 with the forms of Eq. (semiforms).
+//
+// Conventions: (grad v)_{ij} = d v_i / d x_j, F = I + grad u, J = det F.
+// In 2D the adjugate A = J F^{-1} and the cofactor C = J F^{-T} = A^T are
+// linear in grad u, which keeps most terms polynomial:
+//   J grad v F^{-1} v          = G A v
+//   J sigma_f F^{-T}           = (rho nu / J)(G A C + C G^T C) - p C
+//   J F^{-1} : grad v^T        = tr(G A)
+//   outflow correction          = -(rho nu / J) C G^T C n
+// Every flux is written per test slot: for test component c the slot a = 0
+// multiplies the test function value, a = 1, 2 its x / y derivative.
+//   c = 0, 1  momentum (common test function phi of Eq. (variational))
+//   c = 2, 3  displacement rows: kinematic (solid cells, value slot) or
+//             harmonic mesh extension (fluid cells, derivative slots)
+//   c = 4     divergence row (fluid cells, value slot)
+#pragma once
+
+struct M2 {
+  double a, b, c, d;  // [[a, b], [c, d]]
+};
+
+__host__ __device__ inline M2 m2(double a, double b, double c, double d) { return M2{a, b, c, d}; }
+__host__ __device__ inline M2 operator+(M2 x, M2 y) { return m2(x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d); }
+__host__ __device__ inline M2 operator-(M2 x, M2 y) { return m2(x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d); }
+__host__ __device__ inline M2 operator*(double s, M2 x) { return m2(s * x.a, s * x.b, s * x.c, s * x.d); }
+__host__ __device__ inline M2 mul(M2 x, M2 y) {
+  return m2(x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d);
+}
+__host__ __device__ inline M2 tp(M2 x) { return m2(x.a, x.c, x.b, x.d); }
+__host__ __device__ inline double det(M2 x) { return x.a * x.d - x.b * x.c; }
+__host__ __device__ inline M2 adj(M2 x) { return m2(x.d, -x.b, -x.c, x.a); }   // adj(F) = det(F) F^{-1}
+__host__ __device__ inline double trace(M2 x) { return x.a + x.d; }
+__host__ __device__ inline void mv(M2 x, const double* v, double* out) {
+  out[0] = x.a * v[0] + x.b * v[1];
+  out[1] = x.c * v[0] + x.d * v[1];
+}
+__host__ __device__ inline M2 eye2() { return m2(1.0, 0.0, 0.0, 1.0); }
+
+struct Phys {
+  double rho_f, nu_f, rho_s, mu_s, lambda_s;
+  double vbar, ramp_t, H, y0;
+  double alpha0;
+};
+
+// State at one quadrature point: new and old values and gradients.
+struct QpIn {
+  double v[2], u[2], p;
+  M2 G, Hu;             // grad v, grad u at t_n
+  double vo[2], uo[2];
+  M2 Go, Huo;           // grad v, grad u at t_{n-1}
+};
+
+// Quantities shared by the flux and its linearisation.
+struct QpDerived {
+  M2 F, A, C, Q;        // t_n: F, adj F, cof F, Q = G A C + C G^T C
+  double J;
+  M2 Fo, Ao, Co, Qo;
+  double Jo;
+  M2 Gh, Bh;            // midpoint grad v, F_{n-1/2}^{-1}
+  double Jh;            // (J_{n-1} + J_n) / 2
+  double w[2];          // u_n - u_{n-1}
+  double M[2];          // Gh Bh w
+};
+
+__device__ inline void derive(const QpIn& q, QpDerived& d) {
+  d.F = eye2() + q.Hu;
+  d.J = det(d.F);
+  d.A = adj(d.F);
+  d.C = tp(d.A);
+  d.Q = mul(mul(q.G, d.A), d.C) + mul(mul(d.C, tp(q.G)), d.C);
+  d.Fo = eye2() + q.Huo;
+  d.Jo = det(d.Fo);
+  d.Ao = adj(d.Fo);
+  d.Co = tp(d.Ao);
+  d.Qo = mul(mul(q.Go, d.Ao), d.Co) + mul(mul(d.Co, tp(q.Go)), d.Co);
+  d.Gh = 0.5 * (q.G + q.Go);
+  M2 Fh = eye2() + 0.5 * (q.Hu + q.Huo);
+  d.Bh = (1.0 / det(Fh)) * adj(Fh);
+  d.Jh = 0.5 * (d.J + d.Jo);
+  d.w[0] = q.u[0] - q.uo[0];
+  d.w[1] = q.u[1] - q.uo[1];
+  double t[2];
+  mv(d.Bh, d.w, t);
+  mv(d.Gh, t, d.M);
+}
+
+// First Piola stress of the St. Venant-Kirchhoff solid: F (2 mu E + lambda tr E I).
+__device__ inline M2 first_piola(M2 F, double mu, double lam) {
+  M2 E = 0.5 * (mul(tp(F), F) - eye2());
+  double trE = trace(E);
+  M2 S = 2.0 * mu * E + (lam * trE) * eye2();
+  return mul(F, S);
+}
+
+// Residual flux at a volume quadrature point: out[c * 3 + a].
+__device__ inline void qp_flux(const Phys& P, const QpIn& q, const QpDerived& d, bool solid, double k,
+                               double theta, double* out) {
+  for (int i = 0; i < 15; ++i) out[i] = 0.0;
+  const double kt = k * theta, kto = k * (1.0 - theta);
+  if (!solid) {
+    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+    double Av[2], GAv[2], Aov[2], GoAov[2];
+    mv(d.A, q.v, Av);
+    mv(q.G, Av, GAv);
+    mv(d.Ao, q.vo, Aov);
+    mv(q.Go, Aov, GoAov);
+    for (int c = 0; c < 2; ++c) {
+      double mass = rf * d.Jh * ((q.v[c] - q.vo[c]) - d.M[c]);
+      out[c * 3] = mass + kt * rf * GAv[c] + kto * rf * GoAov[c];
+    }
+    M2 S = kt * ((rn / d.J) * d.Q - q.p * d.C) + kto * ((rn / d.Jo) * d.Qo - q.p * d.Co);
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+    M2 Hh = kt * q.Hu + kto * q.Huo;            // harmonic extension, Sec. 2.1
+    out[7] = Hh.a; out[8] = Hh.b; out[10] = Hh.c; out[11] = Hh.d;
+    out[12] = k * trace(mul(q.G, d.A));          // J F^{-1} : grad v^T
+  } else {
+    M2 Pn = first_piola(d.F, P.mu_s, P.lambda_s), Po = first_piola(d.Fo, P.mu_s, P.lambda_s);
+    M2 S = kt * Pn + kto * Po;
+    for (int c = 0; c < 2; ++c) {
+      out[c * 3] = P.rho_s * (q.v[c] - q.vo[c]);
+      out[6 + c * 3] = (q.u[c] - q.uo[c]) - (kt * q.v[c] + kto * q.vo[c]);   // kinematic row
+    }
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+  }
+}
+
+// Directional derivative of qp_flux in the direction (dv, dG, du, dH, dp) of
+// the t_n unknowns: out[c * 3 + a].
+__device__ inline void qp_flux_lin(const Phys& P, const QpIn& q, const QpDerived& d, bool solid, double k,
+                                   double theta, const double* dv, M2 dG, const double* du, M2 dH, double dp,
+                                   double* out) {
+  for (int i = 0; i < 15; ++i) out[i] = 0.0;
+  const double kt = k * theta, kto = k * (1.0 - theta);
+  if (!solid) {
+    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+    const double dJ = trace(mul(d.A, dH));      // d det F = tr(adj(F) dF)
+    const M2 dA = adj(dH);                       // adj is linear in 2D
+    const M2 dC = tp(dA);
+    // ALE mass / domain convection term with midpoint means
+    const double dJh = 0.5 * dJ;
+    const M2 dGh = 0.5 * dG;
+    const M2 dBh = -0.5 * mul(mul(d.Bh, dH), d.Bh);
+    double t1[2], t2[2], t3[2], t4[2], dM[2];
+    mv(d.Bh, d.w, t1);
+    mv(dGh, t1, t2);
+    mv(dBh, d.w, t1);
+    mv(d.Gh, t1, t3);
+    mv(d.Bh, du, t1);
+    mv(d.Gh, t1, t4);
+    for (int c = 0; c < 2; ++c) dM[c] = t2[c] + t3[c] + t4[c];
+    // convection G A v
+    double Av[2], dGAv[2], GdAv[2], GAdv[2];
+    mv(d.A, q.v, Av);
+    mv(dG, Av, dGAv);
+    mv(dA, q.v, t1);
+    mv(q.G, t1, GdAv);
+    mv(d.A, dv, t1);
+    mv(q.G, t1, GAdv);
+    for (int c = 0; c < 2; ++c) {
+      out[c * 3] = rf * (dJh * ((q.v[c] - q.vo[c]) - d.M[c]) + d.Jh * (dv[c] - dM[c])) +
+                   kt * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
+    }
+    // stress (rho nu / J) Q - p C
+    M2 Gt = tp(q.G), dGt = tp(dG);
+    M2 dQ = mul(mul(dG, d.A), d.C) + mul(mul(q.G, dA), d.C) + mul(mul(q.G, d.A), dC) + mul(mul(dC, Gt), d.C) +
+            mul(mul(d.C, dGt), d.C) + mul(mul(d.C, Gt), dC);
+    M2 S = kt * ((rn / d.J) * dQ - (rn * dJ / (d.J * d.J)) * d.Q - dp * d.C - q.p * dC) - (kto * dp) * d.Co;
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+    M2 Hh = kt * dH;
+    out[7] = Hh.a; out[8] = Hh.b; out[10] = Hh.c; out[11] = Hh.d;
+    out[12] = k * (trace(mul(dG, d.A)) + trace(mul(q.G, dA)));
+  } else {
+    const double mu = P.mu_s, lam = P.lambda_s;
+    M2 E = 0.5 * (mul(tp(d.F), d.F) - eye2());
+    M2 Sig = 2.0 * mu * E + (lam * trace(E)) * eye2();
+    M2 dE = 0.5 * (mul(tp(dH), d.F) + mul(tp(d.F), dH));
+    M2 dSig = 2.0 * mu * dE + (lam * trace(dE)) * eye2();
+    M2 S = kt * (mul(dH, Sig) + mul(d.F, dSig));
+    for (int c = 0; c < 2; ++c) {
+      out[c * 3] = P.rho_s * dv[c];
+      out[6 + c * 3] = du[c] - kt * dv[c];
+    }
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+  }
+}
+
+// Do-nothing correction on the outflow boundary x = x_max (normal n = e_x):
+// -k theta (rho nu / J) C G^T C n - k (1 - theta) (rho nu / J_o) C_o G_o^T C_o n,
+// value slot of the momentum rows. Only gradients enter.
+__device__ inline void edge_flux(const Phys& P, M2 G, M2 Hu, M2 Go, M2 Huo, double k, double theta, double* out) {
+  const double rn = P.rho_f * P.nu_f;
+  M2 F = eye2() + Hu, Fo = eye2() + Huo;
+  M2 C = tp(adj(F)), Co = tp(adj(Fo));
+  M2 T = mul(mul(C, tp(G)), C), To = mul(mul(Co, tp(Go)), Co);
+  double J = det(F), Jo = det(Fo);
+  out[0] = -k * theta * rn / J * T.a - k * (1.0 - theta) * rn / Jo * To.a;
+  out[1] = -k * theta * rn / J * T.c - k * (1.0 - theta) * rn / Jo * To.c;
+}
+
+__device__ inline void edge_flux_lin(const Phys& P, M2 G, M2 Hu, M2 dG, M2 dH, double k, double theta, double* out) {
+  const double rn = P.rho_f * P.nu_f;
+  M2 F = eye2() + Hu;
+  M2 A = adj(F), C = tp(A);
+  double J = det(F);
+  double dJ = trace(mul(A, dH));
+  M2 dC = tp(adj(dH));
+  M2 Gt = tp(G);
+  M2 T = mul(mul(C, Gt), C);
+  M2 dT = mul(mul(dC, Gt), C) + mul(mul(C, tp(dG)), C) + mul(mul(C, Gt), dC);
+  M2 R = (-k * theta * rn) * ((1.0 / J) * dT - (dJ / (J * J)) * T);
+  out[0] = R.a;
+  out[1] = R.c;
+}

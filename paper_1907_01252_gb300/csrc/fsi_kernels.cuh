@@ -1,0 +1,873 @@
+// Device kernels of the batched ALE-FSI step: element residual and Jacobian,
+// deterministic node/block gathers, block-sparse SpMV, Vanka smoother,
+// multigrid transfers, coarsest dense inverse and FGMRES vector kernels.
+//
+// Every kernel takes the slice index from blockIdx.y (or a flattened index)
+// and reads an `active` flag per slice: inactive slices do no work. No kernel
+// uses atomics, so the result of a slice never depends on the other slices of
+// the batch (a batched run is bit-for-bit the serial run of each slice).
+#pragma once
+#include <cstdint>
+
+#include "fsi_element.cuh"
+
+// --------------------------------------------------------------------------
+// Reference-cell tables (3 x 3 Gauss points, Q2 basis, q = q2*3 + q1,
+// local node l = b*3 + a), filled from the host at set-up.
+// --------------------------------------------------------------------------
+__constant__ double c_phi[9][9];
+__constant__ double c_dps[9][9];    // d/ds on the unit square
+__constant__ double c_dpt[9][9];    // d/dt
+__constant__ double c_wq[9];        // product weights on the unit square
+__constant__ double c_phie[3][9];   // edge s = 1, t = Gauss points
+__constant__ double c_dpse[3][9];
+__constant__ double c_dpte[3][9];
+__constant__ double c_we[3];
+__constant__ double c_lps_ss[9][9]; // int grad_s kappa phi_i grad_s kappa phi_j over the unit square
+__constant__ double c_lps_tt[9][9];
+
+enum : uint8_t { NF_DIR_V = 1, NF_DIR_U = 2, NF_P_ID = 4, NF_IN_SOLID = 8, NF_INFLOW = 16 };
+enum : uint8_t { CF_SOLID = 1, CF_OUTFLOW = 2 };
+
+struct DevMesh {
+  int nnx, nny, n_nodes, n_cells, nnzb;
+  const int* cell_nodes;    // [n_cells][9]
+  const double* cell_h;     // [n_cells][2]
+  const uint8_t* cell_flags;
+  const uint8_t* node_flags;
+  const double* node_y;
+  const int* node_cells;    // [n_nodes][4]: cell * 9 + local, ascending cell, -1 pad
+  const int* rowptr;        // [n_nodes + 1]
+  const int* colidx;        // [nnzb]
+  const int* blk_row;       // [nnzb]
+  const int* blk_src;       // [nnzb][4]: cell * 81 + li * 9 + lj, -1 pad
+  const int* cell_blk;      // [n_cells][81]
+};
+
+// Whether cell contribution of test component c enters the row of a node.
+__device__ inline bool row_takes(uint8_t cflags, uint8_t nflags, int c) {
+  const bool solid = cflags & CF_SOLID;
+  if (c < 2) return true;
+  if (c < 4) return solid == bool(nflags & NF_IN_SOLID);
+  return !solid;
+}
+
+__device__ inline bool is_identity_row(uint8_t nflags, int c) {
+  if (c < 2) return nflags & NF_DIR_V;
+  if (c < 4) return nflags & NF_DIR_U;
+  return nflags & NF_P_ID;
+}
+
+__device__ inline double inflow_ramp(double t, double ramp_t) {
+  return t < ramp_t ? 0.5 * (1.0 - cos(M_PI * t / ramp_t)) : 1.0;
+}
+
+// Dirichlet value of component c at a node (parabolic inflow, zero elsewhere).
+__device__ inline double dirichlet_value(const Phys& P, uint8_t nflags, double y, int c, double t) {
+  if (c == 0 && (nflags & NF_INFLOW) && (nflags & NF_DIR_V)) {
+    double yy = y - P.y0;
+    return inflow_ramp(t, P.ramp_t) * 1.5 * P.vbar * 4.0 * yy * (P.H - yy) / (P.H * P.H);
+  }
+  return 0.0;
+}
+
+// Gather the 9 x 5 nodal values of a cell.
+__device__ inline void load_cell(const DevMesh& m, const double* U, int cell, double* Ue) {
+  for (int l = 0; l < 9; ++l) {
+    const double* src = U + (size_t)m.cell_nodes[cell * 9 + l] * 5;
+    for (int c = 0; c < 5; ++c) Ue[l * 5 + c] = src[c];
+  }
+}
+
+// alpha_K = alpha0 h_K^2 / (rho_f nu_f + rho_f |vbar_K| h_K), vbar_K the cell mean of v_{n-1}.
+__device__ inline double lps_weight(const Phys& P, const double* Uo, double hx, double hy) {
+  double mx = 0.0, my = 0.0, ws = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    double vx = 0.0, vy = 0.0;
+    for (int l = 0; l < 9; ++l) {
+      vx += c_phi[q][l] * Uo[l * 5 + 0];
+      vy += c_phi[q][l] * Uo[l * 5 + 1];
+    }
+    mx += c_wq[q] * vx;
+    my += c_wq[q] * vy;
+    ws += c_wq[q];
+  }
+  mx /= ws;
+  my /= ws;
+  double h = sqrt(hx * hx + hy * hy);
+  return P.alpha0 * h * h / (P.rho_f * P.nu_f + P.rho_f * sqrt(mx * mx + my * my) * h);
+}
+
+// Values and gradients of all fields at volume quadrature point q.
+__device__ inline void eval_qp(const double* Ue, const double* Uo, int q, double ihx, double ihy, QpIn& s) {
+  double val[5] = {0, 0, 0, 0, 0}, gx[5] = {0, 0, 0, 0, 0}, gy[5] = {0, 0, 0, 0, 0};
+  double valo[4] = {0, 0, 0, 0}, gxo[4] = {0, 0, 0, 0}, gyo[4] = {0, 0, 0, 0};
+  for (int l = 0; l < 9; ++l) {
+    const double ph = c_phi[q][l], ps = c_dps[q][l] * ihx, pt = c_dpt[q][l] * ihy;
+    for (int c = 0; c < 5; ++c) {
+      val[c] += ph * Ue[l * 5 + c];
+      gx[c] += ps * Ue[l * 5 + c];
+      gy[c] += pt * Ue[l * 5 + c];
+    }
+    for (int c = 0; c < 4; ++c) {
+      valo[c] += ph * Uo[l * 5 + c];
+      gxo[c] += ps * Uo[l * 5 + c];
+      gyo[c] += pt * Uo[l * 5 + c];
+    }
+  }
+  s.v[0] = val[0]; s.v[1] = val[1]; s.u[0] = val[2]; s.u[1] = val[3]; s.p = val[4];
+  s.G = m2(gx[0], gy[0], gx[1], gy[1]);
+  s.Hu = m2(gx[2], gy[2], gx[3], gy[3]);
+  s.vo[0] = valo[0]; s.vo[1] = valo[1]; s.uo[0] = valo[2]; s.uo[1] = valo[3];
+  s.Go = m2(gxo[0], gyo[0], gxo[1], gyo[1]);
+  s.Huo = m2(gxo[2], gyo[2], gxo[3], gyo[3]);
+}
+
+__device__ inline void eval_edge_grad(const double* U, int q, double ihx, double ihy, M2& G, M2& Hu) {
+  double gx[4] = {0, 0, 0, 0}, gy[4] = {0, 0, 0, 0};
+  for (int l = 0; l < 9; ++l) {
+    const double ps = c_dpse[q][l] * ihx, pt = c_dpte[q][l] * ihy;
+    for (int c = 0; c < 4; ++c) {
+      gx[c] += ps * U[l * 5 + c];
+      gy[c] += pt * U[l * 5 + c];
+    }
+  }
+  G = m2(gx[0], gy[0], gx[1], gy[1]);
+  Hu = m2(gx[2], gy[2], gx[3], gy[3]);
+}
+
+// --------------------------------------------------------------------------
+// Element residual: one thread per (slice, cell) -> cellbuf[s][cell][45].
+// --------------------------------------------------------------------------
+__global__ void k_cell_residual(DevMesh m, Phys P, const double* __restrict__ U, const double* __restrict__ Uold,
+                                size_t stride, double k, double theta, const uint8_t* __restrict__ active,
+                                double* __restrict__ cellbuf) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || cell >= m.n_cells) return;
+  double Ue[45], Uo[45], R[45];
+  load_cell(m, U + s * stride, cell, Ue);
+  load_cell(m, Uold + s * stride, cell, Uo);
+  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const uint8_t cf = m.cell_flags[cell];
+  const bool solid = cf & CF_SOLID;
+  for (int i = 0; i < 45; ++i) R[i] = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    QpIn st;
+    QpDerived dd;
+    eval_qp(Ue, Uo, q, ihx, ihy, st);
+    derive(st, dd);
+    double f[15];
+    qp_flux(P, st, dd, solid, k, theta, f);
+    const double w = c_wq[q] * area;
+    for (int l = 0; l < 9; ++l) {
+      const double b0 = w * c_phi[q][l], b1 = w * c_dps[q][l] * ihx, b2 = w * c_dpt[q][l] * ihy;
+      for (int c = 0; c < 5; ++c) R[l * 5 + c] += b0 * f[c * 3] + b1 * f[c * 3 + 1] + b2 * f[c * 3 + 2];
+    }
+  }
+  if (!solid) {
+    const double a = lps_weight(P, Uo, hx, hy) * k;
+    const double sx = hy * ihx, sy = hx * ihy;
+    for (int i = 0; i < 9; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < 9; ++j) acc += (sx * c_lps_ss[i][j] + sy * c_lps_tt[i][j]) * Ue[j * 5 + 4];
+      R[i * 5 + 4] += a * acc;
+    }
+    if (cf & CF_OUTFLOW) {
+      for (int q = 0; q < 3; ++q) {
+        M2 G, Hu, Go, Huo;
+        eval_edge_grad(Ue, q, ihx, ihy, G, Hu);
+        eval_edge_grad(Uo, q, ihx, ihy, Go, Huo);
+        double e[2];
+        edge_flux(P, G, Hu, Go, Huo, k, theta, e);
+        const double w = c_we[q] * hy;
+        for (int l = 0; l < 9; ++l) {
+          R[l * 5 + 0] += w * c_phie[q][l] * e[0];
+          R[l * 5 + 1] += w * c_phie[q][l] * e[1];
+        }
+      }
+    }
+  }
+  double* out = cellbuf + ((size_t)s * m.n_cells + cell) * 45;
+  for (int i = 0; i < 45; ++i) out[i] = R[i];
+}
+
+// Node gather of the residual in fixed cell order, identity rows last.
+__global__ void k_gather_residual(DevMesh m, Phys P, const double* __restrict__ cellbuf, const double* __restrict__ U,
+                                  size_t stride, const double* __restrict__ t_new, const uint8_t* __restrict__ active,
+                                  double* __restrict__ R) {
+  const int s = blockIdx.y;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || node >= m.n_nodes) return;
+  const uint8_t nf = m.node_flags[node];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int e = 0; e < 4; ++e) {
+    const int code = m.node_cells[node * 4 + e];
+    if (code < 0) break;
+    const int cell = code / 9, l = code % 9;
+    const uint8_t cf = m.cell_flags[cell];
+    const double* src = cellbuf + ((size_t)s * m.n_cells + cell) * 45 + l * 5;
+    for (int c = 0; c < 5; ++c)
+      if (row_takes(cf, nf, c)) acc[c] += src[c];
+  }
+  const double* Un = U + s * stride + (size_t)node * 5;
+  double* out = R + s * stride + (size_t)node * 5;
+  for (int c = 0; c < 5; ++c) {
+    if (is_identity_row(nf, c)) acc[c] = Un[c] - dirichlet_value(P, nf, m.node_y[node], c, t_new[s]);
+    out[c] = acc[c];
+  }
+}
+
+// Impose the Dirichlet data of time t[s] on a state.
+__global__ void k_apply_dirichlet(DevMesh m, Phys P, double* __restrict__ U, size_t stride, const double* __restrict__ t,
+                                  const uint8_t* __restrict__ active) {
+  const int s = blockIdx.y;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || node >= m.n_nodes) return;
+  const uint8_t nf = m.node_flags[node];
+  double* x = U + s * stride + (size_t)node * 5;
+  for (int c = 0; c < 4; ++c)
+    if (is_identity_row(nf, c)) x[c] = dirichlet_value(P, nf, m.node_y[node], c, t[s]);
+}
+
+// --------------------------------------------------------------------------
+// Element Jacobian: one CTA of 128 threads per (slice, cell).
+// K[(i,ci),(j,cj)] = sum_q w_q sum_{a,b} B_a(i,q) D_q[(ci,a),(cj,b)] B_b(j,q)
+// with D_q the linearised flux (15 test slots x 15 trial directions).
+// --------------------------------------------------------------------------
+constexpr int JAC_THREADS = 128;
+
+__global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
+                                                               const double* __restrict__ Uold, size_t stride,
+                                                               double k, double theta,
+                                                               const uint8_t* __restrict__ active,
+                                                               double* __restrict__ Ke) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x;
+  if (!active[s]) return;
+  __shared__ double sU[45], sUo[45];
+  __shared__ QpIn sq[9];
+  __shared__ QpDerived sd[9];
+  __shared__ double sD[9][15][15];     // [q][test slot][trial direction]
+  __shared__ double sDe[3][2][12];     // outflow edge: [q][momentum comp][trial direction (c<4)]
+  __shared__ double sAlpha;
+  const int tid = threadIdx.x;
+  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const uint8_t cf = m.cell_flags[cell];
+  const bool solid = cf & CF_SOLID;
+  const bool outflow = !solid && (cf & CF_OUTFLOW);
+  if (tid < 45) {
+    sU[tid] = U[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+    sUo[tid] = Uold[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+  }
+  __syncthreads();
+  if (tid < 9) {
+    eval_qp(sU, sUo, tid, ihx, ihy, sq[tid]);
+    derive(sq[tid], sd[tid]);
+  }
+  if (tid == 32 && !solid) sAlpha = lps_weight(P, sUo, hx, hy);
+  __syncthreads();
+  for (int t = tid; t < 9 * 15; t += JAC_THREADS) {
+    const int q = t / 15, dir = t % 15, cj = dir / 3, b = dir % 3;
+    double dv[2] = {0, 0}, du[2] = {0, 0}, dp = 0.0;
+    M2 dG = m2(0, 0, 0, 0), dH = m2(0, 0, 0, 0);
+    // unit trial direction: value (b = 0) or x / y derivative (b = 1, 2) of component cj
+    if (cj < 2) {
+      if (b == 0) dv[cj] = 1.0;
+      else if (cj == 0) { if (b == 1) dG.a = 1.0; else dG.b = 1.0; }
+      else { if (b == 1) dG.c = 1.0; else dG.d = 1.0; }
+    } else if (cj < 4) {
+      const int c = cj - 2;
+      if (b == 0) du[c] = 1.0;
+      else if (c == 0) { if (b == 1) dH.a = 1.0; else dH.b = 1.0; }
+      else { if (b == 1) dH.c = 1.0; else dH.d = 1.0; }
+    } else {
+      if (b == 0) dp = 1.0;
+    }
+    double out[15];
+    qp_flux_lin(P, sq[q], sd[q], solid, k, theta, dv, dG, du, dH, dp, out);
+    for (int r = 0; r < 15; ++r) sD[q][r][dir] = out[r];
+  }
+  if (outflow) {
+    for (int t = tid; t < 3 * 12; t += JAC_THREADS) {
+      const int q = t / 12, dir = t % 12, cj = dir / 3, b = dir % 3;
+      M2 G, Hu;
+      eval_edge_grad(sU, q, ihx, ihy, G, Hu);
+      M2 dG = m2(0, 0, 0, 0), dH = m2(0, 0, 0, 0);
+      double out[2] = {0, 0};
+      if (b > 0) {
+        M2& X = cj < 2 ? dG : dH;
+        const int c = cj % 2;
+        if (c == 0) { if (b == 1) X.a = 1.0; else X.b = 1.0; }
+        else { if (b == 1) X.c = 1.0; else X.d = 1.0; }
+        edge_flux_lin(P, G, Hu, dG, dH, k, theta, out);
+      }
+      sDe[q][0][dir] = out[0];
+      sDe[q][1][dir] = out[1];
+    }
+  }
+  __syncthreads();
+  double* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
+  for (int e = tid; e < 2025; e += JAC_THREADS) {
+    const int row = e / 45, col = e % 45;
+    const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
+    double acc = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      const double Bi[3] = {c_phi[q][i], c_dps[q][i] * ihx, c_dpt[q][i] * ihy};
+      const double Bj[3] = {c_phi[q][j], c_dps[q][j] * ihx, c_dpt[q][j] * ihy};
+      double sum = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double* Drow = sD[q][ci * 3 + a] + cj * 3;
+        sum += Bi[a] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+      }
+      acc += c_wq[q] * area * sum;
+    }
+    if (!solid && ci == 4 && cj == 4)
+      acc += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
+    if (outflow && ci < 2 && cj < 4) {
+      for (int q = 0; q < 3; ++q) {
+        const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
+        const double* Drow = sDe[q][ci] + cj * 3;
+        acc += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+      }
+    }
+    out[e] = acc;
+  }
+}
+
+// Block-sparse assembly: one thread per (slice, block, row component),
+// fixed-order sum over the cells sharing both nodes, identity rows replaced.
+__global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const uint8_t* __restrict__ active,
+                               double* __restrict__ A) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= m.nnzb * 5) return;
+  const int b = t / 5, ci = t % 5;
+  const int i = m.blk_row[b], j = m.colidx[b];
+  const uint8_t nf = m.node_flags[i];
+  double acc[5] = {0, 0, 0, 0, 0};
+  if (is_identity_row(nf, ci)) {
+    if (i == j) acc[ci] = 1.0;
+  } else {
+    for (int e = 0; e < 4; ++e) {
+      const int code = m.blk_src[b * 4 + e];
+      if (code < 0) break;
+      const int cell = code / 81, li = (code / 9) % 9, lj = code % 9;
+      if (!row_takes(m.cell_flags[cell], nf, ci)) continue;
+      const double* src = Ke + ((size_t)s * m.n_cells + cell) * 2025 + (li * 5 + ci) * 45 + lj * 5;
+      for (int cj = 0; cj < 5; ++cj) acc[cj] += src[cj];
+    }
+  }
+  double* dst = A + ((size_t)s * m.nnzb + b) * 25 + ci * 5;
+  for (int cj = 0; cj < 5; ++cj) dst[cj] = acc[cj];
+}
+
+// --------------------------------------------------------------------------
+// Block-sparse matrix-vector product, y = A x or y = b - A x.
+// One thread per (slice, row dof).
+// --------------------------------------------------------------------------
+template <bool RESIDUAL>
+__global__ void k_bsr_spmv(DevMesh m, const double* __restrict__ A, const double* __restrict__ x,
+                           const double* __restrict__ bvec, size_t stride, const uint8_t* __restrict__ active,
+                           double* __restrict__ y) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= m.n_nodes * 5) return;
+  const int i = t / 5, c = t % 5;
+  const double* As = A + (size_t)s * m.nnzb * 25;
+  const double* xs = x + s * stride;
+  double acc = 0.0;
+  for (int b = m.rowptr[i]; b < m.rowptr[i + 1]; ++b) {
+    const double* blk = As + (size_t)b * 25 + c * 5;
+    const double* xj = xs + (size_t)m.colidx[b] * 5;
+    acc += blk[0] * xj[0] + blk[1] * xj[1] + blk[2] * xj[2] + blk[3] * xj[3] + blk[4] * xj[4];
+  }
+  if (RESIDUAL) acc = bvec[s * stride + t] - acc;
+  y[s * stride + t] = acc;
+}
+
+// --------------------------------------------------------------------------
+// Vanka smoother: local 45 x 45 matrices A restricted to a cell's dofs,
+// inverted by Gauss-Jordan with partial pivoting (one CTA per slice-cell),
+// stored transposed: inv[s][cell][col][row].
+// --------------------------------------------------------------------------
+constexpr int VK_THREADS = 128;
+
+__global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const double* __restrict__ A,
+                                                            const uint8_t* __restrict__ active,
+                                                            double* __restrict__ inv, int* __restrict__ status) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x;
+  if (!active[s]) return;
+  __shared__ double M[45][46];
+  __shared__ double I[45][46];
+  __shared__ int piv;
+  __shared__ double colk[45];
+  const int tid = threadIdx.x;
+  const double* As = A + (size_t)s * m.nnzb * 25;
+  for (int e = tid; e < 2025; e += VK_THREADS) {
+    const int r = e / 45, c = e % 45;
+    const int blk = m.cell_blk[cell * 81 + (r / 5) * 9 + c / 5];
+    M[r][c] = As[(size_t)blk * 25 + (r % 5) * 5 + c % 5];
+    I[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  bool singular = false;
+  for (int kk = 0; kk < 45; ++kk) {
+    if (tid == 0) {
+      int p = kk;
+      double best = fabs(M[kk][kk]);
+      for (int r = kk + 1; r < 45; ++r)
+        if (fabs(M[r][kk]) > best) { best = fabs(M[r][kk]); p = r; }
+      piv = (best > 0.0) ? p : -1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p < 0) { singular = true; break; }
+    if (p != kk) {
+      for (int c = tid; c < 45; c += VK_THREADS) {
+        double t0 = M[kk][c]; M[kk][c] = M[p][c]; M[p][c] = t0;
+        double t1 = I[kk][c]; I[kk][c] = I[p][c]; I[p][c] = t1;
+      }
+    }
+    __syncthreads();
+    const double d = 1.0 / M[kk][kk];
+    __syncthreads();
+    for (int c = tid; c < 45; c += VK_THREADS) { M[kk][c] *= d; I[kk][c] *= d; }
+    __syncthreads();
+    for (int r = tid; r < 45; r += VK_THREADS) colk[r] = M[r][kk];
+    __syncthreads();
+    for (int e = tid; e < 2025; e += VK_THREADS) {
+      const int r = e / 45, c = e % 45;
+      if (r != kk) {
+        const double f = colk[r];
+        M[r][c] -= f * M[kk][c];
+        I[r][c] -= f * I[kk][c];
+      }
+    }
+    __syncthreads();
+  }
+  if (singular) {
+    if (tid == 0) status[s] = -6;
+    return;
+  }
+  double* dst = inv + ((size_t)s * m.n_cells + cell) * 2025;
+  for (int e = tid; e < 2025; e += VK_THREADS) {
+    const int c = e / 45, r = e % 45;
+    dst[e] = I[r][c];
+  }
+}
+
+// z_cell = inv_cell * r_cell: one thread per (slice, cell, local row).
+__global__ void k_vanka_cell(DevMesh m, const double* __restrict__ inv, const double* __restrict__ r, size_t stride,
+                             const uint8_t* __restrict__ active, double* __restrict__ cellbuf) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= m.n_cells * 45) return;
+  const int cell = t / 45, row = t % 45;
+  const double* Mi = inv + ((size_t)s * m.n_cells + cell) * 2025;
+  const double* rs = r + s * stride;
+  double acc = 0.0;
+  for (int l = 0; l < 9; ++l) {
+    const double* rl = rs + (size_t)m.cell_nodes[cell * 9 + l] * 5;
+    for (int c = 0; c < 5; ++c) acc += Mi[(l * 5 + c) * 45 + row] * rl[c];
+  }
+  cellbuf[((size_t)s * m.n_cells + cell) * 45 + row] = acc;
+}
+
+// x += omega * (sum over the node's cells of z) / (number of cells).
+__global__ void k_vanka_gather(DevMesh m, const double* __restrict__ cellbuf, double omega, size_t stride,
+                               const uint8_t* __restrict__ active, double* __restrict__ x) {
+  const int s = blockIdx.y;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || node >= m.n_nodes) return;
+  double acc[5] = {0, 0, 0, 0, 0};
+  int cnt = 0;
+  for (int e = 0; e < 4; ++e) {
+    const int code = m.node_cells[node * 4 + e];
+    if (code < 0) break;
+    const double* src = cellbuf + ((size_t)s * m.n_cells + code / 9) * 45 + (code % 9) * 5;
+    for (int c = 0; c < 5; ++c) acc[c] += src[c];
+    ++cnt;
+  }
+  const double w = omega / cnt;
+  double* xs = x + s * stride + (size_t)node * 5;
+  for (int c = 0; c < 5; ++c) xs[c] += w * acc[c];
+}
+
+// --------------------------------------------------------------------------
+// Multigrid transfers (tensor products of 1D Q2 interpolation tables).
+// --------------------------------------------------------------------------
+struct Transfer {
+  int nnx_f, nny_f, nnx_c, nny_c;
+  const int* px_idx;  const double* px_w;   // [nnx_f][3] coarse index / weight (-1 pad)
+  const int* py_idx;  const double* py_w;   // [nny_f][3]
+  const int* rx_idx;  const double* rx_w;   // [nnx_c][7] fine index / weight (-1 pad)
+  const int* ry_idx;  const double* ry_w;   // [nny_c][7]
+  const int* inject;                        // [n_nodes_c] fine node of each coarse node
+};
+
+__device__ inline bool is_free(uint8_t nf, int c) { return !is_identity_row(nf, c); }
+
+__global__ void k_restrict(Transfer T, const uint8_t* __restrict__ nflags_f, const uint8_t* __restrict__ nflags_c,
+                           const double* __restrict__ rf, size_t stride_f, size_t stride_c,
+                           const uint8_t* __restrict__ active, double* __restrict__ rc) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_c = T.nnx_c * T.nny_c;
+  if (!active[s] || t >= n_c * 5) return;
+  const int node = t / 5, c = t % 5;
+  const int I = node % T.nnx_c, Jy = node / T.nnx_c;
+  double acc = 0.0;
+  if (is_free(nflags_c[node], c)) {
+    const double* r = rf + s * stride_f;
+    for (int ey = 0; ey < 7; ++ey) {
+      const int j = T.ry_idx[Jy * 7 + ey];
+      if (j < 0) break;
+      const double wy = T.ry_w[Jy * 7 + ey];
+      for (int ex = 0; ex < 7; ++ex) {
+        const int i = T.rx_idx[I * 7 + ex];
+        if (i < 0) break;
+        const int fn = j * T.nnx_f + i;
+        if (is_free(nflags_f[fn], c)) acc += wy * T.rx_w[I * 7 + ex] * r[(size_t)fn * 5 + c];
+      }
+    }
+  }
+  rc[s * stride_c + t] = acc;
+}
+
+__global__ void k_prolong_add(Transfer T, const uint8_t* __restrict__ nflags_f, const double* __restrict__ xc,
+                              size_t stride_f, size_t stride_c, const uint8_t* __restrict__ active,
+                              double* __restrict__ xf) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_f = T.nnx_f * T.nny_f;
+  if (!active[s] || t >= n_f * 5) return;
+  const int node = t / 5, c = t % 5;
+  if (!is_free(nflags_f[node], c)) return;
+  const int i = node % T.nnx_f, j = node / T.nnx_f;
+  const double* x = xc + s * stride_c;
+  double acc = 0.0;
+  for (int ey = 0; ey < 3; ++ey) {
+    const int J = T.py_idx[j * 3 + ey];
+    if (J < 0) break;
+    const double wy = T.py_w[j * 3 + ey];
+    for (int ex = 0; ex < 3; ++ex) {
+      const int I = T.px_idx[i * 3 + ex];
+      if (I < 0) break;
+      acc += wy * T.px_w[i * 3 + ex] * x[((size_t)J * T.nnx_c + I) * 5 + c];
+    }
+  }
+  xf[s * stride_f + t] += acc;
+}
+
+__global__ void k_inject(const int* __restrict__ inject, int n_c, const double* __restrict__ Uf, size_t stride_f,
+                         size_t stride_c, const uint8_t* __restrict__ active, double* __restrict__ Uc) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= n_c * 5) return;
+  Uc[s * stride_c + t] = Uf[s * stride_f + (size_t)inject[t / 5] * 5 + t % 5];
+}
+
+// --------------------------------------------------------------------------
+// Coarsest level: dense matrix, Gauss-Jordan inverse (one CTA per slice),
+// stored transposed, and its product.
+// --------------------------------------------------------------------------
+__global__ void k_dense_from_bsr(DevMesh m, const double* __restrict__ A, const uint8_t* __restrict__ active,
+                                 double* __restrict__ D) {
+  const int s = blockIdx.y;
+  const int n = m.n_nodes * 5;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= n * n) return;
+  const int r = t / n, c = t % n;
+  const int i = r / 5, j = c / 5;
+  double v = 0.0;
+  for (int b = m.rowptr[i]; b < m.rowptr[i + 1]; ++b)
+    if (m.colidx[b] == j) { v = A[((size_t)s * m.nnzb + b) * 25 + (r % 5) * 5 + c % 5]; break; }
+  D[(size_t)s * n * n + t] = v;
+}
+
+constexpr int GJ_THREADS = 1024;
+
+// In-place Gauss-Jordan inversion with partial pivoting of D[s] (n x n,
+// row-major); the inverse is written transposed to inv[s].
+__global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, double* __restrict__ D, int* __restrict__ perm,
+                                                             const uint8_t* __restrict__ active,
+                                                             double* __restrict__ inv, int* __restrict__ status) {
+  const int s = blockIdx.x;
+  if (!active[s]) return;
+  double* M = D + (size_t)s * n * n;
+  int* pr = perm + (size_t)s * n;
+  __shared__ double red_v[GJ_THREADS / 32];
+  __shared__ int red_i[GJ_THREADS / 32];
+  __shared__ int piv;
+  __shared__ double pinv;
+  extern __shared__ double colk[];   // [n]
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  for (int r = tid; r < n; r += GJ_THREADS) pr[r] = r;
+  __syncthreads();
+  for (int kk = 0; kk < n; ++kk) {
+    double best = -1.0;
+    int bi = kk;
+    for (int r = kk + tid; r < n; r += GJ_THREADS) {
+      const double a = fabs(M[(size_t)r * n + kk]);
+      if (a > best) { best = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red_v[0];
+      int ii = red_i[0];
+      for (int w = 1; w < GJ_THREADS / 32; ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
+      piv = (b > 0.0) ? ii : -1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p < 0) {
+      if (tid == 0) status[s] = -6;
+      return;
+    }
+    if (p != kk) {
+      for (int c = tid; c < n; c += GJ_THREADS) {
+        const double t0 = M[(size_t)kk * n + c];
+        M[(size_t)kk * n + c] = M[(size_t)p * n + c];
+        M[(size_t)p * n + c] = t0;
+      }
+      if (tid == 0) { const int t1 = pr[kk]; pr[kk] = pr[p]; pr[p] = t1; }
+    }
+    __syncthreads();
+    if (tid == 0) pinv = 1.0 / M[(size_t)kk * n + kk];
+    __syncthreads();
+    const double d = pinv;
+    // in-place Gauss-Jordan: column kk becomes the kk-th column of the inverse
+    for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)kk * n + c] = (c == kk) ? d : M[(size_t)kk * n + c] * d;
+    for (int r = tid; r < n; r += GJ_THREADS) colk[r] = (r == kk) ? 0.0 : M[(size_t)r * n + kk];
+    __syncthreads();
+    for (int e = tid; e < n * n; e += GJ_THREADS) {
+      const int r = e / n, c = e % n;
+      if (r == kk) continue;
+      const double f = colk[r];
+      if (c == kk) M[e] = -f * d;
+      else M[e] -= f * M[(size_t)kk * n + c];
+    }
+    __syncthreads();
+  }
+  // undo the row permutation on the columns: inv[:, pr[c]] = M[:, c]
+  double* out = inv + (size_t)s * n * n;
+  for (int e = tid; e < n * n; e += GJ_THREADS) {
+    const int r = e / n, c = e % n;
+    out[(size_t)pr[c] * n + r] = M[e];   // transposed storage: out[col][row]
+  }
+}
+
+// y = inv x with inv stored transposed: one thread per (slice, row).
+__global__ void k_dense_apply(int n, const double* __restrict__ inv, const double* __restrict__ x, size_t stride,
+                              const uint8_t* __restrict__ active, double* __restrict__ y) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  const double* M = inv + (size_t)s * n * n;
+  const double* xs = x + s * stride;
+  double acc = 0.0;
+  for (int c = 0; c < n; ++c) acc += M[(size_t)c * n + r] * xs[c];
+  y[s * stride + r] = acc;
+}
+
+// --------------------------------------------------------------------------
+// Vector kernels for FGMRES and Newton (per slice, fixed reduction order).
+// --------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+constexpr int RED_CHUNK = 4096;   // rows per block: the partition depends on n only
+
+// partial[s][blk][i] = sum over this block's rows of V[s][i][row] * w[s][row], i < nv.
+__global__ void __launch_bounds__(RED_THREADS) k_dots_partial(int n, int nv, const double* __restrict__ V,
+                                                              size_t vstride, size_t vslice,
+                                                              const double* __restrict__ w, size_t wstride,
+                                                              const uint8_t* __restrict__ active,
+                                                              double* __restrict__ partial, int max_nv) {
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  __shared__ double red[RED_THREADS / 32][64];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const int r0 = blockIdx.x * RED_CHUNK;
+  const int r1 = min(n, r0 + RED_CHUNK);
+  const double* Vs = V + s * vslice;
+  const double* ws = w + s * wstride;
+  for (int i = 0; i < nv; ++i) {
+    double acc = 0.0;
+    const double* vi = Vs + i * vstride;
+    for (int r = r0 + tid; r < r1; r += RED_THREADS) acc += vi[r] * ws[r];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp][i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < nv; i += RED_THREADS) {
+    double acc = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) acc += red[wv][i];
+    partial[((size_t)s * gridDim.x + blockIdx.x) * max_nv + i] = acc;
+  }
+}
+
+// out[s][i] = sum_blk partial[s][blk][i] (fixed order); optional sqrt.
+__global__ void k_dots_finish(int nblk, int nv, const double* __restrict__ partial, int max_nv,
+                              const uint8_t* __restrict__ active, double* __restrict__ out, int out_stride,
+                              bool take_sqrt, bool accumulate) {
+  const int s = blockIdx.x;
+  const int i = threadIdx.x;
+  if (!active[s] || i >= nv) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += partial[((size_t)s * nblk + b) * max_nv + i];
+  if (take_sqrt) acc = sqrt(acc);
+  if (accumulate) out[s * out_stride + i] += acc;
+  else out[s * out_stride + i] = acc;
+}
+
+// w[s] -= sum_{i < nv} h[s][i] V[s][i]
+__global__ void k_sub_basis(int n, int nv, const double* __restrict__ V, size_t vstride, size_t vslice,
+                            const double* __restrict__ h, int hstride, const uint8_t* __restrict__ active,
+                            double* __restrict__ w, size_t wstride) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  const double* Vs = V + s * vslice;
+  double acc = w[s * wstride + r];
+  for (int i = 0; i < nv; ++i) acc -= h[s * hstride + i] * Vs[i * vstride + r];
+  w[s * wstride + r] = acc;
+}
+
+// y[s] = x[s] * scale[s] (scale = 1 / norm), or y = a * x when inv = false.
+__global__ void k_scale(int n, const double* __restrict__ x, size_t xstride, const double* __restrict__ sc, int sstride,
+                        bool invert, const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  const double a = invert ? 1.0 / sc[s * sstride] : sc[s * sstride];
+  y[s * ystride + r] = a * x[s * xstride + r];
+}
+
+// x[s] += sum_{i < nv[s]} y[s][i] Z[s][i]
+__global__ void k_add_basis(int n, const int* __restrict__ nv, const double* __restrict__ Z, size_t zstride,
+                            size_t zslice, const double* __restrict__ y, int ystride,
+                            const uint8_t* __restrict__ active, double* __restrict__ x, size_t xstride) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  const double* Zs = Z + s * zslice;
+  double acc = x[s * xstride + r];
+  for (int i = 0; i < nv[s]; ++i) acc += y[s * ystride + i] * Zs[i * zstride + r];
+  x[s * xstride + r] = acc;
+}
+
+// Arnoldi step j of FGMRES for each active slice (one thread per slice):
+// store column j of the Hessenberg matrix, apply the previous Givens
+// rotations, form a new one and update the residual estimate |g[j+1]|.
+__global__ void k_givens(int S, int j, int m, const double* __restrict__ hcol, int hstride,
+                         const double* __restrict__ hnorm, const uint8_t* __restrict__ active,
+                         double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                         double* __restrict__ g, double* __restrict__ resid) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || !active[s]) return;
+  double* Hs = H + (size_t)s * (m + 1) * m;
+  for (int i = 0; i <= j; ++i) Hs[i * m + j] = hcol[s * hstride + i];
+  Hs[(j + 1) * m + j] = hnorm[s];
+  double* c = cs + (size_t)s * m;
+  double* sv = sn + (size_t)s * m;
+  for (int i = 0; i < j; ++i) {
+    const double a = Hs[i * m + j], b = Hs[(i + 1) * m + j];
+    Hs[i * m + j] = c[i] * a + sv[i] * b;
+    Hs[(i + 1) * m + j] = -sv[i] * a + c[i] * b;
+  }
+  const double a = Hs[j * m + j], b = Hs[(j + 1) * m + j];
+  const double r = hypot(a, b);
+  const double cj = (r > 0.0) ? a / r : 1.0, sj = (r > 0.0) ? b / r : 0.0;
+  c[j] = cj;
+  sv[j] = sj;
+  Hs[j * m + j] = r;
+  Hs[(j + 1) * m + j] = 0.0;
+  double* gs = g + (size_t)s * (m + 1);
+  gs[j + 1] = -sj * gs[j];
+  gs[j] = cj * gs[j];
+  resid[s] = fabs(gs[j + 1]);
+}
+
+// Solve the triangular system H y = g of size nv[s] (one thread per slice).
+__global__ void k_backsolve(int S, int m, const int* __restrict__ nv, const double* __restrict__ H,
+                            const double* __restrict__ g, const uint8_t* __restrict__ active, double* __restrict__ y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || !active[s]) return;
+  const int n = nv[s];
+  const double* Hs = H + (size_t)s * (m + 1) * m;
+  const double* gs = g + (size_t)s * (m + 1);
+  double* ys = y + (size_t)s * m;
+  for (int i = n - 1; i >= 0; --i) {
+    double acc = gs[i];
+    for (int k = i + 1; k < n; ++k) acc -= Hs[i * m + k] * ys[k];
+    ys[i] = acc / Hs[i * m + i];
+  }
+}
+
+// Start a restart cycle: g = (beta, 0, ...), V0 = r / beta.
+__global__ void k_init_g(int S, int m, const double* __restrict__ beta, const uint8_t* __restrict__ active,
+                         double* __restrict__ g) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || !active[s]) return;
+  double* gs = g + (size_t)s * (m + 1);
+  gs[0] = beta[s];
+  for (int i = 1; i <= m; ++i) gs[i] = 0.0;
+}
+
+// y = a x + b y, masked per slice.
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, size_t xstride, double b,
+                        const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  y[s * ystride + r] = a * x[s * xstride + r] + b * y[s * ystride + r];
+}
+
+__global__ void k_fill(int n, double v, const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || r >= n) return;
+  y[s * ystride + r] = v;
+}
+
+// Parareal correction U_next = F + (C_new - C_old) (this order, Sec. 3), with
+// per-field partial sums of the squared increment and of the new state.
+__global__ void __launch_bounds__(RED_THREADS) k_parareal_correct(int n, const double* __restrict__ Fv,
+                                                                  const double* __restrict__ Cnew,
+                                                                  const double* __restrict__ Cold,
+                                                                  double* __restrict__ Unext,
+                                                                  double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS / 32][6];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  double a[6] = {0, 0, 0, 0, 0, 0};   // |dv|^2, |du|^2, |dp|^2, |v|^2, |u|^2, |p|^2
+  for (int r = blockIdx.x * blockDim.x + tid; r < n; r += gridDim.x * blockDim.x) {
+    const double un = Fv[r] + (Cnew[r] - Cold[r]);
+    const double d = un - Unext[r];
+    const int c = r % 5;
+    const int f = c < 2 ? 0 : (c < 4 ? 1 : 2);
+    a[f] += d * d;
+    a[3 + f] += un * un;
+    Unext[r] = un;
+  }
+  for (int i = 0; i < 6; ++i) {
+    double v = a[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double v = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) v += red[w][tid];
+    partial[blockIdx.x * 6 + tid] = v;
+  }
+}

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of the C ABI in include/fsi.h (argument marshalling only).
+
+Every computation runs in the CUDA library libfsi.so; PyTorch only provides
+device memory and the current stream. Importing this module does not need a
+GPU; loading the library needs the compiled libfsi.so and raises if it is
+missing (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as wl
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libfsi.so")
+
+FSI_OK, FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ENEWTON, FSI_EGMRES, FSI_EJAC, FSI_ENAN, FSI_EDIVERGE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+
+
+class fsi_mesh(C.Structure):
+    _fields_ = [("n_xseg", C.c_int), ("x_breaks", C.POINTER(C.c_double)), ("nx_seg", C.POINTER(C.c_int)),
+                ("n_yseg", C.c_int), ("y_breaks", C.POINTER(C.c_double)), ("ny_seg", C.POINTER(C.c_int)),
+                ("has_solid", C.c_int), ("solid_x0", C.c_double), ("solid_x1", C.c_double),
+                ("solid_y0", C.c_double), ("solid_y1", C.c_double)]
+
+
+class fsi_params(C.Structure):
+    _fields_ = [("rho_f", C.c_double), ("nu_f", C.c_double), ("rho_s", C.c_double), ("mu_s", C.c_double),
+                ("lambda_s", C.c_double), ("vbar", C.c_double), ("ramp_t", C.c_double), ("theta0", C.c_double),
+                ("alpha0", C.c_double), ("T", C.c_double), ("n_slices", C.c_int), ("m_fine", C.c_int),
+                ("m_coarse", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
+                ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
+                ("mg_coarsest_max_dofs", C.c_int), ("mg_smooth", C.c_int), ("mg_omega", C.c_double),
+                ("max_batch", C.c_int)]
+
+
+class fsi_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_longlong), ("gmres_iters", C.c_longlong), ("max_newton", C.c_int),
+                ("max_gmres", C.c_int), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class fsi_parareal_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("increment_v", C.c_double), ("increment_u", C.c_double),
+                ("increment_p", C.c_double), ("fine_steps", C.c_longlong), ("coarse_steps", C.c_longlong),
+                ("fine", fsi_stats), ("coarse", fsi_stats)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("fine", "coarse")}
+        d["fine"] = self.fine.as_dict()
+        d["coarse"] = self.coarse.as_dict()
+        return d
+
+
+# name -> (restype, argtypes); the exported symbols of include/fsi.h
+_VP, _I, _D = C.c_void_p, C.c_int, C.c_double
+SIGNATURES = {
+    "fsi_setup": (_I, [C.POINTER(fsi_mesh), C.POINTER(fsi_params), C.POINTER(_VP)]),
+    "fsi_destroy": (None, [_VP]),
+    "fsi_last_error": (C.c_char_p, []),
+    "fsi_n_nodes": (_I, [_VP]),
+    "fsi_n_dofs": (_I, [_VP]),
+    "fsi_n_levels": (_I, [_VP]),
+    "fsi_nnzb": (_I, [_VP]),
+    "fsi_bsr_pattern": (_I, [_VP, C.POINTER(_I), C.POINTER(_I)]),
+    "fsi_residual": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
+    "fsi_jacobian": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
+    "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "fsi_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
+    "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
+    "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
+    "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfsi.so and declare its signatures; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FsiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fsi error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != FSI_OK:
+        raise FsiError(rc, load_library().fsi_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dbl(arr):
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Context:
+    """An fsi_ctx built for a workload (mesh from the break points, materials, solver parameters)."""
+
+    def __init__(self, workload: wl.Workload, max_batch: int = 1, **overrides):
+        lib = load_library()
+        w = workload
+        m = w.material
+        xb = (C.c_double * len(wl.X_BREAKS))(*wl.X_BREAKS)
+        yb = (C.c_double * len(wl.Y_BREAKS))(*wl.Y_BREAKS)
+        nxs = (C.c_int * len(w.nx_seg))(*w.nx_seg)
+        nys = (C.c_int * len(w.ny_seg))(*w.ny_seg)
+        (sx0, sx1), (sy0, sy1) = wl.SOLID_BOX
+        self._mesh = fsi_mesh(len(w.nx_seg), xb, nxs, len(w.ny_seg), yb, nys, int(w.with_solid), sx0, sx1, sy0, sy1)
+        self._keep = (xb, yb, nxs, nys)
+        p = dict(rho_f=m.rho_f, nu_f=m.nu_f, rho_s=m.rho_s, mu_s=m.mu_s, lambda_s=m.lambda_s, vbar=m.vbar,
+                 ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
+                 m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
+                 gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
+                 mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, max_batch=max_batch)
+        p.update(overrides)
+        self.params = p
+        self._params = fsi_params(**p)
+        h = C.c_void_p()
+        _check(lib.fsi_setup(C.byref(self._mesh), C.byref(self._params), C.byref(h)))
+        self.handle = h
+        self.lib = lib
+        self.workload = w
+        self.max_batch = max_batch
+        self.n_nodes = lib.fsi_n_nodes(h)
+        self.n_dofs = lib.fsi_n_dofs(h)
+        self.nnzb = lib.fsi_nnzb(h)
+        self.n_levels = lib.fsi_n_levels(h)
+
+    def close(self):
+        if self.handle:
+            self.lib.fsi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- step-level entry points ------------------------------------------
+    def fsi_residual(self, U, U_old, t_new, k, theta, R=None):
+        import torch
+        S = U.shape[0]
+        R = torch.empty_like(U) if R is None else R
+        t, tp = _dbl(t_new)
+        _check(self.lib.fsi_residual(self.handle, S, _ptr(U), _ptr(U_old), tp, k, theta, _ptr(R), _stream()))
+        return R
+
+    def fsi_jacobian(self, U, U_old, k, theta, vals=None):
+        import torch
+        S = U.shape[0]
+        vals = torch.empty((S, self.nnzb, 5, 5), dtype=torch.float64, device=U.device) if vals is None else vals
+        _check(self.lib.fsi_jacobian(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
+        return vals
+
+    def fsi_bsr_pattern(self):
+        rowptr = np.zeros(self.n_nodes + 1, dtype=np.int32)
+        colidx = np.zeros(self.nnzb, dtype=np.int32)
+        _check(self.lib.fsi_bsr_pattern(self.handle, rowptr.ctypes.data_as(C.POINTER(C.c_int)),
+                                        colidx.ctypes.data_as(C.POINTER(C.c_int))))
+        return rowptr, colidx
+
+    def fsi_bsr_spmv(self, vals, x, y=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(self.lib.fsi_bsr_spmv(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def fsi_theta_step(self, U_old, t_old, k, theta, U_new=None):
+        import torch
+        U_new = torch.empty_like(U_old) if U_new is None else U_new
+        st = fsi_stats()
+        t, tp = _dbl(t_old)
+        _check(self.lib.fsi_theta_step(self.handle, U_old.shape[0], _ptr(U_old), tp, k, theta, _ptr(U_new),
+                                       C.byref(st), _stream()))
+        return U_new, st.as_dict()
+
+    def fsi_fine(self, U0, t0, U1=None):
+        import torch
+        U1 = torch.empty_like(U0) if U1 is None else U1
+        st = fsi_stats()
+        t, tp = _dbl(t0)
+        _check(self.lib.fsi_fine(self.handle, U0.shape[0], _ptr(U0), tp, _ptr(U1), C.byref(st), _stream()))
+        return U1, st.as_dict()
+
+    def fsi_coarse(self, U0, t0, U1=None):
+        import torch
+        U1 = torch.empty_like(U0) if U1 is None else U1
+        st = fsi_stats()
+        t, tp = _dbl(t0)
+        _check(self.lib.fsi_coarse(self.handle, U0.shape[0], _ptr(U0), tp, _ptr(U1), C.byref(st), _stream()))
+        return U1, st.as_dict()
+
+    def parareal_iterate(self, U, max_iter, tol):
+        """U: device [n_slices + 1, n_dofs]; U[0] is the initial state. In place."""
+        st = fsi_parareal_stats()
+        _check(self.lib.parareal_iterate(self.handle, _ptr(U), max_iter, tol, C.byref(st), _stream()))
+        return U, st.as_dict()
+
+
+def fsi_setup(workload, max_batch=1, **overrides):
+    return Context(workload, max_batch, **overrides)

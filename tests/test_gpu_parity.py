@@ -1,0 +1,176 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the residual and the Jacobian are the same finite sums evaluated
+in a different order, so they agree to a few hundred ulps of the largest
+term (1e-12 relative to the largest entry). States after Newton solves agree
+to the 1e-10 relative accuracy the library targets (field by field: v, u, p).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fsi as of  # noqa: E402
+from oracle import parareal as opr  # noqa: E402
+from paper_1907_01252_gb300 import workloads as wl  # noqa: E402
+
+DEV = "cuda:0"
+FIELDS = {"v": slice(0, 2), "u": slice(2, 4), "p": slice(4, 5)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1907_01252_gb300 import build
+    build.build_library()
+
+
+def ctx_for(w, S, **kw):
+    from paper_1907_01252_gb300 import fsi
+    return fsi.Context(w, max_batch=S, **kw)
+
+
+def oracle_mesh(w):
+    return of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
+
+
+def to_dev(a):
+    return torch.tensor(np.asarray(a).reshape(a.shape[0], -1), dtype=torch.float64, device=DEV)
+
+
+def rel_field_errors(got, ref):
+    out = {}
+    for name, sl in FIELDS.items():
+        den = np.linalg.norm(ref[..., sl])
+        out[name] = np.linalg.norm(got[..., sl] - ref[..., sl]) / (den if den > 0 else 1.0)
+    return out
+
+
+# 16 x 4 is the small workload; 24 x 6 puts odd segment counts in the
+# multigrid hierarchy; 36 x 10 spans more cells than one reduction chunk.
+MESHES = [(16, 4), (24, 6), (36, 10)]
+
+
+@pytest.mark.parametrize("nx,ny", MESHES)
+def test_residual_matches_oracle(nx, ny):
+    w = wl.Workload(f"r{nx}", nx=nx, ny=ny, T=1.0, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    S = 3
+    U = np.stack([wl.random_state(mesh.n_nodes, 100 + s) for s in range(S)])
+    Uo = np.stack([wl.random_state(mesh.n_nodes, 200 + s) for s in range(S)])
+    t_new = [0.05, 0.13, 0.7]
+    k, th = 1e-2, 0.51
+    ctx = ctx_for(w, S)
+    R = ctx.fsi_residual(to_dev(U), to_dev(Uo), t_new, k, th).cpu().numpy().reshape(S, -1, 5)
+    for s in range(S):
+        prob = of.StepProblem(mesh, w.material, Uo[s], t_new[s], k, th)
+        ref = prob.residual(U[s])
+        assert np.abs(R[s] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nx,ny", MESHES[:2])
+def test_jacobian_matches_oracle(nx, ny):
+    w = wl.Workload(f"j{nx}", nx=nx, ny=ny, T=1.0, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    S = 2
+    U = np.stack([wl.random_state(mesh.n_nodes, 300 + s) for s in range(S)])
+    Uo = np.stack([wl.random_state(mesh.n_nodes, 400 + s) for s in range(S)])
+    k, th = 1e-2, 0.51
+    ctx = ctx_for(w, S)
+    vals = ctx.fsi_jacobian(to_dev(U), to_dev(Uo), k, th).cpu().numpy()
+    rowptr, colidx = ctx.fsi_bsr_pattern()
+    import scipy.sparse as sp
+    for s in range(S):
+        A = sp.bsr_matrix((vals[s], colidx, rowptr), shape=(mesh.n_dofs, mesh.n_dofs)).toarray()
+        prob = of.StepProblem(mesh, w.material, Uo[s], 0.3, k, th)
+        ref = prob.jacobian(U[s]).toarray()
+        assert np.abs(A - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_spmv_matches_oracle_matrix():
+    w = wl.Workload("spmv", nx=24, ny=6, T=1.0, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    S = 2
+    U = np.stack([wl.random_state(mesh.n_nodes, 500 + s) for s in range(S)])
+    x = np.stack([wl.random_state(mesh.n_nodes, 600 + s) for s in range(S)])
+    ctx = ctx_for(w, S)
+    vals = ctx.fsi_jacobian(to_dev(U), to_dev(U), 1e-2, 0.6)
+    y = ctx.fsi_bsr_spmv(vals, to_dev(x)).cpu().numpy()
+    for s in range(S):
+        A = of.StepProblem(mesh, w.material, U[s], 0.2, 1e-2, 0.6).jacobian(U[s])
+        ref = A @ x[s].ravel()
+        assert np.abs(y[s] - ref).max() <= 1e-12 * (abs(A) @ abs(x[s].ravel())).max()
+
+
+def developed_states(w, mesh, steps, k):
+    model = of.FSIModel(mesh, w.material)
+    U = np.zeros((mesh.n_nodes, 5))
+    out = []
+    for n in range(steps):
+        U = model.step(U, n * k, k, model.theta_fine(k))
+        out.append(U)
+    return model, out
+
+
+def test_theta_step_matches_oracle_and_batch_is_bitwise_serial():
+    w = wl.SMALL_16x4
+    mesh = oracle_mesh(w)
+    k = w.k_fine
+    model, states = developed_states(w, mesh, 12, k)
+    pick = [3, 7, 11]
+    U0 = np.stack([states[i] for i in pick])
+    t0 = [(i + 1) * k for i in pick]
+    th = 0.5 + k
+    ctx = ctx_for(w, 3)
+    Ub, stats = ctx.fsi_theta_step(to_dev(U0), t0, k, th)
+    got = Ub.cpu().numpy().reshape(3, -1, 5)
+    for s, i in enumerate(pick):
+        ref = model.step(U0[s], t0[s], k, th)
+        errs = rel_field_errors(got[s], ref)
+        assert max(errs.values()) <= 1e-10, errs
+        # the same slice alone gives the same bits
+        Us, _ = ctx.fsi_theta_step(to_dev(U0[s:s + 1]), [t0[s]], k, th)
+        assert torch.equal(Us[0], Ub[s])
+    assert stats["max_gmres"] < 200
+
+
+def test_fine_and_coarse_propagators_match_oracle():
+    w = wl.Workload("prop", nx=16, ny=4, T=0.5, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    dt = w.T / w.n_slices
+    model = of.FSIModel(mesh, w.material)
+    U0 = np.zeros((2, mesh.n_nodes, 5))
+    U0[1] = model.propagate(U0[0], 0.0, dt, 8)
+    ctx = ctx_for(w, 2)
+    Uf, _ = ctx.fsi_fine(to_dev(U0), [0.0, dt])
+    Uc, _ = ctx.fsi_coarse(to_dev(U0), [0.0, dt])
+    Uf = Uf.cpu().numpy().reshape(2, -1, 5)
+    Uc = Uc.cpu().numpy().reshape(2, -1, 5)
+    for s in range(2):
+        ref_f = model.propagate(U0[s], s * dt, (s + 1) * dt, w.m_fine)
+        ref_c = model.propagate(U0[s], s * dt, (s + 1) * dt, 1, theta=1.0)
+        assert max(rel_field_errors(Uf[s], ref_f).values()) <= 1e-10
+        assert max(rel_field_errors(Uc[s], ref_c).values()) <= 1e-10
+
+
+def test_parareal_matches_oracle_iterates_and_reaches_serial():
+    w = wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    model = of.FSIModel(mesh, w.material)
+    dt = w.T / w.n_slices
+    fine = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine)
+    coarse = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, 1, theta=1.0)
+    U0 = np.zeros((mesh.n_nodes, 5))
+    hist = opr.parareal(U0, w.n_slices, coarse, fine, 2)
+    ser = opr.serial(U0, w.n_slices, fine)
+    ctx = ctx_for(w, w.n_slices)
+    for iters, ref in ((2, hist[2]), (w.n_slices, ser)):
+        U = torch.zeros((w.n_slices + 1, mesh.n_dofs), dtype=torch.float64, device=DEV)
+        U, st = ctx.parareal_iterate(U, iters, 0.0)
+        got = U.cpu().numpy().reshape(w.n_slices + 1, -1, 5)
+        assert st["iterations"] == iters
+        for n in range(1, w.n_slices + 1):
+            errs = rel_field_errors(got[n], ref[n])
+            assert max(errs.values()) <= 1e-10, (iters, n, errs)
