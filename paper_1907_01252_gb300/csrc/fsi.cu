@@ -311,21 +311,12 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
 }
 
 int setup_transfer(Level& C, const Level& F) {
-  std::vector<int> pxi, pyi, rxi, ryi;
-  std::vector<double> pxw, pyw, rxw, ryw;
-  prolong_1d(C.h.xv, F.h.xn, pxi, pxw, rxi, rxw);
+  std::vector<int> pxi, pyi, rxi, ryi, ixi, iyi, d0;
+  std::vector<double> pxw, pyw, rxw, ryw, ixw, iyw, d1;
+  prolong_1d(C.h.xv, F.h.xn, pxi, pxw, rxi, rxw);   // coarse -> fine nodes and its transpose
   prolong_1d(C.h.yv, F.h.yn, pyi, pyw, ryi, ryw);
-  std::vector<int> inj(C.h.n_nodes);
-  for (int J = 0; J < C.h.nny; ++J)
-    for (int I = 0; I < C.h.nnx; ++I) {
-      int fi = -1, fj = -1;
-      for (int i = 0; i < F.h.nnx; ++i)
-        if (std::fabs(F.h.xn[i] - C.h.xn[I]) < 1e-12) { fi = i; break; }
-      for (int j = 0; j < F.h.nny; ++j)
-        if (std::fabs(F.h.yn[j] - C.h.yn[J]) < 1e-12) { fj = j; break; }
-      if (fi < 0 || fj < 0) return fail(FSI_EINVAL, "coarse node not on the fine grid");
-      inj[J * C.h.nnx + I] = fj * F.h.nnx + fi;
-    }
+  prolong_1d(F.h.xv, C.h.xn, ixi, ixw, d0, d1);     // fine field at the coarse nodes
+  prolong_1d(F.h.yv, C.h.yn, iyi, iyw, d0, d1);
   Transfer& T = C.T;
   T.nnx_f = F.h.nnx;
   T.nny_f = F.h.nny;
@@ -339,7 +330,10 @@ int setup_transfer(Level& C, const Level& F) {
   TRY(upload(C.owned, &T.rx_w, rxw));
   TRY(upload(C.owned, &T.ry_idx, ryi));
   TRY(upload(C.owned, &T.ry_w, ryw));
-  TRY(upload(C.owned, &T.inject, inj));
+  TRY(upload(C.owned, &T.ix_idx, ixi));
+  TRY(upload(C.owned, &T.ix_w, ixw));
+  TRY(upload(C.owned, &T.iy_idx, iyi));
+  TRY(upload(C.owned, &T.iy_w, iyw));
   return FSI_OK;
 }
 
@@ -456,8 +450,8 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
     Level& L = c->lev[l];
     if (l > 0) {
       const Level& F = c->lev[l - 1];
-      k_inject<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T.inject, L.h.n_nodes, Ul, F.n, L.n, act, L.U);
-      k_inject<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T.inject, L.h.n_nodes, Uol, F.n, L.n, act, L.Uold);
+      k_interp_state<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T, Ul, F.n, L.n, act, L.U);
+      k_interp_state<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T, Uol, F.n, L.n, act, L.Uold);
       Ul = L.U;
       Uol = L.Uold;
     }

@@ -506,7 +506,8 @@ struct Transfer {
   const int* py_idx;  const double* py_w;   // [nny_f][3]
   const int* rx_idx;  const double* rx_w;   // [nnx_c][7] fine index / weight (-1 pad)
   const int* ry_idx;  const double* ry_w;   // [nny_c][7]
-  const int* inject;                        // [n_nodes_c] fine node of each coarse node
+  const int* ix_idx;  const double* ix_w;   // [nnx_c][3] fine index / weight: fine field at coarse nodes
+  const int* iy_idx;  const double* iy_w;   // [nny_c][3]
 };
 
 __device__ inline bool is_free(uint8_t nf, int c) { return !is_identity_row(nf, c); }
@@ -563,12 +564,27 @@ __global__ void k_prolong_add(Transfer T, const uint8_t* __restrict__ nflags_f, 
   xf[s * stride_f + t] += acc;
 }
 
-__global__ void k_inject(const int* __restrict__ inject, int n_c, const double* __restrict__ Uf, size_t stride_f,
-                         size_t stride_c, const uint8_t* __restrict__ active, double* __restrict__ Uc) {
+// Coarse-level state: the fine Q2 field evaluated at the coarse nodes (the
+// coarsened meshes need not be nested when a segment has an odd cell count).
+__global__ void k_interp_state(Transfer T, const double* __restrict__ Uf, size_t stride_f, size_t stride_c,
+                               const uint8_t* __restrict__ active, double* __restrict__ Uc) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!active[s] || t >= n_c * 5) return;
-  Uc[s * stride_c + t] = Uf[s * stride_f + (size_t)inject[t / 5] * 5 + t % 5];
+  if (!active[s] || t >= T.nnx_c * T.nny_c * 5) return;
+  const int node = t / 5, c = t % 5;
+  const int I = node % T.nnx_c, J = node / T.nnx_c;
+  const double* u = Uf + s * stride_f;
+  double acc = 0.0;
+  for (int ey = 0; ey < 3; ++ey) {
+    const int j = T.iy_idx[J * 3 + ey];
+    if (j < 0) break;
+    for (int ex = 0; ex < 3; ++ex) {
+      const int i = T.ix_idx[I * 3 + ex];
+      if (i < 0) break;
+      acc += T.iy_w[J * 3 + ey] * T.ix_w[I * 3 + ex] * u[((size_t)j * T.nnx_f + i) * 5 + c];
+    }
+  }
+  Uc[s * stride_c + t] = acc;
 }
 
 // --------------------------------------------------------------------------
