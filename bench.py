@@ -1,0 +1,269 @@
+"""Benchmark: Parareal for monolithic ALE-FSI on the 128 x 32 Q2 channel-with-bar
+workload (83,525 dofs per state, T = 2, 64 slices x 32 fine shifted
+Crank-Nicolson steps, FP64 throughout).
+
+One step = one pass of the whole hot path: parareal_iterate with one
+iteration, i.e. the sequential coarse predictor sweep (64 implicit-Euler
+steps), the fine propagator of all 64 slices batched (32 steps of every
+slice at once: residual, Jacobian, multigrid-FGMRES Newton), the corrected
+coarse sweep and the Parareal correction. value = fine time-steps advanced
+per second (64 x 32 per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, one rank each): the path
+does not shard, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Parareal FSI time-steps/s, batched slices vs serial, at 1e-8 rel error"
+UNIT = "fine time-steps/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample():
+    """The FP64 oracle on the host: one fine shifted-CN step (k = 1/1024) of one
+    slice of the 128 x 32 workload from rest, in a single-threaded subprocess."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import fsi as of
+from paper_1907_01252_gb300 import workloads as wl
+w = wl.LARGE_128x32
+mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
+model = of.FSIModel(mesh, w.material, newton_tol=w.newton_tol)
+U = np.zeros((mesh.n_nodes, 5))
+k = w.k_fine
+t0 = time.perf_counter()
+U = model.step(U, 0.0, k, model.theta_fine(k))
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "newton": model.newton_counts}))
+""" % ROOT
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": 1.0 / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one fine theta step (k=1/1024, Newton to 1e-10, sparse LU) of one slice of the "
+                      "128x32 workload from rest, single thread; %.1f s" % r["seconds"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_sample()
+    vals = [cpu_oracle_sample() for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "oracle_sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1907_01252_gb300 import build, fsi, workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build_library()
+    w = wl.LARGE_128x32
+    N = w.n_slices
+    ctx = fsi.Context(w, max_batch=N)
+    n = ctx.n_dofs
+    U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        U[1:].zero_()
+        _, st = ctx.parareal_iterate(U, 1, 0.0)
+        return st
+
+    # warm-up; the last warm-up step also finds the dominant kernel
+    names = fsi.kernel_names()
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fsi.profile_enable(names)
+        st = step()
+    torch.cuda.synchronize()
+    shares = {nm: fsi.profile_read(nm)[0] for nm in names}
+    dominant = max(shares, key=shares.get)
+    total_ms = sum(shares.values())
+    fsi.profile_enable([dominant])
+
+    # timed region
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = fsi.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = fsi.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    dom_ms, dom_n, dom_flops = fsi.profile_read(dominant)
+    fsi.profile_enable([])
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = N * w.m_fine * args.steps * world
+    value = units / (ms / 1000.0)
+
+    # serial single-slice reference on the same GPU (a few fine steps of slice 1)
+    Us = U[1:2].clone()
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    nser = 4
+    t0 = w.T / N
+    cur = Us
+    for j in range(nser):
+        cur, _ = ctx.fsi_theta_step(cur, [t0 + j * w.k_fine], w.k_fine, 0.5 + w.material.theta0 * w.k_fine)
+    torch.cuda.synchronize()
+    serial_rate = nser / (time.perf_counter() - s0)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.zeros((1, n), dtype=torch.float64).pin_memory()
+        h_out = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            U[0:1].copy_(h_in, non_blocking=True)
+            U[1:].zero_()
+            ctx.parareal_iterate(U, 1, 0.0)
+            h_out.copy_(U, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        e2e = {"value": N * w.m_fine * args.steps / (ems / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": h_in.numel() * 8, "d2h_bytes_per_step": h_out.numel() * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+
+    achieved = dom_flops / (dom_ms / 1000.0) / 1e12 if dom_ms > 0 and dom_flops > 0 else None
+    roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": None, "share_of_kernel_time": shares[dominant] / total_ms if total_ms else None,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "n_dofs": n, "n_slices": N,
+                           "m_fine": w.m_fine, "m_coarse": w.m_coarse, "mg_levels": ctx.n_levels,
+                           "step": "parareal_iterate with 1 iteration: coarse predictor sweep + batched fine "
+                                   "sweep of all slices + corrected coarse sweep",
+                           "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
+                           "serial_gpu_fine_steps_per_s": serial_rate,
+                           "batched_vs_serial": value / serial_rate if serial_rate else None,
+                           "newton_fine": st["fine"], "newton_coarse": st["coarse"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -44,7 +44,7 @@ enum {
   FSI_EGMRES = -5,    /* FGMRES did not reach its tolerance within gmres_maxit */
   FSI_EJAC = -6,      /* singular local block (Vanka or coarsest solve) or J <= 0 */
   FSI_ENAN = -7,      /* non-finite residual */
-  FSI_EDIVERGE = -8   /* Parareal increment grew for three iterations in a row */
+  FSI_EDIVERGE = -8   /* Parareal increment is not finite */
 };
 
 /* Interface-fitted tensor-product mesh of the reference domain (Sec. 2.2:
@@ -163,6 +163,22 @@ int fsi_coarse(fsi_ctx* ctx, int S, const double* U0, const double* t0, double* 
  * serial fine solution). Errors: as fsi_theta_step, FSI_EDIVERGE. */
 int parareal_iterate(fsi_ctx* ctx, double* U, int max_iter, double tol,
                      fsi_parareal_stats* stats, void* stream);
+
+/* Measurement hooks (the paper has no counterpart; they serve benchmarking).
+ * Process-wide, for one host thread. Every kernel launch of the library is
+ * counted per kernel id (0 .. fsi_kernel_count()-1, names from
+ * fsi_kernel_name). fsi_profile_enable(mask) clears the timing records and
+ * brackets each later launch of the kernels whose id bit is set with two CUDA
+ * events on the launching stream; fsi_profile_read synchronises on those
+ * events and returns the summed duration, the number of timed launches and the
+ * algorithmic floating-point operations the library attributes to them.
+ * fsi_launch_count(-1) is the total over all kernels. */
+int fsi_profile_enable(unsigned long long kernel_mask);
+int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
+                     double* total_flops);   /* algorithmic FP64 flops of the timed launches (0 if not counted) */
+long long fsi_launch_count(int kernel_id);
+int fsi_kernel_count(void);
+const char* fsi_kernel_name(int kernel_id);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,15 @@ int fail(int code, const std::string& msg) {
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+int g_nact = 0;   // active slices of the current launch sequence (work accounting only)
+
+template <typename V>
+int count_active(const V& v) {
+  int n = 0;
+  for (auto a : v) n += a != 0;
+  return n;
+}
+
 // ---------------------------------------------------------------------------
 // Host mesh of one multigrid level.
 // ---------------------------------------------------------------------------
@@ -244,6 +253,7 @@ struct fsi_ctx {
   int *nv = nullptr, *status = nullptr;
   uint8_t *active = nullptr, *active2 = nullptr;
   double* t_dev = nullptr;
+  int n_act = 0;        // slices set in `active` (host mirror, for work accounting)
   // Parareal workspace
   double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
   int red_blocks = 0;
@@ -400,6 +410,91 @@ int upload_tables() {
   return FSI_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Launch accounting: every kernel launch of the library goes through LAUNCH,
+// which counts it and, when timing is enabled for its id, brackets it with
+// CUDA events on the launching stream (process-wide, one host thread).
+// ---------------------------------------------------------------------------
+enum KernelId {
+  KI_ADD_BASIS,
+  KI_APPLY_DIRICHLET,
+  KI_ASSEMBLE_BSR,
+  KI_AXPBY,
+  KI_BACKSOLVE,
+  KI_BSR_SPMV,
+  KI_CELL_JACOBIAN,
+  KI_CELL_RESIDUAL,
+  KI_DENSE_APPLY,
+  KI_DENSE_FROM_BSR,
+  KI_DENSE_INVERT,
+  KI_DOTS_FINISH,
+  KI_DOTS_PARTIAL,
+  KI_FILL,
+  KI_GATHER_RESIDUAL,
+  KI_GIVENS,
+  KI_INIT_G,
+  KI_INTERP_STATE,
+  KI_PARAREAL_CORRECT,
+  KI_PROLONG_ADD,
+  KI_RESTRICT,
+  KI_SCALE,
+  KI_SUB_BASIS,
+  KI_VANKA_CELL,
+  KI_VANKA_GATHER,
+  KI_VANKA_SETUP,
+  KI_COUNT
+};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup"};
+
+struct Profiler {
+  unsigned long long mask = 0;
+  long long launches[KI_COUNT] = {};
+  long long total = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> rec_id;
+  std::vector<double> rec_work;
+  double pending_work = 0.0;
+};
+Profiler g_prof;
+
+inline void prof_pre(int id, cudaStream_t st) {
+  g_prof.launches[id]++;
+  g_prof.total++;
+  if (!(g_prof.mask >> id & 1ull)) return;
+  if (g_prof.used + 2 > g_prof.pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      g_prof.pool.push_back(e);
+    }
+  }
+  cudaEventRecord(g_prof.pool[g_prof.used], st);
+}
+inline void prof_post(int id, cudaStream_t st) {
+  if (!(g_prof.mask >> id & 1ull)) return;
+  cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
+  g_prof.rec_id.push_back(id);
+  g_prof.rec_work.push_back(g_prof.pending_work);
+  g_prof.used += 2;
+}
+
+// LAUNCH_W also records the algorithmic FP64 flops of the launch.
+#define LAUNCH_W(work, id, kern, grid, block, smem, st, ...) \
+  do {                                                       \
+    g_prof.pending_work = (work);                            \
+    LAUNCH(id, kern, grid, block, smem, st, __VA_ARGS__);    \
+    g_prof.pending_work = 0.0;                               \
+  } while (0)
+
+#define LAUNCH(id, kern, grid, block, smem, st, ...) \
+  do {                                               \
+    prof_pre(id, st);                                \
+    kern<<<grid, block, smem, st>>>(__VA_ARGS__);    \
+    prof_post(id, st);                               \
+  } while (0)
+
 // ---------------------------------------------------------------------------
 // Batched building blocks
 // ---------------------------------------------------------------------------
@@ -411,23 +506,22 @@ int launch_check() {
 
 int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, double* R, cudaStream_t st) {
-  k_cell_residual<<<dim3(nblk(L.h.n_cells, 128), S), 128, 0, st>>>(L.dm, c->P, U, Uold, L.n, k, theta, act,
-                                                                     L.cellbuf);
-  k_gather_residual<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, c->P, L.cellbuf, U, L.n, c->t_dev, act, R);
+  LAUNCH(KI_CELL_RESIDUAL, k_cell_residual, (dim3(nblk(L.h.n_cells, 128), S)), 128, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, act, L.cellbuf);
+  LAUNCH(KI_GATHER_RESIDUAL, k_gather_residual, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, c->P, L.cellbuf, U, L.n, c->t_dev, act, R);
   return launch_check();
 }
 
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, double* A, cudaStream_t st) {
-  k_cell_jacobian<<<dim3(L.h.n_cells, S), JAC_THREADS, 0, st>>>(L.dm, c->P, U, Uold, L.n, k, theta, act, L.KV);
-  k_assemble_bsr<<<dim3(nblk((size_t)L.h.nnzb * 5, 128), S), 128, 0, st>>>(L.dm, L.KV, act, A);
+  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, act, L.KV);
+  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.KV, act, A);
   return launch_check();
 }
 
 template <bool RES>
 int spmv(Level& L, int S, const double* A, const double* x, const double* b, const uint8_t* act, double* y,
          cudaStream_t st) {
-  k_bsr_spmv<RES><<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.dm, A, x, b, L.n, act, y);
+  LAUNCH_W(50.0 * L.h.nnzb * (double)g_nact, KI_BSR_SPMV, k_bsr_spmv<RES>, (dim3(nblk(L.n, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y);
   return launch_check();
 }
 
@@ -435,8 +529,8 @@ int spmv(Level& L, int S, const double* A, const double* x, const double* b, con
 int dots(fsi_ctx* c, int S, size_t n, int nv, const double* V, size_t vstride, size_t vslice, const double* w,
          size_t wstride, const uint8_t* act, double* out, int ostride, bool take_sqrt, cudaStream_t st) {
   const int nb = (int)nblk(n, RED_CHUNK);
-  k_dots_partial<<<dim3(nb, S), RED_THREADS, 0, st>>>((int)n, nv, V, vstride, vslice, w, wstride, act, c->partial, 64);
-  k_dots_finish<<<S, 64, 0, st>>>(nb, nv, c->partial, 64, act, out, ostride, take_sqrt, false);
+  LAUNCH_W(2.0 * nv * (double)n * c->n_act, KI_DOTS_PARTIAL, k_dots_partial, (dim3(nb, S)), RED_THREADS, 0, st, (int)n, nv, V, vstride, vslice, w, wstride, act, c->partial, 64);
+  LAUNCH(KI_DOTS_FINISH, k_dots_finish, (S), 64, 0, st, nb, nv, c->partial, 64, act, out, ostride, take_sqrt, false);
   return launch_check();
 }
 
@@ -450,18 +544,18 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
     Level& L = c->lev[l];
     if (l > 0) {
       const Level& F = c->lev[l - 1];
-      k_interp_state<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T, Ul, F.n, L.n, act, L.U);
-      k_interp_state<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(L.T, Uol, F.n, L.n, act, L.Uold);
+      LAUNCH(KI_INTERP_STATE, k_interp_state, (dim3(nblk(L.n, 128), S)), 128, 0, st, L.T, Ul, F.n, L.n, act, L.U);
+      LAUNCH(KI_INTERP_STATE, k_interp_state, (dim3(nblk(L.n, 128), S)), 128, 0, st, L.T, Uol, F.n, L.n, act, L.Uold);
       Ul = L.U;
       Uol = L.Uold;
     }
     TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st));
     if (L.coarsest) {
       const int n = (int)L.n;
-      k_dense_from_bsr<<<dim3(nblk((size_t)n * n, 256), S), 256, 0, st>>>(L.dm, L.A, act, L.D);
-      k_dense_invert<<<S, GJ_THREADS, n * sizeof(double), st>>>(n, L.D, L.perm, act, L.Dinv, c->status);
+      LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, L.A, act, L.D);
+      LAUNCH(KI_DENSE_INVERT, k_dense_invert, (S), GJ_THREADS, n * sizeof(double), st, n, L.D, L.perm, act, L.Dinv, c->status);
     } else {
-      k_vanka_setup<<<dim3(L.h.n_cells, S), VK_THREADS, 0, st>>>(L.dm, L.A, act, L.KV, c->status);
+      LAUNCH_W(2.0 * 45 * 45 * 45 * L.h.n_cells * (double)c->n_act, KI_VANKA_SETUP, k_vanka_setup, (dim3(L.h.n_cells, S)), VK_THREADS, 0, st, L.dm, L.A, act, L.KV, c->status);
     }
     TRY(launch_check());
   }
@@ -472,29 +566,29 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
 int vcycle(fsi_ctx* c, int l, int S, const double* b, double* x, const uint8_t* act, cudaStream_t st) {
   Level& L = c->lev[l];
   if (L.coarsest) {
-    k_dense_apply<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>((int)L.n, L.Dinv, b, L.n, act, x);
+    LAUNCH(KI_DENSE_APPLY, k_dense_apply, (dim3(nblk(L.n, 128), S)), 128, 0, st, (int)L.n, L.Dinv, b, L.n, act, x);
     return launch_check();
   }
   const int nu = c->prm.mg_smooth;
   const double om = c->prm.mg_omega;
-  k_fill<<<dim3(nblk(L.n, 256), S), 256, 0, st>>>((int)L.n, 0.0, act, x, L.n);
+  LAUNCH(KI_FILL, k_fill, (dim3(nblk(L.n, 256), S)), 256, 0, st, (int)L.n, 0.0, act, x, L.n);
   auto smooth = [&](bool first) -> int {
     const double* r = b;
     if (!first) {
       TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
       r = L.r;
     }
-    k_vanka_cell<<<dim3(nblk((size_t)L.h.n_cells * 45, 128), S), 128, 0, st>>>(L.dm, L.KV, r, L.n, act, L.cellbuf);
-    k_vanka_gather<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, L.cellbuf, om, L.n, act, x);
+    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, L.KV, r, L.n, act, L.cellbuf);
+    LAUNCH(KI_VANKA_GATHER, k_vanka_gather, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, L.cellbuf, om, L.n, act, x);
     return launch_check();
   };
   for (int i = 0; i < nu; ++i) TRY(smooth(i == 0));
   Level& C = c->lev[l + 1];
   TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
-  k_restrict<<<dim3(nblk(C.n, 128), S), 128, 0, st>>>(C.T, L.dm.node_flags, C.dm.node_flags, L.r, L.n, C.n, act, C.b);
+  LAUNCH(KI_RESTRICT, k_restrict, (dim3(nblk(C.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, C.dm.node_flags, L.r, L.n, C.n, act, C.b);
   TRY(launch_check());
   TRY(vcycle(c, l + 1, S, C.b, C.x, act, st));
-  k_prolong_add<<<dim3(nblk(L.n, 128), S), 128, 0, st>>>(C.T, L.dm.node_flags, C.x, L.n, C.n, act, x);
+  LAUNCH(KI_PROLONG_ADD, k_prolong_add, (dim3(nblk(L.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, C.x, L.n, C.n, act, x);
   TRY(launch_check());
   for (int i = 0; i < nu; ++i) TRY(smooth(false));
   return FSI_OK;
@@ -512,7 +606,7 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
   std::vector<int> its(S, 0), nvh(S, 0);
   CK(cudaMemcpyAsync(act.data(), act_in, S, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(c->active, act_in, S, cudaMemcpyDeviceToDevice, st));
-  k_fill<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, 0.0, c->active, x, n);
+  LAUNCH(KI_FILL, k_fill, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 0.0, c->active, x, n);
   TRY(dots(c, S, n, 1, b, 0, n, b, n, c->active, c->scal, 1, true, st));
   CK(cudaMemcpyAsync(bnorm.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -527,6 +621,7 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
   bool first_cycle = true;
   while (any()) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    c->n_act = g_nact = count_active(act);
     // r = b - A x  (x = 0 in the first cycle)
     if (first_cycle) {
       CK(cudaMemcpy2DAsync(c->V, vsl * sizeof(double), b, n * sizeof(double), n * sizeof(double), S,
@@ -539,12 +634,13 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
     }
     first_cycle = false;
     TRY(dots(c, S, n, 1, c->V, 0, vsl, c->V, vsl, c->active, c->scal, 1, true, st));
-    k_init_g<<<nblk(S, 64), 64, 0, st>>>(S, m, c->scal, c->active, c->g);
-    k_scale<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->V, vsl, c->scal, 1, true, c->active, c->V, vsl);
+    LAUNCH(KI_INIT_G, k_init_g, (nblk(S, 64)), 64, 0, st, S, m, c->scal, c->active, c->g);
+    LAUNCH(KI_SCALE, k_scale, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->V, vsl, c->scal, 1, true, c->active, c->V, vsl);
     TRY(launch_check());
     std::vector<uint8_t> cyc = act;   // slices still inside this cycle
     for (int j = 0; j < m; ++j) {
       CK(cudaMemcpyAsync(c->active, cyc.data(), S, cudaMemcpyHostToDevice, st));
+      c->n_act = g_nact = count_active(cyc);
       double* Vj = c->V + (size_t)j * n;
       double* Zj = c->Z + (size_t)j * n;
       // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
@@ -557,13 +653,13 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
       TRY(spmv<false>(L, S, L.A, c->R, nullptr, c->active, c->w, st));
       // classical Gram-Schmidt, twice
       TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol, m + 1, false, st));
-      k_sub_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->hcol, m + 1, c->active, c->w, n);
+      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->hcol, m + 1, c->active, c->w, n);
       TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol2, m + 1, false, st));
-      k_sub_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->hcol2, m + 1, c->active, c->w, n);
-      k_axpby<<<dim3(1, S), 64, 0, st>>>(j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
+      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->hcol2, m + 1, c->active, c->w, n);
+      LAUNCH(KI_AXPBY, k_axpby, (dim3(1, S)), 64, 0, st, j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
       TRY(dots(c, S, n, 1, c->w, 0, n, c->w, n, c->active, c->scal, 1, true, st));
-      k_scale<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->w, n, c->scal, 1, true, c->active, c->V + (size_t)(j + 1) * n, vsl);
-      k_givens<<<nblk(S, 64), 64, 0, st>>>(S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
+      LAUNCH(KI_SCALE, k_scale, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->w, n, c->scal, 1, true, c->active, c->V + (size_t)(j + 1) * n, vsl);
+      LAUNCH(KI_GIVENS, k_givens, (nblk(S, 64)), 64, 0, st, S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
       TRY(launch_check());
       CK(cudaMemcpyAsync(res.data(), c->resid, S * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -591,8 +687,8 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
       if (any_fin) {
         CK(cudaMemcpyAsync(c->active2, fin.data(), S, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(c->nv, nvh.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_backsolve<<<nblk(S, 64), 64, 0, st>>>(S, m, c->nv, c->H, c->g, c->active2, c->y);
-        k_add_basis<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, c->nv, c->Z, n, zsl, c->y, m, c->active2, x, n);
+        LAUNCH(KI_BACKSOLVE, k_backsolve, (nblk(S, 64)), 64, 0, st, S, m, c->nv, c->H, c->g, c->active2, c->y);
+        LAUNCH(KI_ADD_BASIS, k_add_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->nv, c->Z, n, zsl, c->y, m, c->active2, x, n);
         TRY(launch_check());
       }
       if (!any_left) break;
@@ -621,14 +717,16 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
   std::vector<uint8_t> act(S, 1);
   std::vector<int> st_h(S, 0);
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
   CK(cudaMemcpyAsync(c->status, st_h.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  k_apply_dirichlet<<<dim3(nblk(L.h.n_nodes, 128), S), 128, 0, st>>>(L.dm, c->P, c->Uit, n, c->t_dev, c->active);
+  LAUNCH(KI_APPLY_DIRICHLET, k_apply_dirichlet, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, c->P, c->Uit, n, c->t_dev, c->active);
   TRY(launch_check());
   std::vector<double> r0(S, 0.0), nr(S);
   std::vector<int> nit(S, 0);
   int status = FSI_OK;
   for (int it = 0;; ++it) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    c->n_act = g_nact = count_active(act);
     TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
     TRY(dots(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
     CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -656,8 +754,9 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     }
     if (!any) break;
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    c->n_act = g_nact = count_active(act);
     // right-hand side -R
-    k_axpby<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
+    LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
     TRY(launch_check());
     TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st));
     // FGMRES needs R (rhs) and writes the correction; R is reused as scratch
@@ -674,7 +773,8 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed");
     if (rc == FSI_EGMRES) status = FSI_EGMRES;
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-    k_axpby<<<dim3(nblk(n, 256), S), 256, 0, st>>>((int)n, 1.0, c->lev[0].x, n, 1.0, c->active, c->Uit, n);
+    c->n_act = g_nact = count_active(act);
+    LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 1.0, c->lev[0].x, n, 1.0, c->active, c->Uit, n);
     TRY(launch_check());
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -836,6 +936,7 @@ int fsi_residual(fsi_ctx* c, int S, const double* U, const double* U_old, const 
   std::vector<uint8_t> act(S, 1);
   CK(cudaMemcpyAsync(c->t_dev, t_new, S * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
   TRY(residual(c, c->lev[0], S, U, U_old, k, theta, c->active, R, st));
   CK(cudaStreamSynchronize(st));
   return FSI_OK;
@@ -848,6 +949,7 @@ int fsi_jacobian(fsi_ctx* c, int S, const double* U, const double* U_old, double
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<uint8_t> act(S, 1);
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
   TRY(jacobian(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
   CK(cudaStreamSynchronize(st));
   return FSI_OK;
@@ -859,6 +961,7 @@ int fsi_bsr_spmv(fsi_ctx* c, int S, const double* vals, const double* x, double*
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<uint8_t> act(S, 1);
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
   TRY(spmv<false>(c->lev[0], S, vals, x, nullptr, c->active, y, st));
   return FSI_OK;
 }
@@ -930,9 +1033,8 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
         loc.coarse_steps += c->prm.m_coarse;
         Cn = c->Cnew;
       }
-      k_parareal_correct<<<c->red_blocks, RED_THREADS, 0, st>>>((int)n, c->Fv + (size_t)i * n, Cn,
-                                                                c->Cold + (size_t)i * n, U + (size_t)(i + 1) * n,
-                                                                c->ppart);
+      const int nrb = c->red_blocks;
+      LAUNCH(KI_PARAREAL_CORRECT, k_parareal_correct, (nrb), RED_THREADS, 0, st, (int)n, c->Fv + (size_t)i * n, Cn, c->Cold + (size_t)i * n, U + (size_t)(i + 1) * n, c->ppart);
       TRY(launch_check());
       if (i != first)
         CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -955,6 +1057,45 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
   }
   if (stats) *stats = loc;
   return FSI_OK;
+}
+
+int fsi_profile_enable(unsigned long long kernel_mask) {
+  g_prof.mask = kernel_mask;
+  g_prof.used = 0;
+  g_prof.rec_id.clear();
+  g_prof.rec_work.clear();
+  return FSI_OK;
+}
+
+int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches, double* total_flops) {
+  if (kernel_id < 0 || kernel_id >= KI_COUNT || !total_ms || !timed_launches || !total_flops)
+    return fail(FSI_EINVAL, "bad kernel id or null output");
+  double ms = 0.0, work = 0.0;
+  long long cnt = 0;
+  for (size_t r = 0; r < g_prof.rec_id.size(); ++r) {
+    if (g_prof.rec_id[r] != kernel_id) continue;
+    CK(cudaEventSynchronize(g_prof.pool[2 * r + 1]));
+    float e = 0.f;
+    CK(cudaEventElapsedTime(&e, g_prof.pool[2 * r], g_prof.pool[2 * r + 1]));
+    ms += e;
+    work += g_prof.rec_work[r];
+    ++cnt;
+  }
+  *total_ms = ms;
+  *timed_launches = cnt;
+  *total_flops = work;
+  return FSI_OK;
+}
+
+long long fsi_launch_count(int kernel_id) {
+  if (kernel_id < 0) return g_prof.total;
+  return kernel_id < KI_COUNT ? g_prof.launches[kernel_id] : -1;
+}
+
+int fsi_kernel_count(void) { return KI_COUNT; }
+
+const char* fsi_kernel_name(int kernel_id) {
+  return (kernel_id >= 0 && kernel_id < KI_COUNT) ? kKernelNames[kernel_id] : "";
 }
 
 }  // extern "C"

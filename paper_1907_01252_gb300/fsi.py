@@ -75,7 +75,40 @@ SIGNATURES = {
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+    "fsi_profile_enable": (_I, [C.c_ulonglong]),
+    "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
+    "fsi_launch_count": (C.c_longlong, [_I]),
+    "fsi_kernel_count": (_I, []),
+    "fsi_kernel_name": (C.c_char_p, [_I]),
 }
+
+
+def kernel_names():
+    lib = load_library()
+    return [lib.fsi_kernel_name(i).decode() for i in range(lib.fsi_kernel_count())]
+
+
+def profile_enable(names=()):
+    """Time every later launch of the named kernels with CUDA events."""
+    lib = load_library()
+    ids = kernel_names()
+    mask = 0
+    for n in names:
+        mask |= 1 << ids.index(n)
+    _check(lib.fsi_profile_enable(mask))
+
+
+def profile_read(name):
+    """(total milliseconds, timed launches, algorithmic flops) of a kernel since profile_enable."""
+    lib = load_library()
+    ms, cnt, fl = C.c_double(), C.c_longlong(), C.c_double()
+    _check(lib.fsi_profile_read(kernel_names().index(name), C.byref(ms), C.byref(cnt), C.byref(fl)))
+    return ms.value, cnt.value, fl.value
+
+
+def launch_count(name=None):
+    lib = load_library()
+    return lib.fsi_launch_count(-1 if name is None else kernel_names().index(name))
 
 _lib = None
 
