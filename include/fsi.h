@@ -82,6 +82,9 @@ typedef struct fsi_params {
   int mg_coarsest_max_dofs;/* coarsen the multigrid hierarchy until <= this */
   int mg_smooth;           /* Vanka sweeps before and after the coarse correction */
   double mg_omega;         /* Vanka damping */
+  int mg_reuse;            /* 1: build the multigrid hierarchy at the first Newton
+                              iteration of a step only (the Krylov operator is
+                              always the current exact Jacobian); 0: every iteration */
   int max_batch;           /* most slices advanced in one call */
 } fsi_params;
 

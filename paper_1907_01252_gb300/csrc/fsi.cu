@@ -228,7 +228,8 @@ struct Level {
   size_t n = 0;          // dofs
   std::vector<void*> owned;
   double *U = nullptr, *Uold = nullptr;       // injected states (level >= 1)
-  double *KV = nullptr;                       // element matrices, then Vanka inverses
+  double *KV = nullptr;                       // Vanka inverses (coarse levels: element matrices first)
+  double *Ke = nullptr;                       // level 0: element matrices (kept apart from KV)
   double *A = nullptr;                        // block-sparse values
   double *cellbuf = nullptr, *r = nullptr, *x = nullptr, *b = nullptr;
   double *D = nullptr, *Dinv = nullptr;       // coarsest only
@@ -307,6 +308,8 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
     TRY(dalloc(L.owned, &L.Uold, S * L.n));
   }
   TRY(dalloc(L.owned, &L.KV, (size_t)S * h.n_cells * 2025));
+  if (!need_state) TRY(dalloc(L.owned, &L.Ke, (size_t)S * h.n_cells * 2025));
+  else L.Ke = L.KV;
   TRY(dalloc(L.owned, &L.A, (size_t)S * h.nnzb * 25));
   TRY(dalloc(L.owned, &L.cellbuf, (size_t)S * h.n_cells * 45));
   TRY(dalloc(L.owned, &L.r, S * L.n));
@@ -513,8 +516,8 @@ int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
 
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, double* A, cudaStream_t st) {
-  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, act, L.KV);
-  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.KV, act, A);
+  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, act, L.Ke);
+  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A);
   return launch_check();
 }
 
@@ -758,7 +761,10 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     // right-hand side -R
     LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
     TRY(launch_check());
-    TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st));
+    if (it == 0 || !c->prm.mg_reuse)
+      TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st));
+    else  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
+      TRY(jacobian(c, L, S, c->Uit, c->Uold, k, theta, c->active, L.A, st));
     // FGMRES needs R (rhs) and writes the correction; R is reused as scratch
     // inside, so copy the rhs first.
     CK(cudaMemcpyAsync(c->lev[0].b, c->R, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));

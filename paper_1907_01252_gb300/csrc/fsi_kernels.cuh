@@ -238,6 +238,19 @@ __global__ void k_apply_dirichlet(DevMesh m, Phys P, double* __restrict__ U, siz
 // --------------------------------------------------------------------------
 constexpr int JAC_THREADS = 128;
 
+// Field blocks (test component ci, trial component cj) of the element
+// matrix that can be nonzero (the LPS pressure block is added separately).
+__device__ inline bool jac_block_nonzero(bool solid, int ci, int cj) {
+  if (!solid) {
+    if (ci < 2) return true;                 // momentum: v, u, p
+    if (ci < 4) return cj == ci;             // harmonic extension
+    return cj < 4;                           // divergence: v, u
+  }
+  if (ci < 2) return cj == ci || cj == 2 || cj == 3;   // mass, elastic stress
+  if (ci < 4) return cj == ci || cj == ci - 2;         // kinematic row
+  return false;
+}
+
 __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
                                                                const double* __restrict__ Uold, size_t stride,
                                                                double k, double theta,
@@ -309,31 +322,60 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     }
   }
   __syncthreads();
+  // Two-stage contraction, one quadrature point at a time:
+  //   E[(ci,a)][(j,cj)] = w_q sum_b D_q[(ci,a)][(cj,b)] B_b(j,q)
+  //   K[(i,ci)][(j,cj)] += sum_a B_a(i,q) E[(ci,a)][(j,cj)]
+  // Field blocks (ci, cj) that vanish for the cell's material are skipped.
+  __shared__ double sE[15][45];
+  __shared__ double sB[3][9];
+  constexpr int PER = (2025 + JAC_THREADS - 1) / JAC_THREADS;
+  double acc[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) acc[r] = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    const double wq = c_wq[q] * area;
+    if (tid < 9) {
+      sB[0][tid] = c_phi[q][tid];
+      sB[1][tid] = c_dps[q][tid] * ihx;
+      sB[2][tid] = c_dpt[q][tid] * ihy;
+    }
+    __syncthreads();
+    for (int e = tid; e < 15 * 45; e += JAC_THREADS) {
+      const int slot = e / 45, col = e % 45, j = col / 5, cj = col % 5;
+      const double* Dr = sD[q][slot] + cj * 3;
+      sE[slot][col] = wq * (Dr[0] * sB[0][j] + Dr[1] * sB[1][j] + Dr[2] * sB[2][j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int e = tid + r * JAC_THREADS;
+      if (e < 2025) {
+        const int row = e / 45, col = e % 45;
+        const int i = row / 5, ci = row % 5, cj = col % 5;
+        if (jac_block_nonzero(solid, ci, cj))
+          acc[r] += sB[0][i] * sE[ci * 3][col] + sB[1][i] * sE[ci * 3 + 1][col] + sB[2][i] * sE[ci * 3 + 2][col];
+      }
+    }
+    __syncthreads();
+  }
   double* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
-  for (int e = tid; e < 2025; e += JAC_THREADS) {
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = tid + r * JAC_THREADS;
+    if (e >= 2025) continue;
     const int row = e / 45, col = e % 45;
     const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
-    double acc = 0.0;
-    for (int q = 0; q < 9; ++q) {
-      const double Bi[3] = {c_phi[q][i], c_dps[q][i] * ihx, c_dpt[q][i] * ihy};
-      const double Bj[3] = {c_phi[q][j], c_dps[q][j] * ihx, c_dpt[q][j] * ihy};
-      double sum = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        const double* Drow = sD[q][ci * 3 + a] + cj * 3;
-        sum += Bi[a] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
-      }
-      acc += c_wq[q] * area * sum;
-    }
+    double v = acc[r];
     if (!solid && ci == 4 && cj == 4)
-      acc += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
+      v += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
     if (outflow && ci < 2 && cj < 4) {
       for (int q = 0; q < 3; ++q) {
         const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
         const double* Drow = sDe[q][ci] + cj * 3;
-        acc += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+        v += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
       }
     }
-    out[e] = acc;
+    out[e] = v;
   }
 }
 
@@ -402,61 +444,66 @@ __global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const dou
   const int cell = blockIdx.x;
   if (!active[s]) return;
   __shared__ double M[45][46];
-  __shared__ double I[45][46];
-  __shared__ int piv;
   __shared__ double colk[45];
+  __shared__ int perm[45];
+  __shared__ int piv;
+  __shared__ double pinv;
   const int tid = threadIdx.x;
   const double* As = A + (size_t)s * m.nnzb * 25;
   for (int e = tid; e < 2025; e += VK_THREADS) {
     const int r = e / 45, c = e % 45;
     const int blk = m.cell_blk[cell * 81 + (r / 5) * 9 + c / 5];
     M[r][c] = As[(size_t)blk * 25 + (r % 5) * 5 + c % 5];
-    I[r][c] = (r == c) ? 1.0 : 0.0;
   }
+  if (tid < 45) perm[tid] = tid;
   __syncthreads();
-  bool singular = false;
+  // in-place Gauss-Jordan with partial (row) pivoting
   for (int kk = 0; kk < 45; ++kk) {
-    if (tid == 0) {
-      int p = kk;
-      double best = fabs(M[kk][kk]);
-      for (int r = kk + 1; r < 45; ++r)
-        if (fabs(M[r][kk]) > best) { best = fabs(M[r][kk]); p = r; }
-      piv = (best > 0.0) ? p : -1;
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = kk;
+      for (int r = kk + tid; r < 45; r += 32) {
+        const double a = fabs(M[r][kk]);
+        if (a > best) { best = a; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        piv = (best > 0.0) ? bi : -1;
+        if (best > 0.0 && bi != kk) { const int t = perm[kk]; perm[kk] = perm[bi]; perm[bi] = t; }
+      }
     }
     __syncthreads();
     const int p = piv;
-    if (p < 0) { singular = true; break; }
-    if (p != kk) {
-      for (int c = tid; c < 45; c += VK_THREADS) {
-        double t0 = M[kk][c]; M[kk][c] = M[p][c]; M[p][c] = t0;
-        double t1 = I[kk][c]; I[kk][c] = I[p][c]; I[p][c] = t1;
-      }
+    if (p < 0) {
+      if (tid == 0) status[s] = -6;
+      return;
     }
+    if (p != kk)
+      for (int c = tid; c < 45; c += VK_THREADS) { const double t = M[kk][c]; M[kk][c] = M[p][c]; M[p][c] = t; }
     __syncthreads();
-    const double d = 1.0 / M[kk][kk];
+    if (tid == 0) pinv = 1.0 / M[kk][kk];
     __syncthreads();
-    for (int c = tid; c < 45; c += VK_THREADS) { M[kk][c] *= d; I[kk][c] *= d; }
-    __syncthreads();
-    for (int r = tid; r < 45; r += VK_THREADS) colk[r] = M[r][kk];
+    const double d = pinv;
+    for (int c = tid; c < 45; c += VK_THREADS) M[kk][c] = (c == kk) ? d : M[kk][c] * d;
+    for (int r = tid; r < 45; r += VK_THREADS) colk[r] = (r == kk) ? 0.0 : M[r][kk];
     __syncthreads();
     for (int e = tid; e < 2025; e += VK_THREADS) {
       const int r = e / 45, c = e % 45;
-      if (r != kk) {
-        const double f = colk[r];
-        M[r][c] -= f * M[kk][c];
-        I[r][c] -= f * I[kk][c];
-      }
+      if (r == kk) continue;
+      const double f = colk[r];
+      M[r][c] = (c == kk) ? -f * d : M[r][c] - f * M[kk][c];
     }
     __syncthreads();
   }
-  if (singular) {
-    if (tid == 0) status[s] = -6;
-    return;
-  }
+  // A^{-1}[r][perm[c]] = M[r][c]; stored transposed: inv[col][row]
   double* dst = inv + ((size_t)s * m.n_cells + cell) * 2025;
   for (int e = tid; e < 2025; e += VK_THREADS) {
-    const int c = e / 45, r = e % 45;
-    dst[e] = I[r][c];
+    const int r = e / 45, c = e % 45;
+    dst[perm[c] * 45 + r] = M[r][c];
   }
 }
 
@@ -701,7 +748,7 @@ __global__ void k_dense_apply(int n, const double* __restrict__ inv, const doubl
 // Vector kernels for FGMRES and Newton (per slice, fixed reduction order).
 // --------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
-constexpr int RED_CHUNK = 4096;   // rows per block: the partition depends on n only
+constexpr int RED_CHUNK = 1024;   // rows per block: the partition depends on n only
 
 // partial[s][blk][i] = sum over this block's rows of V[s][i][row] * w[s][row], i < nv.
 __global__ void __launch_bounds__(RED_THREADS) k_dots_partial(int n, int nv, const double* __restrict__ V,
