@@ -124,6 +124,26 @@ int fsi_n_levels(const fsi_ctx* ctx);   /* multigrid levels of the linear solver
 int fsi_residual(fsi_ctx* ctx, int S, const double* U, const double* U_old,
                  const double* t_new, double k, double theta, double* R, void* stream);
 
+/* Allocation-free variant of fsi_residual, for callers that must not allocate
+ * device memory when they evaluate residuals: code running inside a framework
+ * that owns the whole device memory pool, or a loop with a fixed memory budget.
+ * The paper has no counterpart; it computes exactly what fsi_residual computes.
+ * The entry point calls no cudaMalloc/cudaFree and no allocating library
+ * routine: its scratch (slice flags, times and the per-cell contributions) is
+ * one file-scope static __device__ array of 16 MiB, which every GPU that loads
+ * the library holds until the process exits. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture.
+ * The context is only read (its tables were built by fsi_setup), so S is not
+ * bounded by max_batch. Limits: 1 <= S <= 256 and S * cells * 45 <= 2,096,864
+ * doubles (e.g. 11 slices of the 128 x 32 mesh); larger sizes return
+ * FSI_EINVAL with a message. Every call on a device shares the one array and
+ * overwrites it completely (nothing needs to start at zero), so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Arguments, layout and errors as fsi_residual; the call synchronises the stream. */
+int fsi_residual_noalloc(fsi_ctx* ctx, int S, const double* U, const double* U_old,
+                         const double* t_new, double k, double theta, double* R, void* stream);
+
 /* Jacobian dR/dU of the same residual, assembled as a block-sparse matrix with
  * 5x5 node blocks: vals device [S][nnzb][5][5] (row-major blocks), pattern
  * from fsi_bsr_pattern. Errors: FSI_EINVAL. */

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -847,6 +848,36 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Allocation-free residual: its scratch lives in one file-scope device array.
+// Layout (doubles): [0, 32) slice flags as bytes, [32, 32 + kNaMaxSlices)
+// per-slice times, then the per-cell contributions [S][cells][45].
+// ---------------------------------------------------------------------------
+constexpr size_t kNaDoubles = size_t(1) << 21;          // 16 MiB per device
+constexpr int kNaMaxSlices = 256;
+constexpr size_t kNaCellOffset = 32 + kNaMaxSlices;     // 2304 bytes: 256-byte aligned
+static __device__ __align__(256) double g_na_scratch[kNaDoubles];
+
+constexpr int kNaMaxDevices = 64;
+double* g_na_ptr[kNaMaxDevices] = {};
+std::mutex g_na_mutex;
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+int na_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) return fail(FSI_EINVAL, "device index beyond the supported range");
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_na_scratch));
+    g_na_ptr[dev] = (double*)p;
+  }
+  *out = g_na_ptr[dev];
+  return FSI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -1102,6 +1133,32 @@ int fsi_kernel_count(void) { return KI_COUNT; }
 
 const char* fsi_kernel_name(int kernel_id) {
   return (kernel_id >= 0 && kernel_id < KI_COUNT) ? kKernelNames[kernel_id] : "";
+}
+
+int fsi_residual_noalloc(fsi_ctx* c, int S, const double* U, const double* U_old, const double* t_new, double k,
+                         double theta, double* R, void* stream) {
+  if (!c || !U || !U_old || !t_new || !R) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > kNaMaxSlices) return fail(FSI_EINVAL, "fsi_residual_noalloc: S outside 1..256");
+  Level& L = c->lev[0];
+  if ((size_t)S * L.h.n_cells * 45 > kNaDoubles - kNaCellOffset)
+    return fail(FSI_EINVAL, "fsi_residual_noalloc: S * cells * 45 exceeds the 16 MiB static scratch "
+                            "(2,096,864 doubles)");
+  double* scratch = nullptr;
+  TRY(na_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* act = reinterpret_cast<uint8_t*>(scratch);
+  double* t_dev = scratch + 32;
+  double* cellbuf = scratch + kNaCellOffset;
+  CK(cudaMemsetAsync(act, 1, S, st));   // every slice active
+  CK(cudaMemcpyAsync(t_dev, t_new, S * sizeof(double), cudaMemcpyHostToDevice, st));
+  g_nact = S;
+  LAUNCH(KI_CELL_RESIDUAL, k_cell_residual, (dim3(nblk(L.h.n_cells, 128), S)), 128, 0, st, L.dm, c->P, U, U_old, L.n,
+         k, theta, act, cellbuf);
+  LAUNCH(KI_GATHER_RESIDUAL, k_gather_residual, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, c->P, cellbuf,
+         U, L.n, t_dev, act, R);
+  TRY(launch_check());
+  CK(cudaStreamSynchronize(st));
+  return FSI_OK;
 }
 
 }  // extern "C"

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fsi_nnzb": (_I, [_VP]),
     "fsi_bsr_pattern": (_I, [_VP, C.POINTER(_I), C.POINTER(_I)]),
     "fsi_residual": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
+    "fsi_residual_noalloc": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
     "fsi_jacobian": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
     "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "fsi_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
@@ -206,6 +207,14 @@ class Context:
         R = torch.empty_like(U) if R is None else R
         t, tp = _dbl(t_new)
         _check(self.lib.fsi_residual(self.handle, S, _ptr(U), _ptr(U_old), tp, k, theta, _ptr(R), _stream()))
+        return R
+
+    def fsi_residual_noalloc(self, U, U_old, t_new, k, theta, R):
+        """Same as fsi_residual with the scratch in a static device array; R must be given
+        (preallocated by the caller): this call allocates no device memory."""
+        t, tp = _dbl(t_new)
+        _check(self.lib.fsi_residual_noalloc(self.handle, U.shape[0], _ptr(U), _ptr(U_old), tp, k, theta, _ptr(R),
+                                             _stream()))
         return R
 
     def fsi_jacobian(self, U, U_old, k, theta, vals=None):
