@@ -11,6 +11,11 @@ per second (64 x 32 per step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Profiling aids (not the benchmark line): --unit fine_step times one batched
+fine theta step of --slices slices of the same workload (the dominant part of
+a Parareal pass), and --kernel-table prints the per-kernel CUDA-event times of
+the last warm-up step to stderr.
+
 N > 1 runs N independent replicas (one per GPU, one rank each): the path
 does not shard, so there is no collective on the data path.
 """
@@ -41,6 +46,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step"])
+    ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
+    ap.add_argument("--kernel-table", action="store_true")
     return ap.parse_args()
 
 
@@ -157,15 +165,25 @@ def main():
     build.build_library()
     w = wl.LARGE_128x32
     N = w.n_slices
-    ctx = fsi.Context(w, max_batch=N)
+    fine_unit = args.unit == "fine_step"
+    ctx = fsi.Context(w, max_batch=args.slices if fine_unit else N)
     n = ctx.n_dofs
     U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        U[1:].zero_()
-        _, st = ctx.parareal_iterate(U, 1, 0.0)
-        return st
+    if fine_unit:
+        Uf = torch.zeros((args.slices, n), dtype=torch.float64, device=dev)
+        tf = [0.1 + 0.01 * s for s in range(args.slices)]
+        kf = w.k_fine
+
+        def step():
+            _, st = ctx.fsi_theta_step(Uf, tf, kf, 0.5 + w.material.theta0 * kf)
+            return {"fine": st, "coarse": {}}
+    else:
+        def step():
+            U[1:].zero_()
+            _, st = ctx.parareal_iterate(U, 1, 0.0)
+            return st
 
     # warm-up; the last warm-up step also finds the dominant kernel
     names = fsi.kernel_names()
@@ -177,6 +195,12 @@ def main():
     shares = {nm: fsi.profile_read(nm)[0] for nm in names}
     dominant = max(shares, key=shares.get)
     total_ms = sum(shares.values())
+    if args.kernel_table and rank == 0:
+        print("kernel event times of the last warm-up step (ms, share, launches):", file=sys.stderr)
+        for nm in sorted(shares, key=shares.get, reverse=True):
+            if shares[nm] > 0:
+                print("  %-20s %10.2f %6.2f%% %8d" % (nm, shares[nm], 100 * shares[nm] / total_ms,
+                                                   fsi.profile_read(nm)[1]), file=sys.stderr)
     fsi.profile_enable([dominant])
 
     # timed region
@@ -203,24 +227,25 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    units = N * w.m_fine * args.steps * world
+    per_step = args.slices if fine_unit else N * w.m_fine
+    units = per_step * args.steps * world
     value = units / (ms / 1000.0)
 
     # serial single-slice reference on the same GPU (a few fine steps of slice 1)
     Us = U[1:2].clone()
     torch.cuda.synchronize()
     s0 = time.perf_counter()
-    nser = 4
+    nser = 0 if fine_unit else 4
     t0 = w.T / N
     cur = Us
     for j in range(nser):
         cur, _ = ctx.fsi_theta_step(cur, [t0 + j * w.k_fine], w.k_fine, 0.5 + w.material.theta0 * w.k_fine)
     torch.cuda.synchronize()
-    serial_rate = nser / (time.perf_counter() - s0)
+    serial_rate = nser / (time.perf_counter() - s0) if nser else None
 
     # end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not fine_unit:
         h_in = torch.zeros((1, n), dtype=torch.float64).pin_memory()
         h_out = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
@@ -250,7 +275,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "n_dofs": n, "n_slices": N,
+                "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "unit": args.unit, "n_dofs": n, "n_slices": N,
                            "m_fine": w.m_fine, "m_coarse": w.m_coarse, "mg_levels": ctx.n_levels,
                            "step": "parareal_iterate with 1 iteration: coarse predictor sweep + batched fine "
                                    "sweep of all slices + corrected coarse sweep",

@@ -71,7 +71,7 @@ struct HostMesh {
   std::vector<double> cell_h;
   std::vector<uint8_t> cell_flags, node_flags;
   std::vector<double> node_y;
-  std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk;
+  std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk, spmv_rows;
 };
 
 std::vector<double> axis_vertices(const std::vector<double>& breaks, const std::vector<int>& counts) {
@@ -153,6 +153,11 @@ void build_mesh(HostMesh& m, bool has_solid, const double box[4]) {
     m.rowptr[n + 1] = (int)m.colidx.size();
   }
   m.nnzb = (int)m.colidx.size();
+  m.spmv_rows.resize(m.n_nodes);
+  for (int n = 0; n < m.n_nodes; ++n) m.spmv_rows[n] = n;
+  std::stable_sort(m.spmv_rows.begin(), m.spmv_rows.end(), [&](int a, int b) {
+    return m.rowptr[a + 1] - m.rowptr[a] > m.rowptr[b + 1] - m.rowptr[b];
+  });
   m.blk_src.assign((size_t)m.nnzb * 4, -1);
   m.cell_blk.assign(m.n_cells * 81, -1);
   std::vector<int> bcnt(m.nnzb, 0);
@@ -302,6 +307,7 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
   TRY(upload(L.owned, &d.blk_row, h.blk_row));
   TRY(upload(L.owned, &d.blk_src, h.blk_src));
   TRY(upload(L.owned, &d.cell_blk, h.cell_blk));
+  TRY(upload(L.owned, &d.spmv_rows, h.spmv_rows));
   L.n = (size_t)h.n_nodes * 5;
   L.coarsest = coarsest;
   if (need_state) {

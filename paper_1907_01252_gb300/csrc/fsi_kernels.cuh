@@ -42,6 +42,7 @@ struct DevMesh {
   const int* blk_row;       // [nnzb]
   const int* blk_src;       // [nnzb][4]: cell * 81 + li * 9 + lj, -1 pad
   const int* cell_blk;      // [n_cells][81]
+  const int* spmv_rows;     // [n_nodes] rows ordered by block count (uniform warps)
 };
 
 // Whether cell contribution of test component c enters the row of a node.
@@ -417,17 +418,23 @@ __global__ void k_bsr_spmv(DevMesh m, const double* __restrict__ A, const double
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= m.n_nodes * 5) return;
-  const int i = t / 5, c = t % 5;
-  const double* As = A + (size_t)s * m.nnzb * 25;
+  // rows visited in order of their block count so that a warp's rows have equal length
+  const int i = m.spmv_rows[t / 5], c = t % 5;
+  const double* As = A + (size_t)s * m.nnzb * 25 + c * 5;
   const double* xs = x + s * stride;
   double acc = 0.0;
-  for (int b = m.rowptr[i]; b < m.rowptr[i + 1]; ++b) {
-    const double* blk = As + (size_t)b * 25 + c * 5;
+  const int b1 = m.rowptr[i + 1];
+  for (int b = m.rowptr[i]; b < b1; ++b) {
+    const double* blk = As + (size_t)b * 25;
     const double* xj = xs + (size_t)m.colidx[b] * 5;
-    acc += blk[0] * xj[0] + blk[1] * xj[1] + blk[2] * xj[2] + blk[3] * xj[3] + blk[4] * xj[4];
+    acc = fma(blk[0], xj[0], acc);
+    acc = fma(blk[1], xj[1], acc);
+    acc = fma(blk[2], xj[2], acc);
+    acc = fma(blk[3], xj[3], acc);
+    acc = fma(blk[4], xj[4], acc);
   }
-  if (RESIDUAL) acc = bvec[s * stride + t] - acc;
-  y[s * stride + t] = acc;
+  const size_t o = s * stride + (size_t)i * 5 + c;
+  y[o] = RESIDUAL ? bvec[o] - acc : acc;
 }
 
 // --------------------------------------------------------------------------
