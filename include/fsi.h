@@ -82,6 +82,10 @@ typedef struct fsi_params {
   int mg_coarsest_max_dofs;/* coarsen the multigrid hierarchy until <= this */
   int mg_smooth;           /* Vanka sweeps before and after the coarse correction */
   double mg_omega;         /* Vanka damping */
+  double mg_coarse_lps;    /* preconditioner only: the stabilisation weight on
+                              multigrid level l is multiplied by mg_coarse_lps^l
+                              (rediscretised coarse levels otherwise carry far more
+                              pressure stabilisation than the fine operator) */
   int mg_reuse;            /* 1: build the multigrid hierarchy at the first Newton
                               iteration of a step only (the Krylov operator is
                               always the current exact Jacobian); 0: every iteration */

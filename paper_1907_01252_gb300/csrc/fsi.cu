@@ -521,9 +521,11 @@ int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
   return launch_check();
 }
 
+// lps_scale = 1 on the finest level (the discretisation); coarse levels of the
+// preconditioner scale the stabilisation weight down (see mg_coarse_lps).
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
-             const uint8_t* act, double* A, cudaStream_t st) {
-  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, act, L.Ke);
+             const uint8_t* act, double* A, cudaStream_t st, double lps_scale = 1.0) {
+  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, L.Ke);
   LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A);
   return launch_check();
 }
@@ -559,7 +561,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
       Ul = L.U;
       Uol = L.Uold;
     }
-    TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st));
+    TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st, std::pow(c->prm.mg_coarse_lps, l)));
     if (L.coarsest) {
       const int n = (int)L.n;
       LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, L.A, act, L.D);
@@ -846,7 +848,7 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
     return fail(FSI_EINVAL, "bad time or batch parameters");
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
     return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
-  if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5)
+  if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5 || !(p->mg_coarse_lps > 0))
     return fail(FSI_EINVAL, "bad multigrid parameters");
   return FSI_OK;
 }

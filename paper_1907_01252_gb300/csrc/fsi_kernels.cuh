@@ -254,7 +254,7 @@ __device__ inline bool jac_block_nonzero(bool solid, int ci, int cj) {
 
 __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
                                                                const double* __restrict__ Uold, size_t stride,
-                                                               double k, double theta,
+                                                               double k, double theta, double lps_scale,
                                                                const uint8_t* __restrict__ active,
                                                                double* __restrict__ Ke) {
   const int s = blockIdx.y;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     eval_qp(sU, sUo, tid, ihx, ihy, sq[tid]);
     derive(sq[tid], sd[tid]);
   }
-  if (tid == 32 && !solid) sAlpha = lps_weight(P, sUo, hx, hy);
+  if (tid == 32 && !solid) sAlpha = lps_scale * lps_weight(P, sUo, hx, hy);
   __syncthreads();
   for (int t = tid; t < 9 * 15; t += JAC_THREADS) {
     const int q = t / 15, dir = t % 15, cj = dir / 3, b = dir % 3;
