@@ -13,8 +13,9 @@ per second (64 x 32 per step).
 
 Profiling aids (not the benchmark line): --unit fine_step times one batched
 fine theta step of --slices slices of the same workload (the dominant part of
-a Parareal pass), and --kernel-table prints the per-kernel CUDA-event times of
-the last warm-up step to stderr.
+a Parareal pass), --unit coarse_step one single-slice coarse (theta = 1) step
+as in the sequential sweep, and --kernel-table prints the per-kernel
+CUDA-event times of the last warm-up step to stderr.
 
 N > 1 runs N independent replicas (one per GPU, one rank each): the path
 does not shard, so there is no collective on the data path.
@@ -46,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step"])
+    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step"])
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
     ap.add_argument("--kernel-table", action="store_true")
     return ap.parse_args()
@@ -165,7 +166,9 @@ def main():
     build.build_library()
     w = wl.LARGE_128x32
     N = w.n_slices
-    fine_unit = args.unit == "fine_step"
+    fine_unit = args.unit in ("fine_step", "coarse_step")
+    if args.unit == "coarse_step":
+        args.slices = 1
     ctx = fsi.Context(w, max_batch=args.slices if fine_unit else N)
     n = ctx.n_dofs
     U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
@@ -173,11 +176,12 @@ def main():
 
     if fine_unit:
         Uf = torch.zeros((args.slices, n), dtype=torch.float64, device=dev)
-        tf = [0.0] * args.slices      # first fine step of the trajectory, from rest
-        kf = w.k_fine
+        tf = [0.0] * args.slices      # first step of the trajectory, from rest
+        kf = w.k_fine if args.unit == "fine_step" else w.k_coarse
+        th = 0.5 + w.material.theta0 * kf if args.unit == "fine_step" else 1.0
 
         def step():
-            _, st = ctx.fsi_theta_step(Uf, tf, kf, 0.5 + w.material.theta0 * kf)
+            _, st = ctx.fsi_theta_step(Uf, tf, kf, th)
             return {"fine": st, "coarse": {}}
     else:
         def step():

@@ -86,9 +86,14 @@ typedef struct fsi_params {
                               multigrid level l is multiplied by mg_coarse_lps^l
                               (rediscretised coarse levels otherwise carry far more
                               pressure stabilisation than the fine operator) */
-  int mg_reuse;            /* 1: build the multigrid hierarchy at the first Newton
-                              iteration of a step only (the Krylov operator is
-                              always the current exact Jacobian); 0: every iteration */
+  int mg_reuse;            /* what the preconditioner keeps from the first Newton
+                              iteration of a step (the Krylov operator is always the
+                              current exact Jacobian): 0 nothing, 1 the coarsest-level
+                              inverse, 2 the whole multigrid hierarchy. Coarse steps
+                              use at most 1 (a stale hierarchy fails on large steps) */
+  int mg_rebuild_every;    /* fine propagator: rebuild the hierarchy at the first
+                              Newton iteration of every mg_rebuild_every-th step and
+                              keep it in between (>= 1; 1 = every step) */
   int max_batch;           /* most slices advanced in one call */
 } fsi_params;
 

@@ -548,7 +548,7 @@ int dots(fsi_ctx* c, int S, size_t n, int nv, const double* V, size_t vstride, s
 
 // Multigrid setup for the Newton iterate U (level 0) and old state Uold.
 int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
-             cudaStream_t st) {
+             cudaStream_t st, bool keep_coarsest = false) {
   const int NL = (int)c->lev.size();
   const double* Ul = U;
   const double* Uol = Uold;
@@ -563,6 +563,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
     }
     TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st, std::pow(c->prm.mg_coarse_lps, l)));
     if (L.coarsest) {
+      if (keep_coarsest) continue;   // inverse of an earlier Newton iteration of this step
       const int n = (int)L.n;
       LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, L.A, act, L.D);
       LAUNCH(KI_DENSE_INVERT, k_dense_invert, (S), GJ_THREADS, n * sizeof(double), st, n, L.D, L.perm, act, L.Dinv, c->status);
@@ -578,7 +579,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
 int vcycle(fsi_ctx* c, int l, int S, const double* b, double* x, const uint8_t* act, cudaStream_t st) {
   Level& L = c->lev[l];
   if (L.coarsest) {
-    LAUNCH(KI_DENSE_APPLY, k_dense_apply, (dim3(nblk(L.n, 128), S)), 128, 0, st, (int)L.n, L.Dinv, b, L.n, act, x);
+    LAUNCH(KI_DENSE_APPLY, k_dense_apply, (dim3(nblk(L.n * 32, 256), S)), 256, 0, st, (int)L.n, L.Dinv, b, L.n, act, x);
     return launch_check();
   }
   const int nu = c->prm.mg_smooth;
@@ -716,8 +717,11 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
 }
 
 // One theta step for S slices (Newton + FGMRES/multigrid).
+// reuse: what the preconditioner keeps across Newton iterations (see mg_reuse);
+// hierarchy_valid: the multigrid hierarchy of an earlier step of the same
+// propagator call may serve the first Newton iteration too.
 int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, double k, double theta, double* U_new,
-               fsi_stats* stats, cudaStream_t st) {
+               fsi_stats* stats, cudaStream_t st, int reuse, bool hierarchy_valid) {
   if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
   Level& L = c->lev[0];
   const size_t n = L.n;
@@ -770,10 +774,11 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     // right-hand side -R
     LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
     TRY(launch_check());
-    if (it == 0 || !c->prm.mg_reuse)
-      TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st));
-    else  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
+    const bool keep_all = (it == 0) ? hierarchy_valid : reuse >= 2;
+    if (keep_all)  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
       TRY(jacobian(c, L, S, c->Uit, c->Uold, k, theta, c->active, L.A, st));
+    else
+      TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st, it > 0 && reuse == 1));
     // FGMRES needs R (rhs) and writes the correction; R is reused as scratch
     // inside, so copy the rhs first.
     CK(cudaMemcpyAsync(c->lev[0].b, c->R, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -815,8 +820,12 @@ int propagate(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1,
   const double theta = fine ? 0.5 + c->prm.theta0 * k : 1.0;
   std::vector<double> t(t0, t0 + S);
   const double* src = U0;
+  const int every = std::max(1, c->prm.mg_rebuild_every);
   for (int j = 0; j < m; ++j) {
-    TRY(theta_step(c, S, src, t.data(), k, theta, U1, stats, st));
+    if (fine)
+      TRY(theta_step(c, S, src, t.data(), k, theta, U1, stats, st, c->prm.mg_reuse, j % every != 0));
+    else
+      TRY(theta_step(c, S, src, t.data(), k, theta, U1, stats, st, std::min(c->prm.mg_reuse, 1), false));
     for (double& x : t) x += k;
     src = U1;
   }
@@ -1015,7 +1024,7 @@ int fsi_theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, 
                    double* U_new, fsi_stats* stats, void* stream) {
   if (!c || !U_old || !t_old || !U_new) return fail(FSI_EINVAL, "null argument");
   if (stats) *stats = fsi_stats{};
-  int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream);
+  int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream, c->prm.mg_reuse, false);
   if (stats) stats->status = rc;
   return rc;
 }

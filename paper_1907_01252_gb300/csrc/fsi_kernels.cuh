@@ -730,25 +730,27 @@ __global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, double* __re
     }
     __syncthreads();
   }
-  // undo the row permutation on the columns: inv[:, pr[c]] = M[:, c]
+  // undo the row permutation on the columns: inv[:, pr[c]] = M[:, c] (row-major)
   double* out = inv + (size_t)s * n * n;
   for (int e = tid; e < n * n; e += GJ_THREADS) {
     const int r = e / n, c = e % n;
-    out[(size_t)pr[c] * n + r] = M[e];   // transposed storage: out[col][row]
+    out[(size_t)r * n + pr[c]] = M[e];
   }
 }
 
-// y = inv x with inv stored transposed: one thread per (slice, row).
+// y = inv x: one warp per (slice, row), lanes split the row.
 __global__ void k_dense_apply(int n, const double* __restrict__ inv, const double* __restrict__ x, size_t stride,
                               const uint8_t* __restrict__ active, double* __restrict__ y) {
   const int s = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
   if (!active[s] || r >= n) return;
-  const double* M = inv + (size_t)s * n * n;
+  const double* M = inv + (size_t)s * n * n + (size_t)r * n;
   const double* xs = x + s * stride;
   double acc = 0.0;
-  for (int c = 0; c < n; ++c) acc += M[(size_t)c * n + r] * xs[c];
-  y[s * stride + r] = acc;
+  for (int c = lane; c < n; c += 32) acc = fma(M[c], xs[c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[s * stride + r] = acc;
 }
 
 // --------------------------------------------------------------------------
