@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Parareal FSI time-steps/s, batched slices vs serial, at 1e-8 rel error"
 UNIT = "fine time-steps/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 x max SM clock
+# DRAM read + write bytes of one finest-level SpMV launch of 8 slices, from the ncu capture summarised in
+# profiles/fsi_spmv_128x32_ncu_full.md (451.4 MB); set to None when k_bsr_spmv changes.
+SPMV_TRAFFIC_8_SLICES = 451.4e6
 
 
 def parse():
@@ -275,7 +278,10 @@ def main():
     achieved = dom_flops / (dom_ms / 1000.0) / 1e12 if dom_ms > 0 and dom_flops > 0 else None
     roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": None, "share_of_kernel_time": shares[dominant] / total_ms if total_ms else None,
+                "traffic": (SPMV_TRAFFIC_8_SLICES * N / 8 if dominant == "k_bsr_spmv" and SPMV_TRAFFIC_8_SLICES
+                            else None),
+                "traffic_note": "DRAM bytes of one finest-level launch over the full batch, scaled from an 8-slice "
+                                "ncu capture (algorithmic 433 MB per 8 slices, ratio 1.04)", "share_of_kernel_time": shares[dominant] / total_ms if total_ms else None,
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -90,7 +90,8 @@ typedef struct fsi_params {
                               iteration of a step (the Krylov operator is always the
                               current exact Jacobian): 0 nothing, 1 the coarsest-level
                               inverse, 2 the whole multigrid hierarchy. Coarse steps
-                              use at most 1 (a stale hierarchy fails on large steps) */
+                              and fsi_theta_step use at most 1 (a stale hierarchy
+                              fails on large steps); the fine propagator uses it as is */
   int mg_rebuild_every;    /* fine propagator: rebuild the hierarchy at the first
                               Newton iteration of every mg_rebuild_every-th step and
                               keep it in between (>= 1; 1 = every step) */

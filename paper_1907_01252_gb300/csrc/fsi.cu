@@ -1024,7 +1024,9 @@ int fsi_theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, 
                    double* U_new, fsi_stats* stats, void* stream) {
   if (!c || !U_old || !t_old || !U_new) return fail(FSI_EINVAL, "null argument");
   if (stats) *stats = fsi_stats{};
-  int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream, c->prm.mg_reuse, false);
+  // a single step may be large: keep at most the coarsest inverse across Newton iterations
+  int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream, std::min(c->prm.mg_reuse, 1),
+                      false);
   if (stats) stats->status = rc;
   return rc;
 }

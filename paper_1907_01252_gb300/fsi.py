@@ -175,8 +175,8 @@ class Context:
                  ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
                  m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
                  gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
-                 mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_coarse_lps=0.25, mg_reuse=1,
-                 mg_rebuild_every=1, max_batch=max_batch)
+                 mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_coarse_lps=0.25, mg_reuse=2,
+                 mg_rebuild_every=4, max_batch=max_batch)
         p.update(overrides)
         self.params = p
         self._params = fsi_params(**p)
