@@ -95,6 +95,11 @@ typedef struct fsi_params {
   int mg_rebuild_every;    /* fine propagator: rebuild the hierarchy at the first
                               Newton iteration of every mg_rebuild_every-th step and
                               keep it in between (>= 1; 1 = every step) */
+  int precision;           /* 0: FP64 throughout. 1: the linear solver (FGMRES,
+                              multigrid, Vanka, block-sparse operator) in FP32 inside
+                              the FP64 Newton loop, whose residual, J = det F and the
+                              Parareal correction stay FP64 (the Newton iteration is
+                              the FP64 refinement; inner tolerance >= 1e-6) */
   int max_batch;           /* most slices advanced in one call */
 } fsi_params;
 

@@ -523,30 +523,34 @@ int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
 
 // lps_scale = 1 on the finest level (the discretisation); coarse levels of the
 // preconditioner scale the stabilisation weight down (see mg_coarse_lps).
+// The element matrices are FP64; the assembled values are stored in T.
+template <typename T>
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
-             const uint8_t* act, double* A, cudaStream_t st, double lps_scale = 1.0) {
+             const uint8_t* act, T* A, cudaStream_t st, double lps_scale = 1.0) {
   LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, L.Ke);
-  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A);
+  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<T>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A);
   return launch_check();
 }
 
-template <bool RES>
-int spmv(Level& L, int S, const double* A, const double* x, const double* b, const uint8_t* act, double* y,
-         cudaStream_t st) {
-  LAUNCH_W(50.0 * L.h.nnzb * (double)g_nact, KI_BSR_SPMV, k_bsr_spmv<RES>, (dim3(nblk(L.n, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y);
+template <typename T, bool RES>
+int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act, T* y, cudaStream_t st) {
+  LAUNCH_W(50.0 * L.h.nnzb * (double)g_nact, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk(L.n, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y);
   return launch_check();
 }
 
 // Norms or dot products with fixed reduction order: out[s*ostride + i] = V_i . w
-int dots(fsi_ctx* c, int S, size_t n, int nv, const double* V, size_t vstride, size_t vslice, const double* w,
+template <typename T>
+int dots(fsi_ctx* c, int S, size_t n, int nv, const T* V, size_t vstride, size_t vslice, const T* w,
          size_t wstride, const uint8_t* act, double* out, int ostride, bool take_sqrt, cudaStream_t st) {
   const int nb = (int)nblk(n, RED_CHUNK);
-  LAUNCH_W(2.0 * nv * (double)n * c->n_act, KI_DOTS_PARTIAL, k_dots_partial, (dim3(nb, S)), RED_THREADS, 0, st, (int)n, nv, V, vstride, vslice, w, wstride, act, c->partial, 64);
+  LAUNCH_W(2.0 * nv * (double)n * c->n_act, KI_DOTS_PARTIAL, k_dots_partial<T>, (dim3(nb, S)), RED_THREADS, 0, st, (int)n, nv, V, vstride, vslice, w, wstride, act, c->partial, 64);
   LAUNCH(KI_DOTS_FINISH, k_dots_finish, (S), 64, 0, st, nb, nv, c->partial, 64, act, out, ostride, take_sqrt, false);
   return launch_check();
 }
 
-// Multigrid setup for the Newton iterate U (level 0) and old state Uold.
+// Multigrid setup for the Newton iterate U (level 0) and old state Uold; the
+// preconditioner's matrices and inverses are stored in T.
+template <typename T>
 int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
              cudaStream_t st, bool keep_coarsest = false) {
   const int NL = (int)c->lev.size();
@@ -561,14 +565,16 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
       Ul = L.U;
       Uol = L.Uold;
     }
-    TRY(jacobian(c, L, S, Ul, Uol, k, theta, act, L.A, st, std::pow(c->prm.mg_coarse_lps, l)));
+    T* A = reinterpret_cast<T*>(L.A);
+    TRY(jacobian<T>(c, L, S, Ul, Uol, k, theta, act, A, st, std::pow(c->prm.mg_coarse_lps, l)));
     if (L.coarsest) {
       if (keep_coarsest) continue;   // inverse of an earlier Newton iteration of this step
       const int n = (int)L.n;
-      LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, L.A, act, L.D);
-      LAUNCH(KI_DENSE_INVERT, k_dense_invert, (S), GJ_THREADS, n * sizeof(double), st, n, L.D, L.perm, act, L.Dinv, c->status);
+      T* D = reinterpret_cast<T*>(L.D);
+      LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr<T>, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, A, act, D);
+      LAUNCH(KI_DENSE_INVERT, k_dense_invert<T>, (S), GJ_THREADS, n * sizeof(T), st, n, D, L.perm, act, reinterpret_cast<T*>(L.Dinv), c->status);
     } else {
-      LAUNCH_W(2.0 * 45 * 45 * 45 * L.h.n_cells * (double)c->n_act, KI_VANKA_SETUP, k_vanka_setup, (dim3(L.h.n_cells, S)), VK_THREADS, 0, st, L.dm, L.A, act, L.KV, c->status);
+      LAUNCH_W(2.0 * 45 * 45 * 45 * L.h.n_cells * (double)c->n_act, KI_VANKA_SETUP, k_vanka_setup<T>, (dim3(L.h.n_cells, S)), VK_THREADS, 0, st, L.dm, A, act, reinterpret_cast<T*>(L.KV), c->status);
     }
     TRY(launch_check());
   }
@@ -576,54 +582,68 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
 }
 
 // x = M_l^{-1} b : one V-cycle with Vanka smoothing, x is overwritten.
-int vcycle(fsi_ctx* c, int l, int S, const double* b, double* x, const uint8_t* act, cudaStream_t st) {
+template <typename T>
+int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaStream_t st) {
   Level& L = c->lev[l];
+  const T* A = reinterpret_cast<const T*>(L.A);
+  T* r = reinterpret_cast<T*>(L.r);
+  T* cellbuf = reinterpret_cast<T*>(L.cellbuf);
   if (L.coarsest) {
-    LAUNCH(KI_DENSE_APPLY, k_dense_apply, (dim3(nblk(L.n * 32, 256), S)), 256, 0, st, (int)L.n, L.Dinv, b, L.n, act, x);
+    LAUNCH(KI_DENSE_APPLY, k_dense_apply<T>, (dim3(nblk(L.n * 32, 256), S)), 256, 0, st, (int)L.n, reinterpret_cast<const T*>(L.Dinv), b, L.n, act, x);
     return launch_check();
   }
   const int nu = c->prm.mg_smooth;
   const double om = c->prm.mg_omega;
-  LAUNCH(KI_FILL, k_fill, (dim3(nblk(L.n, 256), S)), 256, 0, st, (int)L.n, 0.0, act, x, L.n);
+  LAUNCH(KI_FILL, k_fill<T>, (dim3(nblk(L.n, 256), S)), 256, 0, st, (int)L.n, 0.0, act, x, L.n);
   auto smooth = [&](bool first) -> int {
-    const double* r = b;
+    const T* rr = b;
     if (!first) {
-      TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
-      r = L.r;
+      TRY((spmv<T, true>(L, S, A, x, b, act, r, st)));
+      rr = r;
     }
-    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, L.KV, r, L.n, act, L.cellbuf);
-    LAUNCH(KI_VANKA_GATHER, k_vanka_gather, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, L.cellbuf, om, L.n, act, x);
+    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf);
+    LAUNCH(KI_VANKA_GATHER, k_vanka_gather<T>, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, cellbuf, om, L.n, act, x);
     return launch_check();
   };
   for (int i = 0; i < nu; ++i) TRY(smooth(i == 0));
   Level& C = c->lev[l + 1];
-  TRY(spmv<true>(L, S, L.A, x, b, act, L.r, st));
-  LAUNCH(KI_RESTRICT, k_restrict, (dim3(nblk(C.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, C.dm.node_flags, L.r, L.n, C.n, act, C.b);
+  T* Cb = reinterpret_cast<T*>(C.b);
+  T* Cx = reinterpret_cast<T*>(C.x);
+  TRY((spmv<T, true>(L, S, A, x, b, act, r, st)));
+  LAUNCH(KI_RESTRICT, k_restrict<T>, (dim3(nblk(C.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, C.dm.node_flags, r, L.n, C.n, act, Cb);
   TRY(launch_check());
-  TRY(vcycle(c, l + 1, S, C.b, C.x, act, st));
-  LAUNCH(KI_PROLONG_ADD, k_prolong_add, (dim3(nblk(L.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, C.x, L.n, C.n, act, x);
+  TRY(vcycle<T>(c, l + 1, S, Cb, Cx, act, st));
+  LAUNCH(KI_PROLONG_ADD, k_prolong_add<T>, (dim3(nblk(L.n, 128), S)), 128, 0, st, C.T, L.dm.node_flags, Cx, L.n, C.n, act, x);
   TRY(launch_check());
   for (int i = 0; i < nu; ++i) TRY(smooth(false));
   return FSI_OK;
 }
 
 // FGMRES(m) with multigrid right preconditioning: solve A x = b per active
-// slice to ||b - A x|| <= rtol ||b||. x is overwritten.
-int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in, fsi_stats* stats, cudaStream_t st) {
+// slice to ||b - A x|| <= rtol ||b||, vectors and operator in T (the
+// Hessenberg matrix and the rotations are kept in FP64). x is overwritten.
+template <typename T>
+int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rtol, fsi_stats* stats,
+           cudaStream_t st) {
   Level& L = c->lev[0];
   const size_t n = L.n;
   const int m = c->m;
   const size_t vsl = (size_t)(m + 1) * n, zsl = (size_t)m * n;
+  const T* A = reinterpret_cast<const T*>(L.A);
+  T* V = reinterpret_cast<T*>(c->V);
+  T* Z = reinterpret_cast<T*>(c->Z);
+  T* w = reinterpret_cast<T*>(c->w);
+  T* vin = reinterpret_cast<T*>(c->dU);
+  T* vout = reinterpret_cast<T*>(c->R);
   std::vector<uint8_t> act(S), act2(S);
   std::vector<double> bnorm(S), res(S);
   std::vector<int> its(S, 0), nvh(S, 0);
   CK(cudaMemcpyAsync(act.data(), act_in, S, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(c->active, act_in, S, cudaMemcpyDeviceToDevice, st));
-  LAUNCH(KI_FILL, k_fill, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 0.0, c->active, x, n);
-  TRY(dots(c, S, n, 1, b, 0, n, b, n, c->active, c->scal, 1, true, st));
+  LAUNCH(KI_FILL, k_fill<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 0.0, c->active, x, n);
+  TRY(dots<T>(c, S, n, 1, b, 0, n, b, n, c->active, c->scal, 1, true, st));
   CK(cudaMemcpyAsync(bnorm.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  const double rtol = c->prm.gmres_rtol;
   int status = FSI_OK;
   for (int s = 0; s < S; ++s)
     if (act[s] && !(bnorm[s] > 0.0)) {
@@ -637,41 +657,37 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
     c->n_act = g_nact = count_active(act);
     // r = b - A x  (x = 0 in the first cycle)
     if (first_cycle) {
-      CK(cudaMemcpy2DAsync(c->V, vsl * sizeof(double), b, n * sizeof(double), n * sizeof(double), S,
-                           cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpy2DAsync(V, vsl * sizeof(T), b, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
     } else {
       // V[s][0] = b - A x for active slices (strided output through w)
-      TRY(spmv<true>(L, S, L.A, x, b, c->active, c->w, st));
-      CK(cudaMemcpy2DAsync(c->V, vsl * sizeof(double), c->w, n * sizeof(double), n * sizeof(double), S,
-                           cudaMemcpyDeviceToDevice, st));
+      TRY((spmv<T, true>(L, S, A, x, b, c->active, w, st)));
+      CK(cudaMemcpy2DAsync(V, vsl * sizeof(T), w, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
     }
     first_cycle = false;
-    TRY(dots(c, S, n, 1, c->V, 0, vsl, c->V, vsl, c->active, c->scal, 1, true, st));
+    TRY(dots<T>(c, S, n, 1, V, 0, vsl, V, vsl, c->active, c->scal, 1, true, st));
     LAUNCH(KI_INIT_G, k_init_g, (nblk(S, 64)), 64, 0, st, S, m, c->scal, c->active, c->g);
-    LAUNCH(KI_SCALE, k_scale, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->V, vsl, c->scal, 1, true, c->active, c->V, vsl);
+    LAUNCH(KI_SCALE, k_scale<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, V, vsl, c->scal, 1, true, c->active, V, vsl);
     TRY(launch_check());
     std::vector<uint8_t> cyc = act;   // slices still inside this cycle
     for (int j = 0; j < m; ++j) {
       CK(cudaMemcpyAsync(c->active, cyc.data(), S, cudaMemcpyHostToDevice, st));
       c->n_act = g_nact = count_active(cyc);
-      double* Vj = c->V + (size_t)j * n;
-      double* Zj = c->Z + (size_t)j * n;
+      T* Vj = V + (size_t)j * n;
+      T* Zj = Z + (size_t)j * n;
       // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
-      CK(cudaMemcpy2DAsync(c->dU, n * sizeof(double), Vj, vsl * sizeof(double), n * sizeof(double), S,
-                           cudaMemcpyDeviceToDevice, st));
-      TRY(vcycle(c, 0, S, c->dU, c->R, c->active, st));
-      CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(double), c->R, n * sizeof(double), n * sizeof(double), S,
-                           cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpy2DAsync(vin, n * sizeof(T), Vj, vsl * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
+      TRY(vcycle<T>(c, 0, S, vin, vout, c->active, st));
+      CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(T), vout, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
       // w = A Z_j
-      TRY(spmv<false>(L, S, L.A, c->R, nullptr, c->active, c->w, st));
+      TRY((spmv<T, false>(L, S, A, vout, nullptr, c->active, w, st)));
       // classical Gram-Schmidt, twice
-      TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol, m + 1, false, st));
-      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->hcol, m + 1, c->active, c->w, n);
-      TRY(dots(c, S, n, j + 1, c->V, n, vsl, c->w, n, c->active, c->hcol2, m + 1, false, st));
-      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->hcol2, m + 1, c->active, c->w, n);
-      LAUNCH(KI_AXPBY, k_axpby, (dim3(1, S)), 64, 0, st, j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
-      TRY(dots(c, S, n, 1, c->w, 0, n, c->w, n, c->active, c->scal, 1, true, st));
-      LAUNCH(KI_SCALE, k_scale, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->w, n, c->scal, 1, true, c->active, c->V + (size_t)(j + 1) * n, vsl);
+      TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol, m + 1, false, st));
+      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, V, n, vsl, c->hcol, m + 1, c->active, w, n);
+      TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol2, m + 1, false, st));
+      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, V, n, vsl, c->hcol2, m + 1, c->active, w, n);
+      LAUNCH(KI_AXPBY, (k_axpby<double, double>), (dim3(1, S)), 64, 0, st, j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
+      TRY(dots<T>(c, S, n, 1, w, 0, n, w, n, c->active, c->scal, 1, true, st));
+      LAUNCH(KI_SCALE, k_scale<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, w, n, c->scal, 1, true, c->active, V + (size_t)(j + 1) * n, vsl);
       LAUNCH(KI_GIVENS, k_givens, (nblk(S, 64)), 64, 0, st, S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
       TRY(launch_check());
       CK(cudaMemcpyAsync(res.data(), c->resid, S * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -701,7 +717,7 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
         CK(cudaMemcpyAsync(c->active2, fin.data(), S, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(c->nv, nvh.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
         LAUNCH(KI_BACKSOLVE, k_backsolve, (nblk(S, 64)), 64, 0, st, S, m, c->nv, c->H, c->g, c->active2, c->y);
-        LAUNCH(KI_ADD_BASIS, k_add_basis, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->nv, c->Z, n, zsl, c->y, m, c->active2, x, n);
+        LAUNCH(KI_ADD_BASIS, k_add_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, c->nv, Z, n, zsl, c->y, m, c->active2, x, n);
         TRY(launch_check());
       }
       if (!any_left) break;
@@ -714,6 +730,31 @@ int fgmres(fsi_ctx* c, int S, const double* b, double* x, const uint8_t* act_in,
     }
   }
   return status;
+}
+
+// Newton correction for the active slices: build (or update) the
+// preconditioner and solve J delta = -R with the linear solver in T; the
+// result is added to the FP64 iterate.
+template <typename T>
+int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reuse, bool hierarchy_valid,
+                      double rtol, fsi_stats* stats, cudaStream_t st) {
+  Level& L = c->lev[0];
+  const size_t n = L.n;
+  T* b = reinterpret_cast<T*>(L.b);
+  T* x = reinterpret_cast<T*>(L.x);
+  const bool keep_all = (it == 0) ? hierarchy_valid : reuse >= 2;
+  if (keep_all)  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
+    TRY(jacobian<T>(c, L, S, c->Uit, c->Uold, k, theta, c->active, reinterpret_cast<T*>(L.A), st));
+  else
+    TRY(mg_setup<T>(c, S, c->Uit, c->Uold, k, theta, c->active, st, it > 0 && reuse == 1));
+  // right-hand side -R in T (R itself is scratch inside the solver)
+  LAUNCH(KI_AXPBY, (k_axpby<double, T>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, b, n);
+  TRY(launch_check());
+  const int rc = fgmres<T>(c, S, b, x, c->active, rtol, stats, st);
+  if (rc != FSI_OK && rc != FSI_EGMRES) return rc;
+  LAUNCH(KI_AXPBY, (k_axpby<T, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 1.0, x, n, 1.0, c->active, c->Uit, n);
+  TRY(launch_check());
+  return rc;
 }
 
 // One theta step for S slices (Newton + FGMRES/multigrid).
@@ -744,7 +785,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
     TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-    TRY(dots(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
+    TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
     CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     bool any = false;
@@ -771,18 +812,13 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     if (!any) break;
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
-    // right-hand side -R
-    LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->R, n);
-    TRY(launch_check());
-    const bool keep_all = (it == 0) ? hierarchy_valid : reuse >= 2;
-    if (keep_all)  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
-      TRY(jacobian(c, L, S, c->Uit, c->Uold, k, theta, c->active, L.A, st));
-    else
-      TRY(mg_setup(c, S, c->Uit, c->Uold, k, theta, c->active, st, it > 0 && reuse == 1));
-    // FGMRES needs R (rhs) and writes the correction; R is reused as scratch
-    // inside, so copy the rhs first.
-    CK(cudaMemcpyAsync(c->lev[0].b, c->R, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    int rc = fgmres(c, S, c->lev[0].b, c->lev[0].x, c->active, stats, st);
+    // FP64 throughout, or the FP32 linear solver inside the FP64 Newton loop
+    // (FP32 cannot reach FP64 tolerances: its relative tolerance is >= 1e-6)
+    const int rc = c->prm.precision == 1
+                       ? newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid,
+                                                  std::max(c->prm.gmres_rtol, 1e-6), stats, st)
+                       : newton_correction<double>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol,
+                                                   stats, st);
     CK(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int s = 0; s < S; ++s)
@@ -792,10 +828,6 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
       }
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed");
     if (rc == FSI_EGMRES) status = FSI_EGMRES;
-    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-    c->n_act = g_nact = count_active(act);
-    LAUNCH(KI_AXPBY, k_axpby, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 1.0, c->lev[0].x, n, 1.0, c->active, c->Uit, n);
-    TRY(launch_check());
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (stats) {
@@ -857,6 +889,7 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
     return fail(FSI_EINVAL, "bad time or batch parameters");
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
     return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
+  if (p->precision != 0 && p->precision != 1) return fail(FSI_EINVAL, "precision must be 0 (FP64) or 1 (FP32 solver)");
   if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5 || !(p->mg_coarse_lps > 0))
     return fail(FSI_EINVAL, "bad multigrid parameters");
   return FSI_OK;
@@ -1004,7 +1037,7 @@ int fsi_jacobian(fsi_ctx* c, int S, const double* U, const double* U_old, double
   std::vector<uint8_t> act(S, 1);
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
   c->n_act = g_nact = count_active(act);
-  TRY(jacobian(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
+  TRY(jacobian<double>(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
   CK(cudaStreamSynchronize(st));
   return FSI_OK;
 }
@@ -1016,7 +1049,7 @@ int fsi_bsr_spmv(fsi_ctx* c, int S, const double* vals, const double* x, double*
   std::vector<uint8_t> act(S, 1);
   CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
   c->n_act = g_nact = count_active(act);
-  TRY(spmv<false>(c->lev[0], S, vals, x, nullptr, c->active, y, st));
+  TRY((spmv<double, false>(c->lev[0], S, vals, x, nullptr, c->active, y, st)));
   return FSI_OK;
 }
 

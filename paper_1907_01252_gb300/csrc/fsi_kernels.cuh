@@ -382,8 +382,9 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
 
 // Block-sparse assembly: one thread per (slice, block, row component),
 // fixed-order sum over the cells sharing both nodes, identity rows replaced.
+template <typename T>
 __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const uint8_t* __restrict__ active,
-                               double* __restrict__ A) {
+                               T* __restrict__ A) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= m.nnzb * 5) return;
@@ -403,30 +404,30 @@ __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const u
       for (int cj = 0; cj < 5; ++cj) acc[cj] += src[cj];
     }
   }
-  double* dst = A + ((size_t)s * m.nnzb + b) * 25 + ci * 5;
-  for (int cj = 0; cj < 5; ++cj) dst[cj] = acc[cj];
+  T* dst = A + ((size_t)s * m.nnzb + b) * 25 + ci * 5;
+  for (int cj = 0; cj < 5; ++cj) dst[cj] = (T)acc[cj];
 }
 
 // --------------------------------------------------------------------------
 // Block-sparse matrix-vector product, y = A x or y = b - A x.
 // One thread per (slice, row dof).
 // --------------------------------------------------------------------------
-template <bool RESIDUAL>
-__global__ void k_bsr_spmv(DevMesh m, const double* __restrict__ A, const double* __restrict__ x,
-                           const double* __restrict__ bvec, size_t stride, const uint8_t* __restrict__ active,
-                           double* __restrict__ y) {
+template <typename T, bool RESIDUAL>
+__global__ void k_bsr_spmv(DevMesh m, const T* __restrict__ A, const T* __restrict__ x,
+                           const T* __restrict__ bvec, size_t stride, const uint8_t* __restrict__ active,
+                           T* __restrict__ y) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= m.n_nodes * 5) return;
   // rows visited in order of their block count so that a warp's rows have equal length
   const int i = m.spmv_rows[t / 5], c = t % 5;
-  const double* As = A + (size_t)s * m.nnzb * 25 + c * 5;
-  const double* xs = x + s * stride;
-  double acc = 0.0;
+  const T* As = A + (size_t)s * m.nnzb * 25 + c * 5;
+  const T* xs = x + s * stride;
+  T acc = 0;
   const int b1 = m.rowptr[i + 1];
   for (int b = m.rowptr[i]; b < b1; ++b) {
-    const double* blk = As + (size_t)b * 25;
-    const double* xj = xs + (size_t)m.colidx[b] * 5;
+    const T* blk = As + (size_t)b * 25;
+    const T* xj = xs + (size_t)m.colidx[b] * 5;
     acc = fma(blk[0], xj[0], acc);
     acc = fma(blk[1], xj[1], acc);
     acc = fma(blk[2], xj[2], acc);
@@ -444,19 +445,20 @@ __global__ void k_bsr_spmv(DevMesh m, const double* __restrict__ A, const double
 // --------------------------------------------------------------------------
 constexpr int VK_THREADS = 128;
 
-__global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const double* __restrict__ A,
+template <typename T>
+__global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const T* __restrict__ A,
                                                             const uint8_t* __restrict__ active,
-                                                            double* __restrict__ inv, int* __restrict__ status) {
+                                                            T* __restrict__ inv, int* __restrict__ status) {
   const int s = blockIdx.y;
   const int cell = blockIdx.x;
   if (!active[s]) return;
-  __shared__ double M[45][46];
-  __shared__ double colk[45];
+  __shared__ T M[45][46];
+  __shared__ T colk[45];
   __shared__ int perm[45];
   __shared__ int piv;
-  __shared__ double pinv;
+  __shared__ T pinv;
   const int tid = threadIdx.x;
-  const double* As = A + (size_t)s * m.nnzb * 25;
+  const T* As = A + (size_t)s * m.nnzb * 25;
   for (int e = tid; e < 2025; e += VK_THREADS) {
     const int r = e / 45, c = e % 45;
     const int blk = m.cell_blk[cell * 81 + (r / 5) * 9 + c / 5];
@@ -467,20 +469,20 @@ __global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const dou
   // in-place Gauss-Jordan with partial (row) pivoting
   for (int kk = 0; kk < 45; ++kk) {
     if (tid < 32) {
-      double best = -1.0;
+      T best = -1;
       int bi = kk;
       for (int r = kk + tid; r < 45; r += 32) {
-        const double a = fabs(M[r][kk]);
+        const T a = fabs(M[r][kk]);
         if (a > best) { best = a; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const T ob = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
-        piv = (best > 0.0) ? bi : -1;
-        if (best > 0.0 && bi != kk) { const int t = perm[kk]; perm[kk] = perm[bi]; perm[bi] = t; }
+        piv = (best > 0) ? bi : -1;
+        if (best > 0 && bi != kk) { const int t = perm[kk]; perm[kk] = perm[bi]; perm[bi] = t; }
       }
     }
     __syncthreads();
@@ -490,24 +492,24 @@ __global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const dou
       return;
     }
     if (p != kk)
-      for (int c = tid; c < 45; c += VK_THREADS) { const double t = M[kk][c]; M[kk][c] = M[p][c]; M[p][c] = t; }
+      for (int c = tid; c < 45; c += VK_THREADS) { const T t = M[kk][c]; M[kk][c] = M[p][c]; M[p][c] = t; }
     __syncthreads();
-    if (tid == 0) pinv = 1.0 / M[kk][kk];
+    if (tid == 0) pinv = T(1) / M[kk][kk];
     __syncthreads();
-    const double d = pinv;
+    const T d = pinv;
     for (int c = tid; c < 45; c += VK_THREADS) M[kk][c] = (c == kk) ? d : M[kk][c] * d;
-    for (int r = tid; r < 45; r += VK_THREADS) colk[r] = (r == kk) ? 0.0 : M[r][kk];
+    for (int r = tid; r < 45; r += VK_THREADS) colk[r] = (r == kk) ? T(0) : M[r][kk];
     __syncthreads();
     for (int e = tid; e < 2025; e += VK_THREADS) {
       const int r = e / 45, c = e % 45;
       if (r == kk) continue;
-      const double f = colk[r];
+      const T f = colk[r];
       M[r][c] = (c == kk) ? -f * d : M[r][c] - f * M[kk][c];
     }
     __syncthreads();
   }
   // A^{-1}[r][perm[c]] = M[r][c]; stored transposed: inv[col][row]
-  double* dst = inv + ((size_t)s * m.n_cells + cell) * 2025;
+  T* dst = inv + ((size_t)s * m.n_cells + cell) * 2025;
   for (int e = tid; e < 2025; e += VK_THREADS) {
     const int r = e / 45, c = e % 45;
     dst[perm[c] * 45 + r] = M[r][c];
@@ -515,39 +517,41 @@ __global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const dou
 }
 
 // z_cell = inv_cell * r_cell: one thread per (slice, cell, local row).
-__global__ void k_vanka_cell(DevMesh m, const double* __restrict__ inv, const double* __restrict__ r, size_t stride,
-                             const uint8_t* __restrict__ active, double* __restrict__ cellbuf) {
+template <typename T>
+__global__ void k_vanka_cell(DevMesh m, const T* __restrict__ inv, const T* __restrict__ r, size_t stride,
+                             const uint8_t* __restrict__ active, T* __restrict__ cellbuf) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= m.n_cells * 45) return;
   const int cell = t / 45, row = t % 45;
-  const double* Mi = inv + ((size_t)s * m.n_cells + cell) * 2025;
-  const double* rs = r + s * stride;
-  double acc = 0.0;
+  const T* Mi = inv + ((size_t)s * m.n_cells + cell) * 2025;
+  const T* rs = r + s * stride;
+  T acc = 0;
   for (int l = 0; l < 9; ++l) {
-    const double* rl = rs + (size_t)m.cell_nodes[cell * 9 + l] * 5;
+    const T* rl = rs + (size_t)m.cell_nodes[cell * 9 + l] * 5;
     for (int c = 0; c < 5; ++c) acc += Mi[(l * 5 + c) * 45 + row] * rl[c];
   }
   cellbuf[((size_t)s * m.n_cells + cell) * 45 + row] = acc;
 }
 
 // x += omega * (sum over the node's cells of z) / (number of cells).
-__global__ void k_vanka_gather(DevMesh m, const double* __restrict__ cellbuf, double omega, size_t stride,
-                               const uint8_t* __restrict__ active, double* __restrict__ x) {
+template <typename T>
+__global__ void k_vanka_gather(DevMesh m, const T* __restrict__ cellbuf, double omega, size_t stride,
+                               const uint8_t* __restrict__ active, T* __restrict__ x) {
   const int s = blockIdx.y;
   const int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || node >= m.n_nodes) return;
-  double acc[5] = {0, 0, 0, 0, 0};
+  T acc[5] = {0, 0, 0, 0, 0};
   int cnt = 0;
   for (int e = 0; e < 4; ++e) {
     const int code = m.node_cells[node * 4 + e];
     if (code < 0) break;
-    const double* src = cellbuf + ((size_t)s * m.n_cells + code / 9) * 45 + (code % 9) * 5;
+    const T* src = cellbuf + ((size_t)s * m.n_cells + code / 9) * 45 + (code % 9) * 5;
     for (int c = 0; c < 5; ++c) acc[c] += src[c];
     ++cnt;
   }
-  const double w = omega / cnt;
-  double* xs = x + s * stride + (size_t)node * 5;
+  const T w = T(omega / cnt);
+  T* xs = x + s * stride + (size_t)node * 5;
   for (int c = 0; c < 5; ++c) xs[c] += w * acc[c];
 }
 
@@ -566,36 +570,38 @@ struct Transfer {
 
 __device__ inline bool is_free(uint8_t nf, int c) { return !is_identity_row(nf, c); }
 
+template <typename V>
 __global__ void k_restrict(Transfer T, const uint8_t* __restrict__ nflags_f, const uint8_t* __restrict__ nflags_c,
-                           const double* __restrict__ rf, size_t stride_f, size_t stride_c,
-                           const uint8_t* __restrict__ active, double* __restrict__ rc) {
+                           const V* __restrict__ rf, size_t stride_f, size_t stride_c,
+                           const uint8_t* __restrict__ active, V* __restrict__ rc) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_c = T.nnx_c * T.nny_c;
   if (!active[s] || t >= n_c * 5) return;
   const int node = t / 5, c = t % 5;
   const int I = node % T.nnx_c, Jy = node / T.nnx_c;
-  double acc = 0.0;
+  V acc = 0;
   if (is_free(nflags_c[node], c)) {
-    const double* r = rf + s * stride_f;
+    const V* r = rf + s * stride_f;
     for (int ey = 0; ey < 7; ++ey) {
       const int j = T.ry_idx[Jy * 7 + ey];
       if (j < 0) break;
-      const double wy = T.ry_w[Jy * 7 + ey];
+      const V wy = (V)T.ry_w[Jy * 7 + ey];
       for (int ex = 0; ex < 7; ++ex) {
         const int i = T.rx_idx[I * 7 + ex];
         if (i < 0) break;
         const int fn = j * T.nnx_f + i;
-        if (is_free(nflags_f[fn], c)) acc += wy * T.rx_w[I * 7 + ex] * r[(size_t)fn * 5 + c];
+        if (is_free(nflags_f[fn], c)) acc += wy * (V)T.rx_w[I * 7 + ex] * r[(size_t)fn * 5 + c];
       }
     }
   }
   rc[s * stride_c + t] = acc;
 }
 
-__global__ void k_prolong_add(Transfer T, const uint8_t* __restrict__ nflags_f, const double* __restrict__ xc,
+template <typename V>
+__global__ void k_prolong_add(Transfer T, const uint8_t* __restrict__ nflags_f, const V* __restrict__ xc,
                               size_t stride_f, size_t stride_c, const uint8_t* __restrict__ active,
-                              double* __restrict__ xf) {
+                              V* __restrict__ xf) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_f = T.nnx_f * T.nny_f;
@@ -603,16 +609,16 @@ __global__ void k_prolong_add(Transfer T, const uint8_t* __restrict__ nflags_f, 
   const int node = t / 5, c = t % 5;
   if (!is_free(nflags_f[node], c)) return;
   const int i = node % T.nnx_f, j = node / T.nnx_f;
-  const double* x = xc + s * stride_c;
-  double acc = 0.0;
+  const V* x = xc + s * stride_c;
+  V acc = 0;
   for (int ey = 0; ey < 3; ++ey) {
     const int J = T.py_idx[j * 3 + ey];
     if (J < 0) break;
-    const double wy = T.py_w[j * 3 + ey];
+    const V wy = (V)T.py_w[j * 3 + ey];
     for (int ex = 0; ex < 3; ++ex) {
       const int I = T.px_idx[i * 3 + ex];
       if (I < 0) break;
-      acc += wy * T.px_w[i * 3 + ex] * x[((size_t)J * T.nnx_c + I) * 5 + c];
+      acc += wy * (V)T.px_w[i * 3 + ex] * x[((size_t)J * T.nnx_c + I) * 5 + c];
     }
   }
   xf[s * stride_f + t] += acc;
@@ -645,15 +651,16 @@ __global__ void k_interp_state(Transfer T, const double* __restrict__ Uf, size_t
 // Coarsest level: dense matrix, Gauss-Jordan inverse (one CTA per slice),
 // stored transposed, and its product.
 // --------------------------------------------------------------------------
-__global__ void k_dense_from_bsr(DevMesh m, const double* __restrict__ A, const uint8_t* __restrict__ active,
-                                 double* __restrict__ D) {
+template <typename T>
+__global__ void k_dense_from_bsr(DevMesh m, const T* __restrict__ A, const uint8_t* __restrict__ active,
+                                 T* __restrict__ D) {
   const int s = blockIdx.y;
   const int n = m.n_nodes * 5;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= n * n) return;
   const int r = t / n, c = t % n;
   const int i = r / 5, j = c / 5;
-  double v = 0.0;
+  T v = 0;
   for (int b = m.rowptr[i]; b < m.rowptr[i + 1]; ++b)
     if (m.colidx[b] == j) { v = A[((size_t)s * m.nnzb + b) * 25 + (r % 5) * 5 + c % 5]; break; }
   D[(size_t)s * n * n + t] = v;
@@ -663,41 +670,43 @@ constexpr int GJ_THREADS = 1024;
 
 // In-place Gauss-Jordan inversion with partial pivoting of D[s] (n x n,
 // row-major); the inverse is written transposed to inv[s].
-__global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, double* __restrict__ D, int* __restrict__ perm,
+template <typename T>
+__global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, T* __restrict__ D, int* __restrict__ perm,
                                                              const uint8_t* __restrict__ active,
-                                                             double* __restrict__ inv, int* __restrict__ status) {
+                                                             T* __restrict__ inv, int* __restrict__ status) {
   const int s = blockIdx.x;
   if (!active[s]) return;
-  double* M = D + (size_t)s * n * n;
+  T* M = D + (size_t)s * n * n;
   int* pr = perm + (size_t)s * n;
-  __shared__ double red_v[GJ_THREADS / 32];
+  __shared__ T red_v[GJ_THREADS / 32];
   __shared__ int red_i[GJ_THREADS / 32];
   __shared__ int piv;
-  __shared__ double pinv;
-  extern __shared__ double colk[];   // [n]
+  __shared__ T pinv;
+  extern __shared__ unsigned char colk_raw[];
+  T* colk = reinterpret_cast<T*>(colk_raw);   // [n]
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   for (int r = tid; r < n; r += GJ_THREADS) pr[r] = r;
   __syncthreads();
   for (int kk = 0; kk < n; ++kk) {
-    double best = -1.0;
+    T best = -1;
     int bi = kk;
     for (int r = kk + tid; r < n; r += GJ_THREADS) {
-      const double a = fabs(M[(size_t)r * n + kk]);
+      const T a = fabs(M[(size_t)r * n + kk]);
       if (a > best) { best = a; bi = r; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const T ob = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
-      double b = red_v[0];
+      T b = red_v[0];
       int ii = red_i[0];
       for (int w = 1; w < GJ_THREADS / 32; ++w)
         if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
-      piv = (b > 0.0) ? ii : -1;
+      piv = (b > 0) ? ii : -1;
     }
     __syncthreads();
     const int p = piv;
@@ -707,31 +716,31 @@ __global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, double* __re
     }
     if (p != kk) {
       for (int c = tid; c < n; c += GJ_THREADS) {
-        const double t0 = M[(size_t)kk * n + c];
+        const T t0 = M[(size_t)kk * n + c];
         M[(size_t)kk * n + c] = M[(size_t)p * n + c];
         M[(size_t)p * n + c] = t0;
       }
       if (tid == 0) { const int t1 = pr[kk]; pr[kk] = pr[p]; pr[p] = t1; }
     }
     __syncthreads();
-    if (tid == 0) pinv = 1.0 / M[(size_t)kk * n + kk];
+    if (tid == 0) pinv = T(1) / M[(size_t)kk * n + kk];
     __syncthreads();
-    const double d = pinv;
+    const T d = pinv;
     // in-place Gauss-Jordan: column kk becomes the kk-th column of the inverse
     for (int c = tid; c < n; c += GJ_THREADS) M[(size_t)kk * n + c] = (c == kk) ? d : M[(size_t)kk * n + c] * d;
-    for (int r = tid; r < n; r += GJ_THREADS) colk[r] = (r == kk) ? 0.0 : M[(size_t)r * n + kk];
+    for (int r = tid; r < n; r += GJ_THREADS) colk[r] = (r == kk) ? T(0) : M[(size_t)r * n + kk];
     __syncthreads();
     for (int e = tid; e < n * n; e += GJ_THREADS) {
       const int r = e / n, c = e % n;
       if (r == kk) continue;
-      const double f = colk[r];
+      const T f = colk[r];
       if (c == kk) M[e] = -f * d;
       else M[e] -= f * M[(size_t)kk * n + c];
     }
     __syncthreads();
   }
   // undo the row permutation on the columns: inv[:, pr[c]] = M[:, c] (row-major)
-  double* out = inv + (size_t)s * n * n;
+  T* out = inv + (size_t)s * n * n;
   for (int e = tid; e < n * n; e += GJ_THREADS) {
     const int r = e / n, c = e % n;
     out[(size_t)r * n + pr[c]] = M[e];
@@ -739,15 +748,16 @@ __global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, double* __re
 }
 
 // y = inv x: one warp per (slice, row), lanes split the row.
-__global__ void k_dense_apply(int n, const double* __restrict__ inv, const double* __restrict__ x, size_t stride,
-                              const uint8_t* __restrict__ active, double* __restrict__ y) {
+template <typename T>
+__global__ void k_dense_apply(int n, const T* __restrict__ inv, const T* __restrict__ x, size_t stride,
+                              const uint8_t* __restrict__ active, T* __restrict__ y) {
   const int s = blockIdx.y;
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
   if (!active[s] || r >= n) return;
-  const double* M = inv + (size_t)s * n * n + (size_t)r * n;
-  const double* xs = x + s * stride;
-  double acc = 0.0;
+  const T* M = inv + (size_t)s * n * n + (size_t)r * n;
+  const T* xs = x + s * stride;
+  T acc = 0;
   for (int c = lane; c < n; c += 32) acc = fma(M[c], xs[c], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) y[s * stride + r] = acc;
@@ -760,9 +770,10 @@ constexpr int RED_THREADS = 256;
 constexpr int RED_CHUNK = 1024;   // rows per block: the partition depends on n only
 
 // partial[s][blk][i] = sum over this block's rows of V[s][i][row] * w[s][row], i < nv.
-__global__ void __launch_bounds__(RED_THREADS) k_dots_partial(int n, int nv, const double* __restrict__ V,
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_dots_partial(int n, int nv, const T* __restrict__ V,
                                                               size_t vstride, size_t vslice,
-                                                              const double* __restrict__ w, size_t wstride,
+                                                              const T* __restrict__ w, size_t wstride,
                                                               const uint8_t* __restrict__ active,
                                                               double* __restrict__ partial, int max_nv) {
   const int s = blockIdx.y;
@@ -771,14 +782,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots_partial(int n, int nv, con
   const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int r0 = blockIdx.x * RED_CHUNK;
   const int r1 = min(n, r0 + RED_CHUNK);
-  const double* Vs = V + s * vslice;
-  const double* ws = w + s * wstride;
+  const T* Vs = V + s * vslice;
+  const T* ws = w + s * wstride;
   for (int i = 0; i < nv; ++i) {
-    double acc = 0.0;
-    const double* vi = Vs + i * vstride;
+    T acc = 0;
+    const T* vi = Vs + i * vstride;
     for (int r = r0 + tid; r < r1; r += RED_THREADS) acc += vi[r] * ws[r];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp][i] = acc;
+    if (lane == 0) red[warp][i] = (double)acc;
   }
   __syncthreads();
   for (int i = tid; i < nv; i += RED_THREADS) {
@@ -803,38 +814,41 @@ __global__ void k_dots_finish(int nblk, int nv, const double* __restrict__ parti
 }
 
 // w[s] -= sum_{i < nv} h[s][i] V[s][i]
-__global__ void k_sub_basis(int n, int nv, const double* __restrict__ V, size_t vstride, size_t vslice,
+template <typename T>
+__global__ void k_sub_basis(int n, int nv, const T* __restrict__ V, size_t vstride, size_t vslice,
                             const double* __restrict__ h, int hstride, const uint8_t* __restrict__ active,
-                            double* __restrict__ w, size_t wstride) {
+                            T* __restrict__ w, size_t wstride) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || r >= n) return;
-  const double* Vs = V + s * vslice;
-  double acc = w[s * wstride + r];
-  for (int i = 0; i < nv; ++i) acc -= h[s * hstride + i] * Vs[i * vstride + r];
+  const T* Vs = V + s * vslice;
+  T acc = w[s * wstride + r];
+  for (int i = 0; i < nv; ++i) acc -= (T)h[s * hstride + i] * Vs[i * vstride + r];
   w[s * wstride + r] = acc;
 }
 
 // y[s] = x[s] * scale[s] (scale = 1 / norm), or y = a * x when inv = false.
-__global__ void k_scale(int n, const double* __restrict__ x, size_t xstride, const double* __restrict__ sc, int sstride,
-                        bool invert, const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+template <typename T>
+__global__ void k_scale(int n, const T* __restrict__ x, size_t xstride, const double* __restrict__ sc, int sstride,
+                        bool invert, const uint8_t* __restrict__ active, T* __restrict__ y, size_t ystride) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || r >= n) return;
-  const double a = invert ? 1.0 / sc[s * sstride] : sc[s * sstride];
+  const T a = (T)(invert ? 1.0 / sc[s * sstride] : sc[s * sstride]);
   y[s * ystride + r] = a * x[s * xstride + r];
 }
 
 // x[s] += sum_{i < nv[s]} y[s][i] Z[s][i]
-__global__ void k_add_basis(int n, const int* __restrict__ nv, const double* __restrict__ Z, size_t zstride,
+template <typename T>
+__global__ void k_add_basis(int n, const int* __restrict__ nv, const T* __restrict__ Z, size_t zstride,
                             size_t zslice, const double* __restrict__ y, int ystride,
-                            const uint8_t* __restrict__ active, double* __restrict__ x, size_t xstride) {
+                            const uint8_t* __restrict__ active, T* __restrict__ x, size_t xstride) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || r >= n) return;
-  const double* Zs = Z + s * zslice;
-  double acc = x[s * xstride + r];
-  for (int i = 0; i < nv[s]; ++i) acc += y[s * ystride + i] * Zs[i * zstride + r];
+  const T* Zs = Z + s * zslice;
+  T acc = x[s * xstride + r];
+  for (int i = 0; i < nv[s]; ++i) acc += (T)y[s * ystride + i] * Zs[i * zstride + r];
   x[s * xstride + r] = acc;
 }
 
@@ -897,19 +911,22 @@ __global__ void k_init_g(int S, int m, const double* __restrict__ beta, const ui
 }
 
 // y = a x + b y, masked per slice.
-__global__ void k_axpby(int n, double a, const double* __restrict__ x, size_t xstride, double b,
-                        const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+template <typename TX, typename TY>
+__global__ void k_axpby(int n, double a, const TX* __restrict__ x, size_t xstride, double b,
+                        const uint8_t* __restrict__ active, TY* __restrict__ y, size_t ystride) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || r >= n) return;
-  y[s * ystride + r] = a * x[s * xstride + r] + b * y[s * ystride + r];
+  if (b == 0.0) y[s * ystride + r] = (TY)(a * (double)x[s * xstride + r]);
+  else y[s * ystride + r] = (TY)(a * (double)x[s * xstride + r] + b * (double)y[s * ystride + r]);
 }
 
-__global__ void k_fill(int n, double v, const uint8_t* __restrict__ active, double* __restrict__ y, size_t ystride) {
+template <typename T>
+__global__ void k_fill(int n, double v, const uint8_t* __restrict__ active, T* __restrict__ y, size_t ystride) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || r >= n) return;
-  y[s * ystride + r] = v;
+  y[s * ystride + r] = (T)v;
 }
 
 // Parareal correction U_next = F + (C_new - C_old) (this order, Sec. 3), with
