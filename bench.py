@@ -104,6 +104,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms_local, units_per_rank, dist=None, device=None):
+    """Whole-job rate of independent replicas: the time is the maximum over
+    ranks, the work the sum over ranks (every rank does units_per_rank)."""
+    import torch
+    world = 1
+    ms = ms_local
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world / (ms / 1000.0)
+
+
 def cpu_oracle_sample():
     """The FP64 oracle on the host: one fine shifted-CN step (k = 1/1024) of one
     slice of the 128 x 32 workload from rest, in a single-threaded subprocess."""
@@ -232,13 +246,8 @@ def main():
     clk = clocks.stop()
     dom_ms, dom_n, dom_flops = fsi.profile_read(dominant)
     fsi.profile_enable([])
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     per_step = args.slices if fine_unit else N * w.m_fine
-    units = per_step * args.steps * world
-    value = units / (ms / 1000.0)
+    ms, value = aggregate(ms, per_step * args.steps, dist, dev)
 
     # serial single-slice reference on the same GPU (a few fine steps of slice 1)
     Us = U[1:2].clone()
