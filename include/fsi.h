@@ -82,6 +82,10 @@ typedef struct fsi_params {
   int mg_coarsest_max_dofs;/* coarsen the multigrid hierarchy until <= this */
   int mg_smooth;           /* Vanka sweeps before and after the coarse correction */
   double mg_omega;         /* Vanka damping */
+  int mg_smoother;         /* 0: additive Vanka (all cells at once, corrections
+                              averaged over the cells of a node); 1: multiplicative,
+                              four colours of cells that share no node, one after
+                              the other with the residual updated in between */
   double mg_coarse_lps;    /* preconditioner only: the stabilisation weight on
                               multigrid level l is multiplied by mg_coarse_lps^l
                               (rediscretised coarse levels otherwise carry far more

@@ -72,6 +72,9 @@ struct HostMesh {
   std::vector<uint8_t> cell_flags, node_flags;
   std::vector<double> node_y;
   std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk, spmv_rows;
+  // multiplicative smoother: colour (cx%2 + 2 cy%2) -> its cells, its nodes and
+  // the (cell, local node) each of those nodes belongs to
+  std::vector<int> col_cells[4], col_nodes[4], col_src[4];
 };
 
 std::vector<double> axis_vertices(const std::vector<double>& breaks, const std::vector<int>& counts) {
@@ -153,6 +156,20 @@ void build_mesh(HostMesh& m, bool has_solid, const double box[4]) {
     m.rowptr[n + 1] = (int)m.colidx.size();
   }
   m.nnzb = (int)m.colidx.size();
+  for (int k = 0; k < 4; ++k) {
+    m.col_cells[k].clear();
+    m.col_nodes[k].clear();
+    m.col_src[k].clear();
+  }
+  for (int cy = 0; cy < m.ny; ++cy)
+    for (int cx = 0; cx < m.nx; ++cx) {
+      const int c = cy * m.nx + cx, k = (cx % 2) + 2 * (cy % 2);
+      m.col_cells[k].push_back(c);
+      for (int l = 0; l < 9; ++l) {
+        m.col_nodes[k].push_back(m.cell_nodes[c * 9 + l]);
+        m.col_src[k].push_back(c * 9 + l);
+      }
+    }
   m.spmv_rows.resize(m.n_nodes);
   for (int n = 0; n < m.n_nodes; ++n) m.spmv_rows[n] = n;
   std::stable_sort(m.spmv_rows.begin(), m.spmv_rows.end(), [&](int a, int b) {
@@ -230,6 +247,7 @@ void prolong_1d(const std::vector<double>& vc, const std::vector<double>& xf, st
 struct Level {
   HostMesh h;
   DevMesh dm{};
+  const int *col_cells[4] = {}, *col_nodes[4] = {}, *col_src[4] = {};
   Transfer T{};          // coarse = this level, fine = previous level (level >= 1)
   size_t n = 0;          // dofs
   std::vector<void*> owned;
@@ -308,6 +326,11 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
   TRY(upload(L.owned, &d.blk_src, h.blk_src));
   TRY(upload(L.owned, &d.cell_blk, h.cell_blk));
   TRY(upload(L.owned, &d.spmv_rows, h.spmv_rows));
+  for (int k = 0; k < 4; ++k) {
+    TRY(upload(L.owned, &L.col_cells[k], h.col_cells[k]));
+    TRY(upload(L.owned, &L.col_nodes[k], h.col_nodes[k]));
+    TRY(upload(L.owned, &L.col_src[k], h.col_src[k]));
+  }
   L.n = (size_t)h.n_nodes * 5;
   L.coarsest = coarsest;
   if (need_state) {
@@ -453,9 +476,10 @@ enum KernelId {
   KI_VANKA_CELL,
   KI_VANKA_GATHER,
   KI_VANKA_SETUP,
+  KI_VANKA_SCATTER,
   KI_COUNT
 };
-const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup"};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter"};
 
 struct Profiler {
   unsigned long long mask = 0;
@@ -533,8 +557,14 @@ int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
 }
 
 template <typename T, bool RES>
-int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act, T* y, cudaStream_t st) {
-  LAUNCH_W(50.0 * L.h.nnzb * (double)g_nact, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk(L.n, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y);
+int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act, T* y, cudaStream_t st,
+         const int* rows = nullptr, int nrows = -1) {
+  if (!rows) {
+    rows = L.dm.spmv_rows;
+    nrows = L.h.n_nodes;
+  }
+  const double blocks = nrows == L.h.n_nodes ? (double)L.h.nnzb : (double)L.h.nnzb * nrows / L.h.n_nodes;
+  LAUNCH_W(50.0 * blocks * (double)g_nact, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
   return launch_check();
 }
 
@@ -596,12 +626,27 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
   const double om = c->prm.mg_omega;
   LAUNCH(KI_FILL, k_fill<T>, (dim3(nblk(L.n, 256), S)), 256, 0, st, (int)L.n, 0.0, act, x, L.n);
   auto smooth = [&](bool first) -> int {
+    if (c->prm.mg_smoother == 1) {
+      // multiplicative: colour by colour, residual only on the colour's nodes
+      for (int k = 0; k < 4; ++k) {
+        const int nn = (int)L.h.col_nodes[k].size(), nc = (int)L.h.col_cells[k].size();
+        if (nc == 0) continue;
+        const T* rr = b;
+        if (!(first && k == 0)) {
+          TRY((spmv<T, true>(L, S, A, x, b, act, r, st, L.col_nodes[k], nn)));
+          rr = r;
+        }
+        LAUNCH_W(2.0 * 2025 * nc * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)nc * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, L.col_cells[k], nc);
+        LAUNCH(KI_VANKA_SCATTER, k_vanka_scatter<T>, (dim3(nblk((size_t)nn * 5, 128), S)), 128, 0, st, L.h.n_cells, L.col_nodes[k], L.col_src[k], nn, cellbuf, om, L.n, act, x);
+      }
+      return launch_check();
+    }
     const T* rr = b;
     if (!first) {
       TRY((spmv<T, true>(L, S, A, x, b, act, r, st)));
       rr = r;
     }
-    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf);
+    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, (const int*)nullptr, L.h.n_cells);
     LAUNCH(KI_VANKA_GATHER, k_vanka_gather<T>, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, cellbuf, om, L.n, act, x);
     return launch_check();
   };
@@ -890,6 +935,7 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
     return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
   if (p->precision != 0 && p->precision != 1) return fail(FSI_EINVAL, "precision must be 0 (FP64) or 1 (FP32 solver)");
+  if (p->mg_smoother != 0 && p->mg_smoother != 1) return fail(FSI_EINVAL, "mg_smoother must be 0 or 1");
   if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5 || !(p->mg_coarse_lps > 0))
     return fail(FSI_EINVAL, "bad multigrid parameters");
   return FSI_OK;

@@ -412,15 +412,17 @@ __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const u
 // Block-sparse matrix-vector product, y = A x or y = b - A x.
 // One thread per (slice, row dof).
 // --------------------------------------------------------------------------
+// rows: the node rows to compute (m.spmv_rows for all rows, visited in order
+// of their block count so that a warp's rows have equal length, or the rows of
+// one colour of the multiplicative smoother); the other rows of y are untouched.
 template <typename T, bool RESIDUAL>
 __global__ void k_bsr_spmv(DevMesh m, const T* __restrict__ A, const T* __restrict__ x,
                            const T* __restrict__ bvec, size_t stride, const uint8_t* __restrict__ active,
-                           T* __restrict__ y) {
+                           T* __restrict__ y, const int* __restrict__ rows, int nrows) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!active[s] || t >= m.n_nodes * 5) return;
-  // rows visited in order of their block count so that a warp's rows have equal length
-  const int i = m.spmv_rows[t / 5], c = t % 5;
+  if (!active[s] || t >= nrows * 5) return;
+  const int i = rows[t / 5], c = t % 5;
   const T* As = A + (size_t)s * m.nnzb * 25 + c * 5;
   const T* xs = x + s * stride;
   T acc = 0;
@@ -517,13 +519,15 @@ __global__ void __launch_bounds__(VK_THREADS) k_vanka_setup(DevMesh m, const T* 
 }
 
 // z_cell = inv_cell * r_cell: one thread per (slice, cell, local row).
+// cells: optional list of cells (one colour of the multiplicative smoother).
 template <typename T>
 __global__ void k_vanka_cell(DevMesh m, const T* __restrict__ inv, const T* __restrict__ r, size_t stride,
-                             const uint8_t* __restrict__ active, T* __restrict__ cellbuf) {
+                             const uint8_t* __restrict__ active, T* __restrict__ cellbuf,
+                             const int* __restrict__ cells, int ncells) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!active[s] || t >= m.n_cells * 45) return;
-  const int cell = t / 45, row = t % 45;
+  if (!active[s] || t >= ncells * 45) return;
+  const int cell = cells ? cells[t / 45] : t / 45, row = t % 45;
   const T* Mi = inv + ((size_t)s * m.n_cells + cell) * 2025;
   const T* rs = r + s * stride;
   T acc = 0;
@@ -553,6 +557,20 @@ __global__ void k_vanka_gather(DevMesh m, const T* __restrict__ cellbuf, double 
   const T w = T(omega / cnt);
   T* xs = x + s * stride + (size_t)node * 5;
   for (int c = 0; c < 5; ++c) xs[c] += w * acc[c];
+}
+
+// Multiplicative (coloured) Vanka: cells of one colour share no node, so each
+// node of the colour takes the correction of its one cell: x += omega z.
+template <typename T>
+__global__ void k_vanka_scatter(int n_cells, const int* __restrict__ nodes, const int* __restrict__ src, int nnodes,
+                                const T* __restrict__ cellbuf, double omega, size_t stride,
+                                const uint8_t* __restrict__ active, T* __restrict__ x) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= nnodes * 5) return;
+  const int k = t / 5, c = t % 5;
+  const int code = src[k];
+  x[s * stride + (size_t)nodes[k] * 5 + c] += (T)omega * cellbuf[((size_t)s * n_cells + code / 9) * 45 + (code % 9) * 5 + c];
 }
 
 // --------------------------------------------------------------------------

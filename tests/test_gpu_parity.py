@@ -174,3 +174,21 @@ def test_parareal_matches_oracle_iterates_and_reaches_serial():
         for n in range(1, w.n_slices + 1):
             errs = rel_field_errors(got[n], ref[n])
             assert max(errs.values()) <= 1e-10, (iters, n, errs)
+
+
+def test_multiplicative_smoother_step_matches_oracle():
+    """The coloured multiplicative Vanka smoother changes only the preconditioner."""
+    w = wl.SMALL_16x4
+    mesh = oracle_mesh(w)
+    k = w.k_fine
+    model, states = developed_states(w, mesh, 6, k)
+    U0 = np.stack([states[2], states[5]])
+    t0 = [3 * k, 6 * k]
+    ctx = ctx_for(w, 2, mg_smoother=1, mg_smooth=1, mg_omega=1.0)
+    Ub, _ = ctx.fsi_theta_step(to_dev(U0), t0, k, 0.5 + k)
+    got = Ub.cpu().numpy().reshape(2, -1, 5)
+    for s in range(2):
+        ref = model.step(U0[s], t0[s], k, 0.5 + k)
+        assert max(rel_field_errors(got[s], ref).values()) <= 1e-10
+    Us, _ = ctx.fsi_theta_step(to_dev(U0[1:]), t0[1:], k, 0.5 + k)
+    assert torch.equal(Us[0], Ub[1])
