@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step"])
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
     ap.add_argument("--kernel-table", action="store_true")
+    ap.add_argument("--no-precision-variant", action="store_true",
+                    help="skip the extra pass with the FP32 linear solver")
     return ap.parse_args()
 
 
@@ -280,6 +282,30 @@ def main():
         e2e = {"value": N * w.m_fine * args.steps / (ems / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h_in.numel() * 8, "d2h_bytes_per_step": h_out.numel() * 8}
 
+    # the precision variant (FP32 linear solver inside the FP64 Newton loop) on the
+    # same Parareal pass, timed the same way after one warm-up pass
+    variant = None
+    if not args.no_precision_variant and not fine_unit:
+        ctx32 = fsi.Context(w, max_batch=N, precision=1)
+
+        def step32():
+            U[1:].zero_()
+            _, s32 = ctx32.parareal_iterate(U, 1, 0.0)
+            return s32
+        step32()
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            s32 = step32()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        vms = b0.elapsed_time(b1)
+        variant = {"precision": "FP32 FGMRES/multigrid/Vanka in an FP64 Newton loop (FP64 residual, J, correction)",
+                   "value": N * w.m_fine * args.steps / (vms / 1000.0), "unit": UNIT,
+                   "ms_per_step": vms / args.steps, "newton_fine": s32["fine"], "newton_coarse": s32["coarse"]}
+        del ctx32
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
@@ -305,6 +331,7 @@ def main():
                            "batched_vs_serial": value / serial_rate if serial_rate else None,
                            "newton_fine": st["fine"], "newton_coarse": st["coarse"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "precision_variant": variant,
                 "gpu_launches": launches}
         print(json.dumps(line))
     if dist:
