@@ -206,6 +206,36 @@ int fsi_coarse(fsi_ctx* ctx, int S, const double* U0, const double* t0, double* 
 int parareal_iterate(fsi_ctx* ctx, double* U, int max_iter, double tol,
                      fsi_parareal_stats* stats, void* stream);
 
+/* Jacobian of the same step residual with respect to the old state U_{n-1}
+ * (Sec. 2.3: U_{n-1} enters the ALE mass term, the (1 - theta) terms, the
+ * kinematic and harmonic rows and, through the cell-mean velocity, the
+ * stabilisation weight; the old pressure does not enter). Same layout as
+ * fsi_jacobian; rows with Dirichlet data or p = 0 are zero. The stabilisation
+ * weight is not differentiable where a cell mean velocity is exactly zero;
+ * there its derivative is taken as zero. Errors: FSI_EINVAL. */
+int fsi_jacobian_old(fsi_ctx* ctx, int S, const double* U, const double* U_old,
+                     double k, double theta, double* vals, void* stream);
+
+/* Change the solid Lame parameters and the mean inflow velocity of a context
+ * (Eq. (stress) material, Sec. 4 inflow profile). Errors: FSI_EINVAL. */
+int fsi_set_material(fsi_ctx* ctx, double mu_s, double lambda_s, double vbar);
+
+/* Discrete adjoint of the fine trajectory (the paper gives no adjoint; this is
+ * the exact derivative of its discrete scheme, the theta step of Sec. 2.3).
+ * One slice: n_steps fine steps (k = T / n_slices / m_fine, theta = 1/2 +
+ * theta0 k) from the device state U0 [n_dofs] at time t0. Functional
+ *   J = sum_{n=0}^{n_steps} w_n |u(x_tip, t_n)|^2, trapezoid weights w_n (k/2 at the ends),
+ * x_tip the node at the top centre of the solid box. Output (host): J_out and
+ * grad[3] = (dJ/dmu_s, dJ/dlambda_s, dJ/dvbar), all partial derivatives.
+ * Backward sweep: (dR_n/dU_n)^T lam_n = -w_n dg/dU_n - (dR_{n+1}/dU_n)^T lam_{n+1},
+ * dJ/dp = sum_n lam_n^T dR_n/dp; transposed solves by FGMRES with the multigrid
+ * hierarchy of the transposed operators. States are checkpointed at slice
+ * boundaries (every m_fine steps) and recomputed slice by slice. Needs
+ * precision 0. The first call allocates the adjoint workspace of the context.
+ * Errors: FSI_EINVAL (no tip node, n_steps < 1), solver errors as fsi_theta_step. */
+int fsi_adjoint(fsi_ctx* ctx, const double* U0, double t0, int n_steps, double* J_out,
+                double* grad, fsi_stats* stats, void* stream);
+
 /* Measurement hooks (the paper has no counterpart; they serve benchmarking).
  * Process-wide, for one host thread. Every kernel launch of the library is
  * counted per kernel id (0 .. fsi_kernel_count()-1, names from

@@ -328,13 +328,13 @@ def element_residual(mesh: Mesh, tab: CellTables, mat, Ue, Uo, k, theta, alpha):
     R[..., 2:4] = sf * test_value(kin) + ff * test_grad(harm)
     R[..., 4] = fluid[:, None] * test_value(div[..., None])[..., 0]
     # local projection stabilisation (R4), constant in the unknowns apart from p
-    R[..., 4] += (fluid * k * alpha)[:, None] * np.einsum("clm,...cm->...cl", tab.S_lps, Ue[..., 4])
+    R[..., 4] += (fluid * k * alpha)[..., :, None] * np.einsum("clm,...cm->...cl", tab.S_lps, Ue[..., 4])
 
     # ---- do-nothing correction on the outflow boundary (Eq. variational) ----
     oc = mesh.outflow_cells
     if len(oc):
         Ue_o = Ue[..., oc, :, :]
-        Uo_o = Uo[oc]
+        Uo_o = Uo[..., oc, :, :]
         ge = np.einsum("cqld,...clf->...cqfd", tab.dphi_e, Ue_o)
         geo = np.einsum("cqld,...clf->...cqfd", tab.dphi_e, Uo_o)
         n = np.array([1.0, 0.0])

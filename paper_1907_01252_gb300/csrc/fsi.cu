@@ -71,7 +71,7 @@ struct HostMesh {
   std::vector<double> cell_h;
   std::vector<uint8_t> cell_flags, node_flags;
   std::vector<double> node_y;
-  std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk, spmv_rows;
+  std::vector<int> node_cells, rowptr, colidx, blk_row, blk_src, cell_blk, spmv_rows, blk_t;
   // multiplicative smoother: colour (cx%2 + 2 cy%2) -> its cells, its nodes and
   // the (cell, local node) each of those nodes belongs to
   std::vector<int> col_cells[4], col_nodes[4], col_src[4];
@@ -170,6 +170,12 @@ void build_mesh(HostMesh& m, bool has_solid, const double box[4]) {
         m.col_src[k].push_back(c * 9 + l);
       }
     }
+  m.blk_t.assign(m.nnzb, -1);
+  for (int b = 0; b < m.nnzb; ++b) {
+    const int i = m.blk_row[b], j = m.colidx[b];
+    auto beg = m.colidx.begin() + m.rowptr[j], end = m.colidx.begin() + m.rowptr[j + 1];
+    m.blk_t[b] = (int)(std::lower_bound(beg, end, i) - m.colidx.begin());
+  }
   m.spmv_rows.resize(m.n_nodes);
   for (int n = 0; n < m.n_nodes; ++n) m.spmv_rows[n] = n;
   std::stable_sort(m.spmv_rows.begin(), m.spmv_rows.end(), [&](int a, int b) {
@@ -248,6 +254,7 @@ struct Level {
   HostMesh h;
   DevMesh dm{};
   const int *col_cells[4] = {}, *col_nodes[4] = {}, *col_src[4] = {};
+  const int* blk_t = nullptr;   // index of the transposed block
   Transfer T{};          // coarse = this level, fine = previous level (level >= 1)
   size_t n = 0;          // dofs
   std::vector<void*> owned;
@@ -279,6 +286,10 @@ struct fsi_ctx {
   uint8_t *active = nullptr, *active2 = nullptr;
   double* t_dev = nullptr;
   int n_act = 0;        // slices set in `active` (host mirror, for work accounting)
+  int tip = -1;         // node at the top centre of the solid box (adjoint functional)
+  // adjoint workspace (one slice)
+  double *adj_ck = nullptr, *adj_sb = nullptr, *adj_vec = nullptr, *adj_B = nullptr, *adj_Bt = nullptr;
+  size_t adj_ck_len = 0, adj_sb_len = 0;
   // Parareal workspace
   double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
   int red_blocks = 0;
@@ -326,6 +337,7 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
   TRY(upload(L.owned, &d.blk_src, h.blk_src));
   TRY(upload(L.owned, &d.cell_blk, h.cell_blk));
   TRY(upload(L.owned, &d.spmv_rows, h.spmv_rows));
+  TRY(upload(L.owned, &L.blk_t, h.blk_t));
   for (int k = 0; k < 4; ++k) {
     TRY(upload(L.owned, &L.col_cells[k], h.col_cells[k]));
     TRY(upload(L.owned, &L.col_nodes[k], h.col_nodes[k]));
@@ -477,9 +489,14 @@ enum KernelId {
   KI_VANKA_GATHER,
   KI_VANKA_SETUP,
   KI_VANKA_SCATTER,
+  KI_BSR_TRANSPOSE,
+  KI_CELL_JACOBIAN_OLD,
+  KI_CELL_DRES_DLAME,
+  KI_GATHER_VECTOR,
+  KI_DRES_DVBAR,
   KI_COUNT
 };
-const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter"};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar"};
 
 struct Profiler {
   unsigned long long mask = 0;
@@ -551,8 +568,8 @@ int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
 template <typename T>
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, T* A, cudaStream_t st, double lps_scale = 1.0) {
-  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, L.Ke);
-  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<T>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A);
+  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian<false>, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, L.Ke);
+  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<T>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A, 1.0);
   return launch_check();
 }
 
@@ -582,7 +599,7 @@ int dots(fsi_ctx* c, int S, size_t n, int nv, const T* V, size_t vstride, size_t
 // preconditioner's matrices and inverses are stored in T.
 template <typename T>
 int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
-             cudaStream_t st, bool keep_coarsest = false) {
+             cudaStream_t st, bool keep_coarsest = false, bool transpose = false) {
   const int NL = (int)c->lev.size();
   const double* Ul = U;
   const double* Uol = Uold;
@@ -597,6 +614,11 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
     }
     T* A = reinterpret_cast<T*>(L.A);
     TRY(jacobian<T>(c, L, S, Ul, Uol, k, theta, act, A, st, std::pow(c->prm.mg_coarse_lps, l)));
+    if (transpose) {   // the hierarchy of the transposed operator (adjoint solves, FP64 only)
+      double* Ad = reinterpret_cast<double*>(A);
+      LAUNCH(KI_BSR_TRANSPOSE, k_bsr_transpose, (dim3(nblk((size_t)L.h.nnzb * 25, 256), S)), 256, 0, st, L.h.nnzb, L.blk_t, Ad, act, L.Ke);
+      CK(cudaMemcpyAsync(Ad, L.Ke, (size_t)S * L.h.nnzb * 25 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     if (L.coarsest) {
       if (keep_coarsest) continue;   // inverse of an earlier Newton iteration of this step
       const int n = (int)L.n;
@@ -944,6 +966,123 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Discrete adjoint of the fine trajectory (one slice).
+// ---------------------------------------------------------------------------
+int tip_u(fsi_ctx* c, const double* U, double out[2], cudaStream_t st) {
+  CK(cudaMemcpyAsync(out, U + (size_t)c->tip * 5 + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FSI_OK;
+}
+
+int adjoint_impl(fsi_ctx* c, const double* U0, double t0, int M, double* J_out, double* grad, fsi_stats* stats,
+                 cudaStream_t st) {
+  if (c->tip < 0) return fail(FSI_EINVAL, "no mesh node at the top centre of the solid (adjoint functional)");
+  if (M < 1) return fail(FSI_EINVAL, "n_steps must be >= 1");
+  if (c->prm.precision != 0) return fail(FSI_EINVAL, "the adjoint runs in FP64 (precision 0)");
+  Level& L = c->lev[0];
+  const size_t n = c->n;
+  const int m = c->prm.m_fine;
+  const double k = c->prm.T / c->prm.n_slices / m;
+  const double theta = 0.5 + c->prm.theta0 * k;
+  const int nslice = (M + m - 1) / m;
+  const size_t ck_len = (size_t)(nslice + 1) * n, sb_len = (size_t)(m + 1) * n;
+  if (c->adj_ck_len < ck_len) {
+    if (c->adj_ck) cudaFree(c->adj_ck);
+    c->adj_ck = nullptr;
+    CK(cudaMalloc(&c->adj_ck, ck_len * sizeof(double)));
+    c->adj_ck_len = ck_len;
+  }
+  if (!c->adj_sb) {
+    CK(cudaMalloc(&c->adj_sb, sb_len * sizeof(double)));
+    CK(cudaMalloc(&c->adj_vec, 6 * n * sizeof(double)));
+    CK(cudaMalloc(&c->adj_B, (size_t)L.h.nnzb * 25 * sizeof(double)));
+    CK(cudaMalloc(&c->adj_Bt, (size_t)L.h.nnzb * 25 * sizeof(double)));
+    c->adj_sb_len = sb_len;
+  }
+  double *lam = c->adj_vec, *lamn = lam + n, *rhs = lam + 2 * n, *rhs2 = lam + 3 * n, *dR = lam + 4 * n,
+         *Unext = lam + 5 * n;
+  std::vector<double> w(M + 1, k);
+  w[0] = w[M] = 0.5 * k;
+  // forward sweep, checkpoints at slice boundaries
+  double u[2];
+  CK(cudaMemcpyAsync(c->adj_ck, U0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(c->adj_sb, U0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TRY(tip_u(c, U0, u, st));
+  double J = w[0] * (u[0] * u[0] + u[1] * u[1]);
+  double* cur = c->adj_sb;
+  for (int step = 1; step <= M; ++step) {
+    const double told = t0 + (step - 1) * k;
+    TRY(theta_step(c, 1, cur, &told, k, theta, cur, stats, st, 1, false));
+    TRY(tip_u(c, cur, u, st));
+    J += w[step] * (u[0] * u[0] + u[1] * u[1]);
+    if (step % m == 0 || step == M)
+      CK(cudaMemcpyAsync(c->adj_ck + (size_t)((step + m - 1) / m) * n, cur, n * sizeof(double),
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  // backward sweep: recompute each slice from its checkpoint, then adjoint steps
+  double g[3] = {0, 0, 0};
+  bool have_next = false;
+  std::vector<uint8_t> one(1, 1);
+  for (int sl = nslice - 1; sl >= 0; --sl) {
+    const int s0 = sl * m, s1 = std::min(M, s0 + m);   // steps s0+1 .. s1
+    CK(cudaMemcpyAsync(c->adj_sb, c->adj_ck + (size_t)sl * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int j = 1; j <= s1 - s0; ++j) {
+      const double told = t0 + (s0 + j - 1) * k;
+      TRY(theta_step(c, 1, c->adj_sb + (size_t)(j - 1) * n, &told, k, theta, c->adj_sb + (size_t)j * n, stats, st, 1,
+                     false));
+    }
+    for (int nn = s1; nn > s0; --nn) {
+      const double* Un = c->adj_sb + (size_t)(nn - s0) * n;
+      const double* Um = c->adj_sb + (size_t)(nn - s0 - 1) * n;
+      CK(cudaMemcpyAsync(c->active, one.data(), 1, cudaMemcpyHostToDevice, st));
+      c->n_act = g_nact = 1;
+      // rhs = -w_n dg/dU_n - (dR_{n+1}/dU_n)^T lam_{n+1}
+      TRY(tip_u(c, Un, u, st));
+      CK(cudaMemsetAsync(rhs, 0, n * sizeof(double), st));
+      const double gtip[2] = {-w[nn] * 2.0 * u[0], -w[nn] * 2.0 * u[1]};
+      CK(cudaMemcpyAsync(rhs + (size_t)c->tip * 5 + 2, gtip, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+      if (have_next) {
+        const double* Up = nn < s1 ? c->adj_sb + (size_t)(nn - s0 + 1) * n : Unext;
+        LAUNCH(KI_CELL_JACOBIAN_OLD, k_cell_jacobian<true>, (dim3(L.h.n_cells, 1)), JAC_THREADS, 0, st, L.dm, c->P, Up, Un, L.n, k, theta, 1.0, c->active, L.Ke);
+        LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<double>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), 1)), 128, 0, st, L.dm, L.Ke, c->active, c->adj_B, 0.0);
+        LAUNCH(KI_BSR_TRANSPOSE, k_bsr_transpose, (dim3(nblk((size_t)L.h.nnzb * 25, 256), 1)), 256, 0, st, L.h.nnzb, L.blk_t, c->adj_B, c->active, c->adj_Bt);
+        TRY((spmv<double, true>(L, 1, c->adj_Bt, lamn, rhs, c->active, rhs2, st)));
+        CK(cudaMemcpyAsync(rhs, rhs2, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+      // (dR_n/dU_n)^T lam_n = rhs with the transposed multigrid hierarchy
+      TRY(mg_setup<double>(c, 1, Un, Um, k, theta, c->active, st, false, true));
+      CK(cudaMemcpyAsync(L.b, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      int rc = fgmres<double>(c, 1, L.b, L.x, c->active, c->prm.gmres_rtol, stats, st);
+      if (rc != FSI_OK) return fail(rc, "adjoint linear solve failed");
+      CK(cudaMemcpyAsync(lam, L.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      // dJ/dp += lam^T dR_n/dp
+      CK(cudaMemcpyAsync(c->active, one.data(), 1, cudaMemcpyHostToDevice, st));
+      const double tn = t0 + nn * k;
+      CK(cudaMemcpyAsync(c->t_dev, &tn, sizeof(double), cudaMemcpyHostToDevice, st));
+      for (int which = 0; which < 3; ++which) {
+        if (which < 2) {
+          LAUNCH(KI_CELL_DRES_DLAME, k_cell_dres_dlame, (dim3(nblk(L.h.n_cells, 128), 1)), 128, 0, st, L.dm, Un, Um, L.n, k, theta, which, c->active, L.cellbuf);
+          LAUNCH(KI_GATHER_VECTOR, k_gather_vector, (dim3(nblk(L.h.n_nodes, 128), 1)), 128, 0, st, L.dm, L.cellbuf, L.n, c->active, dR);
+        } else {
+          LAUNCH(KI_DRES_DVBAR, k_dres_dvbar, (dim3(nblk(L.h.n_nodes, 128), 1)), 128, 0, st, L.dm, c->P, c->t_dev, L.n, c->active, dR);
+        }
+        TRY(dots<double>(c, 1, n, 1, dR, 0, n, lam, n, c->active, c->scal, 1, false, st));
+        double d = 0.0;
+        CK(cudaMemcpyAsync(&d, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        g[which] += d;
+      }
+      CK(cudaMemcpyAsync(lamn, lam, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      have_next = true;
+    }
+    CK(cudaMemcpyAsync(Unext, c->adj_sb + n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  *J_out = J;
+  for (int i = 0; i < 3; ++i) grad[i] = g[i];
+  return FSI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free residual: its scratch lives in one file-scope device array.
 // Layout (doubles): [0, 32) slice flags as bytes, [32, 32 + kNaMaxSlices)
 // per-slice times, then the per-cell contributions [S][cells][45].
@@ -982,6 +1121,8 @@ const char* fsi_last_error(void) { return g_err.c_str(); }
 
 void fsi_destroy(fsi_ctx* c) {
   if (!c) return;
+  for (double* p : {c->adj_ck, c->adj_sb, c->adj_vec, c->adj_B, c->adj_Bt})
+    if (p) cudaFree(p);
   for (auto& L : c->lev)
     for (void* p : L.owned) cudaFree(p);
   for (void* p : c->owned) cudaFree(p);
@@ -1033,6 +1174,13 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
     if (l > 0 && (rc = setup_transfer(c->lev[l], c->lev[l - 1]))) return cleanup(rc);
   }
   c->n = c->lev[0].n;
+  if (mesh->has_solid) {
+    const HostMesh& h = c->lev[0].h;
+    const double xt = 0.5 * (mesh->solid_x0 + mesh->solid_x1), yt = mesh->solid_y1;
+    for (int j = 0; j < h.nny; ++j)
+      for (int i = 0; i < h.nnx; ++i)
+        if (std::fabs(h.xn[i] - xt) < 1e-12 && std::fabs(h.yn[j] - yt) < 1e-12) c->tip = j * h.nnx + i;
+  }
   const size_t S = c->S, n = c->n, m = c->m;
   auto A = [&](auto** ptr, size_t cnt) { return dalloc(c->owned, ptr, cnt); };
   if ((rc = A(&c->Uit, S * n)) || (rc = A(&c->Uold, S * n)) || (rc = A(&c->R, S * n)) || (rc = A(&c->dU, S * n)) ||
@@ -1231,6 +1379,39 @@ int fsi_kernel_count(void) { return KI_COUNT; }
 
 const char* fsi_kernel_name(int kernel_id) {
   return (kernel_id >= 0 && kernel_id < KI_COUNT) ? kKernelNames[kernel_id] : "";
+}
+
+int fsi_jacobian_old(fsi_ctx* c, int S, const double* U, const double* U_old, double k, double theta,
+                     double* vals, void* stream) {
+  if (!c || !U || !U_old || !vals) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& L = c->lev[0];
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = S;
+  LAUNCH(KI_CELL_JACOBIAN_OLD, k_cell_jacobian<true>, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, U_old, L.n, k, theta, 1.0, c->active, L.Ke);
+  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<double>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, c->active, vals, 0.0);
+  TRY(launch_check());
+  CK(cudaStreamSynchronize(st));
+  return FSI_OK;
+}
+
+int fsi_set_material(fsi_ctx* c, double mu_s, double lambda_s, double vbar) {
+  if (!c || !(mu_s > 0) || !(lambda_s > 0) || !(vbar >= 0)) return fail(FSI_EINVAL, "bad material");
+  c->prm.mu_s = c->P.mu_s = mu_s;
+  c->prm.lambda_s = c->P.lambda_s = lambda_s;
+  c->prm.vbar = c->P.vbar = vbar;
+  return FSI_OK;
+}
+
+int fsi_adjoint(fsi_ctx* c, const double* U0, double t0, int n_steps, double* J_out, double* grad, fsi_stats* stats,
+                void* stream) {
+  if (!c || !U0 || !J_out || !grad) return fail(FSI_EINVAL, "null argument");
+  if (stats) *stats = fsi_stats{};
+  int rc = adjoint_impl(c, U0, t0, n_steps, J_out, grad, stats, (cudaStream_t)stream);
+  if (stats) stats->status = rc;
+  return rc;
 }
 
 int fsi_residual_noalloc(fsi_ctx* c, int S, const double* U, const double* U_old, const double* t_new, double k,

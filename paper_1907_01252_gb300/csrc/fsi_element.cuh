@@ -215,3 +215,79 @@ __device__ inline void edge_flux_lin(const Phys& P, M2 G, M2 Hu, M2 dG, M2 dH, d
   out[0] = R.a;
   out[1] = R.c;
 }
+
+// Directional derivative of qp_flux with respect to the t_{n-1} state
+// (dvo, dGo, duo, dHuo); the old pressure does not enter the step. Used by the
+// discrete adjoint (the old-state Jacobian dR_n / dU_{n-1}).
+__device__ inline void qp_flux_lin_old(const Phys& P, const QpIn& q, const QpDerived& d, bool solid, double k,
+                                       double theta, const double* dvo, M2 dGo, const double* duo, M2 dHo,
+                                       double* out) {
+  for (int i = 0; i < 15; ++i) out[i] = 0.0;
+  const double kto = k * (1.0 - theta);
+  if (!solid) {
+    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+    const double dJo = trace(mul(d.Ao, dHo));
+    const M2 dAo = adj(dHo);
+    const M2 dCo = tp(dAo);
+    // ALE mass term: J_{n-1/2}, grad v_{n-1/2}, F_{n-1/2} and u_n - u_{n-1} depend on the old state
+    const double dJh = 0.5 * dJo;
+    const M2 dGh = 0.5 * dGo;
+    const M2 dBh = -0.5 * mul(mul(d.Bh, dHo), d.Bh);
+    double t1[2], t2[2], t3[2], t4[2], dM[2], mdw[2] = {-duo[0], -duo[1]};
+    mv(d.Bh, d.w, t1);
+    mv(dGh, t1, t2);
+    mv(dBh, d.w, t1);
+    mv(d.Gh, t1, t3);
+    mv(d.Bh, mdw, t1);
+    mv(d.Gh, t1, t4);
+    for (int c = 0; c < 2; ++c) dM[c] = t2[c] + t3[c] + t4[c];
+    // old convection G_o A_o v_o
+    double Aov[2], dGAv[2], GdAv[2], GAdv[2];
+    mv(d.Ao, q.vo, Aov);
+    mv(dGo, Aov, dGAv);
+    mv(dAo, q.vo, t1);
+    mv(q.Go, t1, GdAv);
+    mv(d.Ao, dvo, t1);
+    mv(q.Go, t1, GAdv);
+    for (int c = 0; c < 2; ++c)
+      out[c * 3] = rf * (dJh * ((q.v[c] - q.vo[c]) - d.M[c]) + d.Jh * (-dvo[c] - dM[c])) +
+                   kto * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
+    // old stress (rho nu / J_o) Q_o - p_n C_o
+    M2 Gt = tp(q.Go), dGt = tp(dGo);
+    M2 dQ = mul(mul(dGo, d.Ao), d.Co) + mul(mul(q.Go, dAo), d.Co) + mul(mul(q.Go, d.Ao), dCo) +
+            mul(mul(dCo, Gt), d.Co) + mul(mul(d.Co, dGt), d.Co) + mul(mul(d.Co, Gt), dCo);
+    M2 S = kto * ((rn / d.Jo) * dQ - (rn * dJo / (d.Jo * d.Jo)) * d.Qo - q.p * dCo);
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+    M2 Hh = kto * dHo;
+    out[7] = Hh.a; out[8] = Hh.b; out[10] = Hh.c; out[11] = Hh.d;
+  } else {
+    const double mu = P.mu_s, lam = P.lambda_s;
+    M2 E = 0.5 * (mul(tp(d.Fo), d.Fo) - eye2());
+    M2 Sig = 2.0 * mu * E + (lam * trace(E)) * eye2();
+    M2 dE = 0.5 * (mul(tp(dHo), d.Fo) + mul(tp(d.Fo), dHo));
+    M2 dSig = 2.0 * mu * dE + (lam * trace(dE)) * eye2();
+    M2 S = kto * (mul(dHo, Sig) + mul(d.Fo, dSig));
+    for (int c = 0; c < 2; ++c) {
+      out[c * 3] = -P.rho_s * dvo[c];
+      out[6 + c * 3] = -duo[c] - kto * dvo[c];
+    }
+    out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
+  }
+}
+
+// Old-state part of the outflow correction, -k (1 - theta)(rho nu / J_o) C_o G_o^T C_o n.
+__device__ inline void edge_flux_lin_old(const Phys& P, M2 Go, M2 Huo, M2 dGo, M2 dHo, double k, double theta,
+                                         double* out) {
+  edge_flux_lin(P, Go, Huo, dGo, dHo, k, 1.0 - theta, out);
+}
+
+// Derivatives of the solid first Piola stress F Sigma with respect to the Lame
+// parameters: dP/dmu = F 2E, dP/dlambda = F tr(E) I.
+__device__ inline M2 dpiola_dmu(M2 F) {
+  M2 E = 0.5 * (mul(tp(F), F) - eye2());
+  return mul(F, 2.0 * E);
+}
+__device__ inline M2 dpiola_dlambda(M2 F) {
+  M2 E = 0.5 * (mul(tp(F), F) - eye2());
+  return trace(E) * F;
+}

@@ -252,6 +252,17 @@ __device__ inline bool jac_block_nonzero(bool solid, int ci, int cj) {
   return false;
 }
 
+// Old-state blocks (OLD = true: dR_n / dU_{n-1}, for the discrete adjoint):
+// the t_{n-1} fields (v, u) enter every row but the divergence rows, which see
+// the old state only through the stabilisation weight (added separately).
+__device__ inline bool jac_old_block_nonzero(bool solid, int ci, int cj) {
+  if (cj >= 4 || ci == 4) return false;
+  if (!solid) return ci < 2 || cj == ci;
+  if (ci < 2) return cj == ci || cj == 2 || cj == 3;
+  return cj == ci || cj == ci - 2;
+}
+
+template <bool OLD>
 __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
                                                                const double* __restrict__ Uold, size_t stride,
                                                                double k, double theta, double lps_scale,
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
   __shared__ double sD[9][15][15];     // [q][test slot][trial direction]
   __shared__ double sDe[3][2][12];     // outflow edge: [q][momentum comp][trial direction (c<4)]
   __shared__ double sAlpha;
+  __shared__ double sSp[9], sDalpha[2];   // OLD: S p per local node, d alpha / d vbar
   const int tid = threadIdx.x;
   const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
   const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
@@ -282,6 +294,33 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     derive(sq[tid], sd[tid]);
   }
   if (tid == 32 && !solid) sAlpha = lps_scale * lps_weight(P, sUo, hx, hy);
+  if (OLD && !solid && tid >= 64 && tid < 73) {
+    const int i = tid - 64;
+    double acc = 0.0;
+    for (int j = 0; j < 9; ++j) acc += (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]) * sU[j * 5 + 4];
+    sSp[i] = acc;
+  }
+  if (OLD && !solid && tid == 96) {
+    // alpha = alpha0 h^2 / (rho nu + rho |vbar| h): derivative in the cell mean of v_{n-1}
+    double mx = 0.0, my = 0.0, ws = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      double vx = 0.0, vy = 0.0;
+      for (int l = 0; l < 9; ++l) {
+        vx += c_phi[q][l] * sUo[l * 5 + 0];
+        vy += c_phi[q][l] * sUo[l * 5 + 1];
+      }
+      mx += c_wq[q] * vx;
+      my += c_wq[q] * vy;
+      ws += c_wq[q];
+    }
+    mx /= ws;
+    my /= ws;
+    const double sp = sqrt(mx * mx + my * my), h = sqrt(hx * hx + hy * hy);
+    const double den = P.rho_f * P.nu_f + P.rho_f * sp * h;
+    const double f = sp > 0.0 ? -lps_scale * P.alpha0 * h * h * P.rho_f * h / (den * den * sp) : 0.0;
+    sDalpha[0] = f * mx;
+    sDalpha[1] = f * my;
+  }
   __syncthreads();
   for (int t = tid; t < 9 * 15; t += JAC_THREADS) {
     const int q = t / 15, dir = t % 15, cj = dir / 3, b = dir % 3;
@@ -301,14 +340,15 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
       if (b == 0) dp = 1.0;
     }
     double out[15];
-    qp_flux_lin(P, sq[q], sd[q], solid, k, theta, dv, dG, du, dH, dp, out);
+    if (OLD) qp_flux_lin_old(P, sq[q], sd[q], solid, k, theta, dv, dG, du, dH, out);
+    else qp_flux_lin(P, sq[q], sd[q], solid, k, theta, dv, dG, du, dH, dp, out);
     for (int r = 0; r < 15; ++r) sD[q][r][dir] = out[r];
   }
   if (outflow) {
     for (int t = tid; t < 3 * 12; t += JAC_THREADS) {
       const int q = t / 12, dir = t % 12, cj = dir / 3, b = dir % 3;
       M2 G, Hu;
-      eval_edge_grad(sU, q, ihx, ihy, G, Hu);
+      eval_edge_grad(OLD ? sUo : sU, q, ihx, ihy, G, Hu);
       M2 dG = m2(0, 0, 0, 0), dH = m2(0, 0, 0, 0);
       double out[2] = {0, 0};
       if (b > 0) {
@@ -316,7 +356,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
         const int c = cj % 2;
         if (c == 0) { if (b == 1) X.a = 1.0; else X.b = 1.0; }
         else { if (b == 1) X.c = 1.0; else X.d = 1.0; }
-        edge_flux_lin(P, G, Hu, dG, dH, k, theta, out);
+        if (OLD) edge_flux_lin_old(P, G, Hu, dG, dH, k, theta, out);
+        else edge_flux_lin(P, G, Hu, dG, dH, k, theta, out);
       }
       sDe[q][0][dir] = out[0];
       sDe[q][1][dir] = out[1];
@@ -353,7 +394,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
       if (e < 2025) {
         const int row = e / 45, col = e % 45;
         const int i = row / 5, ci = row % 5, cj = col % 5;
-        if (jac_block_nonzero(solid, ci, cj))
+        if (OLD ? jac_old_block_nonzero(solid, ci, cj) : jac_block_nonzero(solid, ci, cj))
           acc[r] += sB[0][i] * sE[ci * 3][col] + sB[1][i] * sE[ci * 3 + 1][col] + sB[2][i] * sE[ci * 3 + 2][col];
       }
     }
@@ -367,8 +408,16 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     const int row = e / 45, col = e % 45;
     const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
     double v = acc[r];
-    if (!solid && ci == 4 && cj == 4)
+    if (!OLD && !solid && ci == 4 && cj == 4)
       v += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
+    if (OLD && !solid && ci == 4 && cj < 2) {
+      double mj = 0.0, ws = 0.0;   // d vbar / d v_{n-1} at local node j
+      for (int q = 0; q < 9; ++q) {
+        mj += c_wq[q] * c_phi[q][j];
+        ws += c_wq[q];
+      }
+      v += k * sSp[i] * sDalpha[cj] * (mj / ws);
+    }
     if (outflow && ci < 2 && cj < 4) {
       for (int q = 0; q < 3; ++q) {
         const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
@@ -382,9 +431,11 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
 
 // Block-sparse assembly: one thread per (slice, block, row component),
 // fixed-order sum over the cells sharing both nodes, identity rows replaced.
+// identity_value: 1 for dR/dU (identity rows), 0 for dR/dU_old (those rows do
+// not depend on the old state).
 template <typename T>
 __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const uint8_t* __restrict__ active,
-                               T* __restrict__ A) {
+                               T* __restrict__ A, double identity_value) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (!active[s] || t >= m.nnzb * 5) return;
@@ -393,7 +444,7 @@ __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const u
   const uint8_t nf = m.node_flags[i];
   double acc[5] = {0, 0, 0, 0, 0};
   if (is_identity_row(nf, ci)) {
-    if (i == j) acc[ci] = 1.0;
+    if (i == j) acc[ci] = identity_value;
   } else {
     for (int e = 0; e < 4; ++e) {
       const int code = m.blk_src[b * 4 + e];
@@ -779,6 +830,84 @@ __global__ void k_dense_apply(int n, const T* __restrict__ inv, const T* __restr
   for (int c = lane; c < n; c += 32) acc = fma(M[c], xs[c], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) y[s * stride + r] = acc;
+}
+
+// --------------------------------------------------------------------------
+// Discrete adjoint helpers.
+// --------------------------------------------------------------------------
+// Block transpose: At[bt[b]] = A[b]^T (the block pattern is symmetric).
+__global__ void k_bsr_transpose(int nnzb, const int* __restrict__ bt, const double* __restrict__ A,
+                                const uint8_t* __restrict__ active, double* __restrict__ At) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= nnzb * 25) return;
+  const int b = t / 25, r = (t % 25) / 5, c = t % 5;
+  At[((size_t)s * nnzb + bt[b]) * 25 + c * 5 + r] = A[((size_t)s * nnzb + b) * 25 + r * 5 + c];
+}
+
+// Cell contributions of dR/dmu_s (which = 0) or dR/dlambda_s (which = 1):
+// k theta dP(F_n) + k (1 - theta) dP(F_{n-1}) tested with grad phi, solid cells.
+__global__ void k_cell_dres_dlame(DevMesh m, const double* __restrict__ U, const double* __restrict__ Uold,
+                                  size_t stride, double k, double theta, int which,
+                                  const uint8_t* __restrict__ active, double* __restrict__ cellbuf) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || cell >= m.n_cells) return;
+  double* out = cellbuf + ((size_t)s * m.n_cells + cell) * 45;
+  for (int i = 0; i < 45; ++i) out[i] = 0.0;
+  if (!(m.cell_flags[cell] & CF_SOLID)) return;
+  double Ue[45], Uo[45];
+  load_cell(m, U + s * stride, cell, Ue);
+  load_cell(m, Uold + s * stride, cell, Uo);
+  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  for (int q = 0; q < 9; ++q) {
+    QpIn st;
+    eval_qp(Ue, Uo, q, ihx, ihy, st);
+    const M2 F = eye2() + st.Hu, Fo = eye2() + st.Huo;
+    const M2 S = which == 0 ? (k * theta) * dpiola_dmu(F) + (k * (1.0 - theta)) * dpiola_dmu(Fo)
+                            : (k * theta) * dpiola_dlambda(F) + (k * (1.0 - theta)) * dpiola_dlambda(Fo);
+    const double w = c_wq[q] * area;
+    for (int l = 0; l < 9; ++l) {
+      const double b1 = w * c_dps[q][l] * ihx, b2 = w * c_dpt[q][l] * ihy;
+      out[l * 5 + 0] += b1 * S.a + b2 * S.b;
+      out[l * 5 + 1] += b1 * S.c + b2 * S.d;
+    }
+  }
+}
+
+// Node gather of cell contributions with the residual's row selection and
+// zero on identity rows (derivatives of rows that do not depend on the input).
+__global__ void k_gather_vector(DevMesh m, const double* __restrict__ cellbuf, size_t stride,
+                                const uint8_t* __restrict__ active, double* __restrict__ R) {
+  const int s = blockIdx.y;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || node >= m.n_nodes) return;
+  const uint8_t nf = m.node_flags[node];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int e = 0; e < 4; ++e) {
+    const int code = m.node_cells[node * 4 + e];
+    if (code < 0) break;
+    const int cell = code / 9, l = code % 9;
+    const double* src = cellbuf + ((size_t)s * m.n_cells + cell) * 45 + l * 5;
+    for (int c = 0; c < 5; ++c)
+      if (row_takes(m.cell_flags[cell], nf, c)) acc[c] += src[c];
+  }
+  for (int c = 0; c < 5; ++c) R[s * stride + (size_t)node * 5 + c] = is_identity_row(nf, c) ? 0.0 : acc[c];
+}
+
+// dR/dvbar: the inflow rows carry U - g(t), g proportional to vbar.
+__global__ void k_dres_dvbar(DevMesh m, Phys P, const double* __restrict__ t, size_t stride,
+                             const uint8_t* __restrict__ active, double* __restrict__ R) {
+  const int s = blockIdx.y;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || node >= m.n_nodes) return;
+  const uint8_t nf = m.node_flags[node];
+  for (int c = 0; c < 5; ++c) {
+    double v = 0.0;
+    if (c == 0 && P.vbar != 0.0) v = -dirichlet_value(P, nf, m.node_y[node], 0, t[s]) / P.vbar;
+    R[s * stride + (size_t)node * 5 + c] = v;
+  }
 }
 
 // --------------------------------------------------------------------------

@@ -73,6 +73,9 @@ SIGNATURES = {
     "fsi_residual": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
     "fsi_residual_noalloc": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
     "fsi_jacobian": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
+    "fsi_jacobian_old": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
+    "fsi_set_material": (_I, [_VP, _D, _D, _D]),
+    "fsi_adjoint": (_I, [_VP, _VP, _D, _I, C.POINTER(_D), C.POINTER(_D), C.POINTER(fsi_stats), _VP]),
     "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "fsi_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
@@ -227,6 +230,24 @@ class Context:
         _check(self.lib.fsi_jacobian(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
         return vals
 
+    def fsi_jacobian_old(self, U, U_old, k, theta, vals=None):
+        import torch
+        S = U.shape[0]
+        vals = torch.empty((S, self.nnzb, 5, 5), dtype=torch.float64, device=U.device) if vals is None else vals
+        _check(self.lib.fsi_jacobian_old(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
+        return vals
+
+    def fsi_set_material(self, mu_s, lambda_s, vbar):
+        _check(self.lib.fsi_set_material(self.handle, mu_s, lambda_s, vbar))
+
+    def fsi_adjoint(self, U0, t0, n_steps):
+        """(J, [dJ/dmu_s, dJ/dlambda_s, dJ/dvbar], stats) of the n_steps fine trajectory from U0 [n_dofs]."""
+        J = C.c_double()
+        grad = (C.c_double * 3)()
+        st = fsi_stats()
+        _check(self.lib.fsi_adjoint(self.handle, _ptr(U0), t0, n_steps, C.byref(J), grad, C.byref(st), _stream()))
+        return J.value, [grad[0], grad[1], grad[2]], st.as_dict()
+
     def fsi_bsr_pattern(self):
         rowptr = np.zeros(self.n_nodes + 1, dtype=np.int32)
         colidx = np.zeros(self.nnzb, dtype=np.int32)
@@ -274,3 +295,27 @@ class Context:
 
 def fsi_setup(workload, max_batch=1, **overrides):
     return Context(workload, max_batch, **overrides)
+
+
+def tip_functional(ctx: Context, U0, t0, n_steps):
+    """torch.autograd.Function for the bar-tip functional of the fine trajectory.
+
+    tip_functional(ctx, U0, t0, n)(params) with params = tensor([mu_s, lambda_s,
+    vbar]) returns J; its backward uses the discrete adjoint (fsi_adjoint)."""
+    import torch
+
+    class _TipFunctional(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, params):
+            p = params.detach().cpu().double().tolist()
+            ctx.fsi_set_material(*p)
+            J, grad, _ = ctx.fsi_adjoint(U0, t0, n_steps)
+            fctx.save_for_backward(torch.tensor(grad, dtype=params.dtype, device=params.device))
+            return torch.tensor(J, dtype=params.dtype, device=params.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (grad,) = fctx.saved_tensors
+            return gout * grad
+
+    return _TipFunctional.apply
