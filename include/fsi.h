@@ -122,6 +122,9 @@ typedef struct fsi_parareal_stats {
   long long fine_steps;    /* fine theta steps run (slices x steps) */
   long long coarse_steps;  /* coarse theta steps run */
   fsi_stats fine, coarse;  /* summed solver statistics */
+  double* history;         /* optional host array [history_len][3]: the relative
+                              increments (v, u, p) of every iteration; NULL to skip */
+  int history_len;
 } fsi_parareal_stats;
 
 typedef struct fsi_ctx fsi_ctx;

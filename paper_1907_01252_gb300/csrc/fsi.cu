@@ -1284,6 +1284,10 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
   const size_t n = c->n;
   const double dt = c->prm.T / N;
   fsi_parareal_stats loc{};
+  if (stats) {
+    loc.history = stats->history;
+    loc.history_len = stats->history_len;
+  }
   if (!c->Cold) {
     c->red_blocks = 152;
     if (dalloc(c->owned, &c->Cold, (size_t)N * n) || dalloc(c->owned, &c->Fv, (size_t)N * n) ||
@@ -1335,6 +1339,8 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
     loc.increment_v = inc[0];
     loc.increment_u = inc[1];
     loc.increment_p = inc[2];
+    if (loc.history && it - 1 < loc.history_len)
+      for (int f = 0; f < 3; ++f) loc.history[(it - 1) * 3 + f] = inc[f];
     loc.iterations = it;
     if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
   }

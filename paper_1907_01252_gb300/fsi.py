@@ -50,10 +50,11 @@ class fsi_stats(C.Structure):
 class fsi_parareal_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("increment_v", C.c_double), ("increment_u", C.c_double),
                 ("increment_p", C.c_double), ("fine_steps", C.c_longlong), ("coarse_steps", C.c_longlong),
-                ("fine", fsi_stats), ("coarse", fsi_stats)]
+                ("fine", fsi_stats), ("coarse", fsi_stats), ("history", C.POINTER(C.c_double)),
+                ("history_len", C.c_int)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("fine", "coarse")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("fine", "coarse", "history", "history_len")}
         d["fine"] = self.fine.as_dict()
         d["coarse"] = self.coarse.as_dict()
         return d
@@ -286,11 +287,19 @@ class Context:
         _check(self.lib.fsi_coarse(self.handle, U0.shape[0], _ptr(U0), tp, _ptr(U1), C.byref(st), _stream()))
         return U1, st.as_dict()
 
-    def parareal_iterate(self, U, max_iter, tol):
-        """U: device [n_slices + 1, n_dofs]; U[0] is the initial state. In place."""
+    def parareal_iterate(self, U, max_iter, tol, history=False):
+        """U: device [n_slices + 1, n_dofs]; U[0] is the initial state. In place.
+        With history=True the stats hold the (v, u, p) increments of every iteration."""
         st = fsi_parareal_stats()
+        hist = np.zeros((max(max_iter, 1), 3)) if history else None
+        if history:
+            st.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.history_len = max_iter
         _check(self.lib.parareal_iterate(self.handle, _ptr(U), max_iter, tol, C.byref(st), _stream()))
-        return U, st.as_dict()
+        d = st.as_dict()
+        if history:
+            d["history"] = hist[:d["iterations"]].tolist()
+        return U, d
 
 
 def fsi_setup(workload, max_batch=1, **overrides):
