@@ -99,6 +99,9 @@ typedef struct fsi_params {
   int mg_rebuild_every;    /* fine propagator: rebuild the hierarchy at the first
                               Newton iteration of every mg_rebuild_every-th step and
                               keep it in between (>= 1; 1 = every step) */
+  int graph_max_batch;     /* batches of at most this many slices run each FGMRES
+                              iteration as one CUDA graph (captured once per batch
+                              size and Krylov index); 0 disables graphs */
   int precision;           /* 0: FP64 throughout. 1: the linear solver (FGMRES,
                               multigrid, Vanka, block-sparse operator) in FP32 inside
                               the FP64 Newton loop, whose residual, J = det F and the

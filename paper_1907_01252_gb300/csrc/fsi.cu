@@ -17,7 +17,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -270,6 +272,130 @@ struct Level {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Launch accounting: every kernel launch of the library goes through LAUNCH,
+// which counts it and, when timing is enabled for its id, brackets it with
+// CUDA events on the launching stream (process-wide, one host thread).
+// ---------------------------------------------------------------------------
+enum KernelId {
+  KI_ADD_BASIS,
+  KI_APPLY_DIRICHLET,
+  KI_ASSEMBLE_BSR,
+  KI_AXPBY,
+  KI_BACKSOLVE,
+  KI_BSR_SPMV,
+  KI_CELL_JACOBIAN,
+  KI_CELL_RESIDUAL,
+  KI_DENSE_APPLY,
+  KI_DENSE_FROM_BSR,
+  KI_DENSE_INVERT,
+  KI_DOTS_FINISH,
+  KI_DOTS_PARTIAL,
+  KI_FILL,
+  KI_GATHER_RESIDUAL,
+  KI_GIVENS,
+  KI_INIT_G,
+  KI_INTERP_STATE,
+  KI_PARAREAL_CORRECT,
+  KI_PROLONG_ADD,
+  KI_RESTRICT,
+  KI_SCALE,
+  KI_SUB_BASIS,
+  KI_VANKA_CELL,
+  KI_VANKA_GATHER,
+  KI_VANKA_SETUP,
+  KI_VANKA_SCATTER,
+  KI_BSR_TRANSPOSE,
+  KI_CELL_JACOBIAN_OLD,
+  KI_CELL_DRES_DLAME,
+  KI_GATHER_VECTOR,
+  KI_DRES_DVBAR,
+  KI_COUNT
+};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar"};
+
+struct Profiler {
+  unsigned long long mask = 0;
+  long long launches[KI_COUNT] = {};
+  long long total = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> rec_id;
+  std::vector<double> rec_work;
+  double pending_work = 0.0;
+  // launches replayed inside CUDA graphs: summed after every replay
+  double gms[KI_COUNT] = {}, gwork[KI_COUNT] = {};
+  long long gcnt[KI_COUNT] = {};
+  unsigned epoch = 1;   // bumped by fsi_profile_enable: graphs captured earlier are re-captured
+};
+Profiler g_prof;
+
+// A timed launch recorded while a CUDA graph is being captured.
+struct CapRec {
+  int id;
+  size_t ev;
+  double work_per_slice;
+};
+struct Capture {
+  bool on = false;
+  int n_act = 1;
+  std::vector<CapRec> recs;
+  long long launches[KI_COUNT] = {};
+};
+Capture g_cap;
+
+void prof_grow_pool(size_t need) {
+  while (g_prof.used + need > g_prof.pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      g_prof.pool.push_back(e);
+    }
+  }
+}
+
+inline void prof_pre(int id, cudaStream_t st) {
+  if (g_cap.on) {
+    g_cap.launches[id]++;
+  } else {
+    g_prof.launches[id]++;
+    g_prof.total++;
+  }
+  if (!(g_prof.mask >> id & 1ull)) return;
+  prof_grow_pool(2);
+  cudaEventRecord(g_prof.pool[g_prof.used], st);
+}
+inline void prof_post(int id, cudaStream_t st) {
+  if (!(g_prof.mask >> id & 1ull)) return;
+  cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
+  if (g_cap.on) {
+    g_cap.recs.push_back({id, g_prof.used, g_prof.pending_work / std::max(1, g_cap.n_act)});
+  } else {
+    g_prof.rec_id.push_back(id);
+    g_prof.rec_work.push_back(g_prof.pending_work);
+  }
+  g_prof.used += 2;
+}
+
+// LAUNCH_W also records the algorithmic FP64 flops of the launch.
+#define LAUNCH_W(work, id, kern, grid, block, smem, st, ...) \
+  do {                                                       \
+    g_prof.pending_work = (work);                            \
+    LAUNCH(id, kern, grid, block, smem, st, __VA_ARGS__);    \
+    g_prof.pending_work = 0.0;                               \
+  } while (0)
+
+#define LAUNCH(id, kern, grid, block, smem, st, ...) \
+  do {                                               \
+    prof_pre(id, st);                                \
+    kern<<<grid, block, smem, st>>>(__VA_ARGS__);    \
+    prof_post(id, st);                               \
+  } while (0)
+
+}  // namespace
+
 struct fsi_ctx {
   fsi_params prm{};
   Phys P{};
@@ -287,6 +413,16 @@ struct fsi_ctx {
   double* t_dev = nullptr;
   int n_act = 0;        // slices set in `active` (host mirror, for work accounting)
   int tip = -1;         // node at the top centre of the solid box (adjoint functional)
+  // CUDA graphs of one FGMRES iteration for small batches, keyed by
+  // (scalar size, batch, Krylov index); captured on an internal stream
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned epoch = 0;
+    std::vector<CapRec> recs;
+    long long launches[KI_COUNT] = {};
+  };
+  std::map<std::tuple<int, int, int>, Graph> graphs;
+  cudaStream_t cap_stream = nullptr;
   // adjoint workspace (one slice)
   double *adj_ck = nullptr, *adj_sb = nullptr, *adj_vec = nullptr, *adj_B = nullptr, *adj_Bt = nullptr;
   size_t adj_ck_len = 0, adj_sb_len = 0;
@@ -456,95 +592,6 @@ int upload_tables() {
 }
 
 
-// ---------------------------------------------------------------------------
-// Launch accounting: every kernel launch of the library goes through LAUNCH,
-// which counts it and, when timing is enabled for its id, brackets it with
-// CUDA events on the launching stream (process-wide, one host thread).
-// ---------------------------------------------------------------------------
-enum KernelId {
-  KI_ADD_BASIS,
-  KI_APPLY_DIRICHLET,
-  KI_ASSEMBLE_BSR,
-  KI_AXPBY,
-  KI_BACKSOLVE,
-  KI_BSR_SPMV,
-  KI_CELL_JACOBIAN,
-  KI_CELL_RESIDUAL,
-  KI_DENSE_APPLY,
-  KI_DENSE_FROM_BSR,
-  KI_DENSE_INVERT,
-  KI_DOTS_FINISH,
-  KI_DOTS_PARTIAL,
-  KI_FILL,
-  KI_GATHER_RESIDUAL,
-  KI_GIVENS,
-  KI_INIT_G,
-  KI_INTERP_STATE,
-  KI_PARAREAL_CORRECT,
-  KI_PROLONG_ADD,
-  KI_RESTRICT,
-  KI_SCALE,
-  KI_SUB_BASIS,
-  KI_VANKA_CELL,
-  KI_VANKA_GATHER,
-  KI_VANKA_SETUP,
-  KI_VANKA_SCATTER,
-  KI_BSR_TRANSPOSE,
-  KI_CELL_JACOBIAN_OLD,
-  KI_CELL_DRES_DLAME,
-  KI_GATHER_VECTOR,
-  KI_DRES_DVBAR,
-  KI_COUNT
-};
-const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar"};
-
-struct Profiler {
-  unsigned long long mask = 0;
-  long long launches[KI_COUNT] = {};
-  long long total = 0;
-  std::vector<cudaEvent_t> pool;
-  size_t used = 0;
-  std::vector<int> rec_id;
-  std::vector<double> rec_work;
-  double pending_work = 0.0;
-};
-Profiler g_prof;
-
-inline void prof_pre(int id, cudaStream_t st) {
-  g_prof.launches[id]++;
-  g_prof.total++;
-  if (!(g_prof.mask >> id & 1ull)) return;
-  if (g_prof.used + 2 > g_prof.pool.size()) {
-    for (int i = 0; i < 256; ++i) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      g_prof.pool.push_back(e);
-    }
-  }
-  cudaEventRecord(g_prof.pool[g_prof.used], st);
-}
-inline void prof_post(int id, cudaStream_t st) {
-  if (!(g_prof.mask >> id & 1ull)) return;
-  cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
-  g_prof.rec_id.push_back(id);
-  g_prof.rec_work.push_back(g_prof.pending_work);
-  g_prof.used += 2;
-}
-
-// LAUNCH_W also records the algorithmic FP64 flops of the launch.
-#define LAUNCH_W(work, id, kern, grid, block, smem, st, ...) \
-  do {                                                       \
-    g_prof.pending_work = (work);                            \
-    LAUNCH(id, kern, grid, block, smem, st, __VA_ARGS__);    \
-    g_prof.pending_work = 0.0;                               \
-  } while (0)
-
-#define LAUNCH(id, kern, grid, block, smem, st, ...) \
-  do {                                               \
-    prof_pre(id, st);                                \
-    kern<<<grid, block, smem, st>>>(__VA_ARGS__);    \
-    prof_post(id, st);                               \
-  } while (0)
 
 // ---------------------------------------------------------------------------
 // Batched building blocks
@@ -741,24 +788,73 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       c->n_act = g_nact = count_active(cyc);
       T* Vj = V + (size_t)j * n;
       T* Zj = Z + (size_t)j * n;
-      // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
-      CK(cudaMemcpy2DAsync(vin, n * sizeof(T), Vj, vsl * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
-      TRY(vcycle<T>(c, 0, S, vin, vout, c->active, st));
-      CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(T), vout, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, st));
-      // w = A Z_j
-      TRY((spmv<T, false>(L, S, A, vout, nullptr, c->active, w, st)));
-      // classical Gram-Schmidt, twice
-      TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol, m + 1, false, st));
-      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, V, n, vsl, c->hcol, m + 1, c->active, w, n);
-      TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol2, m + 1, false, st));
-      LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, j + 1, V, n, vsl, c->hcol2, m + 1, c->active, w, n);
-      LAUNCH(KI_AXPBY, (k_axpby<double, double>), (dim3(1, S)), 64, 0, st, j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
-      TRY(dots<T>(c, S, n, 1, w, 0, n, w, n, c->active, c->scal, 1, true, st));
-      LAUNCH(KI_SCALE, k_scale<T>, (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, w, n, c->scal, 1, true, c->active, V + (size_t)(j + 1) * n, vsl);
-      LAUNCH(KI_GIVENS, k_givens, (nblk(S, 64)), 64, 0, st, S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
-      TRY(launch_check());
+      // one Arnoldi step: device work only, so that it can be a CUDA graph
+      auto body = [&](cudaStream_t s2) -> int {
+        // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
+        CK(cudaMemcpy2DAsync(vin, n * sizeof(T), Vj, vsl * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, s2));
+        TRY(vcycle<T>(c, 0, S, vin, vout, c->active, s2));
+        CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(T), vout, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, s2));
+        // w = A Z_j
+        TRY((spmv<T, false>(L, S, A, vout, nullptr, c->active, w, s2)));
+        // classical Gram-Schmidt, twice
+        TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol, m + 1, false, s2));
+        LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, s2, (int)n, j + 1, V, n, vsl, c->hcol, m + 1, c->active, w, n);
+        TRY(dots<T>(c, S, n, j + 1, V, n, vsl, w, n, c->active, c->hcol2, m + 1, false, s2));
+        LAUNCH_W(2.0 * (j + 1) * (double)n * c->n_act, KI_SUB_BASIS, k_sub_basis<T>, (dim3(nblk(n, 256), S)), 256, 0, s2, (int)n, j + 1, V, n, vsl, c->hcol2, m + 1, c->active, w, n);
+        LAUNCH(KI_AXPBY, (k_axpby<double, double>), (dim3(1, S)), 64, 0, s2, j + 1, 1.0, c->hcol2, m + 1, 1.0, c->active, c->hcol, m + 1);
+        TRY(dots<T>(c, S, n, 1, w, 0, n, w, n, c->active, c->scal, 1, true, s2));
+        LAUNCH(KI_SCALE, k_scale<T>, (dim3(nblk(n, 256), S)), 256, 0, s2, (int)n, w, n, c->scal, 1, true, c->active, V + (size_t)(j + 1) * n, vsl);
+        LAUNCH(KI_GIVENS, k_givens, (nblk(S, 64)), 64, 0, s2, S, j, m, c->hcol, m + 1, c->scal, c->active, c->H, c->cs, c->sn, c->g, c->resid);
+        return launch_check();
+      };
+      fsi_ctx::Graph* replayed = nullptr;
+      if (S <= c->prm.graph_max_batch) {
+        fsi_ctx::Graph& ge = c->graphs[std::make_tuple((int)sizeof(T), S, j)];
+        if (!ge.exec || ge.epoch != g_prof.epoch) {
+          if (ge.exec) {
+            cudaGraphExecDestroy(ge.exec);
+            ge.exec = nullptr;
+          }
+          if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+          if (g_prof.mask) prof_grow_pool(4096);
+          g_cap = Capture{};
+          g_cap.on = true;
+          g_cap.n_act = c->n_act;
+          CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+          const int rc = body(c->cap_stream);
+          cudaGraph_t graph = nullptr;
+          const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+          g_cap.on = false;
+          if (rc != FSI_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != FSI_OK ? rc : fail(FSI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+          }
+          const cudaError_t ei = cudaGraphInstantiate(&ge.exec, graph, 0);
+          cudaGraphDestroy(graph);
+          if (ei != cudaSuccess) return fail(FSI_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+          ge.epoch = g_prof.epoch;
+          ge.recs = g_cap.recs;
+          for (int id = 0; id < KI_COUNT; ++id) ge.launches[id] = g_cap.launches[id];
+        }
+        CK(cudaGraphLaunch(ge.exec, st));
+        for (int id = 0; id < KI_COUNT; ++id) {
+          g_prof.launches[id] += ge.launches[id];
+          g_prof.total += ge.launches[id];
+        }
+        replayed = &ge;
+      } else {
+        TRY(body(st));
+      }
       CK(cudaMemcpyAsync(res.data(), c->resid, S * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
+      if (replayed)   // event times of timed kernels inside the graph, read before the next replay
+        for (const CapRec& r : replayed->recs) {
+          float e = 0.f;
+          CK(cudaEventElapsedTime(&e, g_prof.pool[r.ev], g_prof.pool[r.ev + 1]));
+          g_prof.gms[r.id] += e;
+          g_prof.gwork[r.id] += r.work_per_slice * c->n_act;
+          g_prof.gcnt[r.id] += 1;
+        }
       std::vector<uint8_t> fin(S, 0);
       bool any_fin = false, any_left = false;
       for (int s = 0; s < S; ++s) {
@@ -1121,6 +1217,9 @@ const char* fsi_last_error(void) { return g_err.c_str(); }
 
 void fsi_destroy(fsi_ctx* c) {
   if (!c) return;
+  for (auto& kv : c->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (double* p : {c->adj_ck, c->adj_sb, c->adj_vec, c->adj_B, c->adj_Bt})
     if (p) cudaFree(p);
   for (auto& L : c->lev)
@@ -1353,6 +1452,8 @@ int fsi_profile_enable(unsigned long long kernel_mask) {
   g_prof.used = 0;
   g_prof.rec_id.clear();
   g_prof.rec_work.clear();
+  for (int i = 0; i < KI_COUNT; ++i) g_prof.gms[i] = g_prof.gwork[i] = 0.0, g_prof.gcnt[i] = 0;
+  ++g_prof.epoch;
   return FSI_OK;
 }
 
@@ -1370,9 +1471,9 @@ int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
     work += g_prof.rec_work[r];
     ++cnt;
   }
-  *total_ms = ms;
-  *timed_launches = cnt;
-  *total_flops = work;
+  *total_ms = ms + g_prof.gms[kernel_id];
+  *timed_launches = cnt + g_prof.gcnt[kernel_id];
+  *total_flops = work + g_prof.gwork[kernel_id];
   return FSI_OK;
 }
 

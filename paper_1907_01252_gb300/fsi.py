@@ -36,7 +36,7 @@ class fsi_params(C.Structure):
                 ("mg_coarsest_max_dofs", C.c_int), ("mg_smooth", C.c_int), ("mg_omega", C.c_double),
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
-                ("precision", C.c_int), ("max_batch", C.c_int)]
+                ("graph_max_batch", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int)]
 
 
 class fsi_stats(C.Structure):
@@ -181,7 +181,7 @@ class Context:
                  m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
                  gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
                  mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
-                 mg_rebuild_every=4, precision=0, max_batch=max_batch)
+                 mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
         p.update(overrides)
         self.params = p
         self._params = fsi_params(**p)

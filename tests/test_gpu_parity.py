@@ -192,3 +192,20 @@ def test_multiplicative_smoother_step_matches_oracle():
         assert max(rel_field_errors(got[s], ref).values()) <= 1e-10
     Us, _ = ctx.fsi_theta_step(to_dev(U0[1:]), t0[1:], k, 0.5 + k)
     assert torch.equal(Us[0], Ub[1])
+
+
+def test_cuda_graph_replay_is_bitwise_identical():
+    """FGMRES iterations replayed from CUDA graphs (small batches) run the same
+    kernels in the same order as direct launches."""
+    w = wl.SMALL_16x4
+    mesh = oracle_mesh(w)
+    k = w.k_coarse
+    _, states = developed_states(w, mesh, 4, w.k_fine)
+    U0 = to_dev(np.stack([states[3], states[1]]))
+    out = []
+    for gmax in (0, 4):
+        ctx = ctx_for(w, 2, graph_max_batch=gmax)
+        U1, st = ctx.fsi_theta_step(U0, [0.1, 0.1], k, 1.0)
+        U2, _ = ctx.fsi_theta_step(U1, [0.1 + k, 0.1 + k], k, 1.0)   # replays the captured graphs
+        out.append(U2)
+    assert torch.equal(out[0], out[1])
