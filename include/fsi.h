@@ -102,11 +102,16 @@ typedef struct fsi_params {
   int graph_max_batch;     /* batches of at most this many slices run each FGMRES
                               iteration as one CUDA graph (captured once per batch
                               size and Krylov index); 0 disables graphs */
-  int precision;           /* 0: FP64 throughout. 1: the linear solver (FGMRES,
+  int precision;           /* 0: FP64 throughout. 1: the whole linear solver (FGMRES,
                               multigrid, Vanka, block-sparse operator) in FP32 inside
-                              the FP64 Newton loop, whose residual, J = det F and the
-                              Parareal correction stay FP64 (the Newton iteration is
-                              the FP64 refinement; inner tolerance >= 1e-6) */
+                              the FP64 Newton loop (inner tolerance >= 1e-6); the
+                              Newton refinement only contracts while cond(J) times the
+                              FP32 unit roundoff stays below one, which large coarse
+                              steps violate. 2: FP64 FGMRES on the FP64 Jacobian,
+                              preconditioned by the multigrid V-cycle in FP32 (Vanka
+                              inverses, transfers, level operators): GMRES-based
+                              refinement, as accurate as 0. In every mode the Newton
+                              residual, J = det F and the Parareal correction are FP64 */
   int max_batch;           /* most slices advanced in one call */
 } fsi_params;
 

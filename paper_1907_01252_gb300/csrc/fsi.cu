@@ -266,6 +266,7 @@ struct Level {
   double *A = nullptr;                        // block-sparse values
   double *cellbuf = nullptr, *r = nullptr, *x = nullptr, *b = nullptr;
   double *D = nullptr, *Dinv = nullptr;       // coarsest only
+  float* A32 = nullptr;                       // level 0, mixed precision: the preconditioner's FP32 copy
   int* perm = nullptr;
   bool coarsest = false;
 };
@@ -411,6 +412,7 @@ struct fsi_ctx {
   int *nv = nullptr, *status = nullptr;
   uint8_t *active = nullptr, *active2 = nullptr;
   double* t_dev = nullptr;
+  float *p_in = nullptr, *p_out = nullptr;   // FP32 preconditioner input / output (mixed precision)
   int n_act = 0;        // slices set in `active` (host mirror, for work accounting)
   int tip = -1;         // node at the top centre of the solid box (adjoint functional)
   // CUDA graphs of one FGMRES iteration for small batches, keyed by
@@ -489,6 +491,7 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
   if (!need_state) TRY(dalloc(L.owned, &L.Ke, (size_t)S * h.n_cells * 2025));
   else L.Ke = L.KV;
   TRY(dalloc(L.owned, &L.A, (size_t)S * h.nnzb * 25));
+  if (!need_state) TRY(dalloc(L.owned, &L.A32, (size_t)S * h.nnzb * 25));
   TRY(dalloc(L.owned, &L.cellbuf, (size_t)S * h.n_cells * 45));
   TRY(dalloc(L.owned, &L.r, S * L.n));
   TRY(dalloc(L.owned, &L.x, S * L.n));
@@ -609,14 +612,21 @@ int residual(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
   return launch_check();
 }
 
+// Mixed precision: FP64 Krylov solver with an FP32 multigrid preconditioner.
+template <typename T>
+bool mixed(const fsi_ctx* c) {
+  return sizeof(T) == sizeof(float) && c->prm.precision == 2;
+}
+
 // lps_scale = 1 on the finest level (the discretisation); coarse levels of the
 // preconditioner scale the stabilisation weight down (see mg_coarse_lps).
-// The element matrices are FP64; the assembled values are stored in T.
+// The tangent is FP64; the element contraction, the element matrices and the
+// assembled values are in T.
 template <typename T>
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, T* A, cudaStream_t st, double lps_scale = 1.0) {
-  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, k_cell_jacobian<false>, (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, L.Ke);
-  LAUNCH(KI_ASSEMBLE_BSR, k_assemble_bsr<T>, (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, A, 1.0);
+  LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, (k_cell_jacobian<false, T>), (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, reinterpret_cast<T*>(L.Ke));
+  LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<T, T>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.Ke), act, A, 1.0);
   return launch_check();
 }
 
@@ -660,7 +670,14 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
       Uol = L.Uold;
     }
     T* A = reinterpret_cast<T*>(L.A);
-    TRY(jacobian<T>(c, L, S, Ul, Uol, k, theta, act, A, st, std::pow(c->prm.mg_coarse_lps, l)));
+    if (l == 0 && mixed<T>(c)) {
+      // FP64 operator for the Krylov solver, FP32 copy for the preconditioner
+      TRY(jacobian<double>(c, L, S, Ul, Uol, k, theta, act, L.A, st));
+      LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<float, double>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, L.Ke, act, L.A32, 1.0);
+      A = reinterpret_cast<T*>(L.A32);
+    } else {
+      TRY(jacobian<T>(c, L, S, Ul, Uol, k, theta, act, A, st, std::pow(c->prm.mg_coarse_lps, l)));
+    }
     if (transpose) {   // the hierarchy of the transposed operator (adjoint solves, FP64 only)
       double* Ad = reinterpret_cast<double*>(A);
       LAUNCH(KI_BSR_TRANSPOSE, k_bsr_transpose, (dim3(nblk((size_t)L.h.nnzb * 25, 256), S)), 256, 0, st, L.h.nnzb, L.blk_t, Ad, act, L.Ke);
@@ -684,7 +701,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
 template <typename T>
 int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaStream_t st) {
   Level& L = c->lev[l];
-  const T* A = reinterpret_cast<const T*>(L.A);
+  const T* A = (l == 0 && mixed<T>(c)) ? reinterpret_cast<const T*>(L.A32) : reinterpret_cast<const T*>(L.A);
   T* r = reinterpret_cast<T*>(L.r);
   T* cellbuf = reinterpret_cast<T*>(L.cellbuf);
   if (L.coarsest) {
@@ -736,7 +753,7 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
 // FGMRES(m) with multigrid right preconditioning: solve A x = b per active
 // slice to ||b - A x|| <= rtol ||b||, vectors and operator in T (the
 // Hessenberg matrix and the rotations are kept in FP64). x is overwritten.
-template <typename T>
+template <typename T, typename TP = T>
 int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rtol, fsi_stats* stats,
            cudaStream_t st) {
   Level& L = c->lev[0];
@@ -792,7 +809,15 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       auto body = [&](cudaStream_t s2) -> int {
         // Z_j = M^{-1} V_j (the V-cycle works on contiguous [S][n] buffers)
         CK(cudaMemcpy2DAsync(vin, n * sizeof(T), Vj, vsl * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, s2));
-        TRY(vcycle<T>(c, 0, S, vin, vout, c->active, s2));
+        if (sizeof(TP) == sizeof(T)) {
+          TRY(vcycle<TP>(c, 0, S, reinterpret_cast<const TP*>(vin), reinterpret_cast<TP*>(vout), c->active, s2));
+        } else {   // preconditioner in TP: convert in and out
+          TP* pin = reinterpret_cast<TP*>(c->p_in);
+          TP* pout = reinterpret_cast<TP*>(c->p_out);
+          LAUNCH(KI_AXPBY, (k_axpby<T, TP>), (dim3(nblk(n, 256), S)), 256, 0, s2, (int)n, 1.0, vin, n, 0.0, c->active, pin, n);
+          TRY(vcycle<TP>(c, 0, S, pin, pout, c->active, s2));
+          LAUNCH(KI_AXPBY, (k_axpby<TP, T>), (dim3(nblk(n, 256), S)), 256, 0, s2, (int)n, 1.0, pout, n, 0.0, c->active, vout, n);
+        }
         CK(cudaMemcpy2DAsync(Zj, zsl * sizeof(T), vout, n * sizeof(T), n * sizeof(T), S, cudaMemcpyDeviceToDevice, s2));
         // w = A Z_j
         TRY((spmv<T, false>(L, S, A, vout, nullptr, c->active, w, s2)));
@@ -809,7 +834,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       };
       fsi_ctx::Graph* replayed = nullptr;
       if (S <= c->prm.graph_max_batch) {
-        fsi_ctx::Graph& ge = c->graphs[std::make_tuple((int)sizeof(T), S, j)];
+        fsi_ctx::Graph& ge = c->graphs[std::make_tuple((int)(sizeof(T) * 16 + sizeof(TP)), S, j)];
         if (!ge.exec || ge.epoch != g_prof.epoch) {
           if (ge.exec) {
             cudaGraphExecDestroy(ge.exec);
@@ -898,7 +923,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
 // Newton correction for the active slices: build (or update) the
 // preconditioner and solve J delta = -R with the linear solver in T; the
 // result is added to the FP64 iterate.
-template <typename T>
+template <typename T, typename TP = T>
 int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reuse, bool hierarchy_valid,
                       double rtol, fsi_stats* stats, cudaStream_t st) {
   Level& L = c->lev[0];
@@ -909,11 +934,11 @@ int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reu
   if (keep_all)  // exact Jacobian for the Krylov operator; the multigrid hierarchy is kept
     TRY(jacobian<T>(c, L, S, c->Uit, c->Uold, k, theta, c->active, reinterpret_cast<T*>(L.A), st));
   else
-    TRY(mg_setup<T>(c, S, c->Uit, c->Uold, k, theta, c->active, st, it > 0 && reuse == 1));
+    TRY(mg_setup<TP>(c, S, c->Uit, c->Uold, k, theta, c->active, st, it > 0 && reuse == 1));
   // right-hand side -R in T (R itself is scratch inside the solver)
   LAUNCH(KI_AXPBY, (k_axpby<double, T>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, b, n);
   TRY(launch_check());
-  const int rc = fgmres<T>(c, S, b, x, c->active, rtol, stats, st);
+  const int rc = fgmres<T, TP>(c, S, b, x, c->active, rtol, stats, st);
   if (rc != FSI_OK && rc != FSI_EGMRES) return rc;
   LAUNCH(KI_AXPBY, (k_axpby<T, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 1.0, x, n, 1.0, c->active, c->Uit, n);
   TRY(launch_check());
@@ -977,11 +1002,15 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     c->n_act = g_nact = count_active(act);
     // FP64 throughout, or the FP32 linear solver inside the FP64 Newton loop
     // (FP32 cannot reach FP64 tolerances: its relative tolerance is >= 1e-6)
-    const int rc = c->prm.precision == 1
-                       ? newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid,
-                                                  std::max(c->prm.gmres_rtol, 1e-6), stats, st)
-                       : newton_correction<double>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol,
-                                                   stats, st);
+    int rc;
+    if (c->prm.precision == 1)        // all-FP32 linear solver (inner tolerance >= 1e-6)
+      rc = newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid, std::max(c->prm.gmres_rtol, 1e-6),
+                                    stats, st);
+    else if (c->prm.precision == 2)   // FP64 FGMRES, FP32 multigrid preconditioner
+      rc = newton_correction<double, float>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol, stats,
+                                            st);
+    else
+      rc = newton_correction<double>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol, stats, st);
     CK(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int s = 0; s < S; ++s)
@@ -1052,7 +1081,7 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
     return fail(FSI_EINVAL, "bad time or batch parameters");
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
     return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
-  if (p->precision != 0 && p->precision != 1) return fail(FSI_EINVAL, "precision must be 0 (FP64) or 1 (FP32 solver)");
+  if (p->precision < 0 || p->precision > 2) return fail(FSI_EINVAL, "precision must be 0, 1 or 2");
   if (p->mg_smoother != 0 && p->mg_smoother != 1) return fail(FSI_EINVAL, "mg_smoother must be 0 or 1");
   if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5 || !(p->mg_coarse_lps > 0))
     return fail(FSI_EINVAL, "bad multigrid parameters");
@@ -1288,7 +1317,8 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
       (rc = A(&c->g, S * (m + 1))) || (rc = A(&c->y, S * m)) || (rc = A(&c->hcol, S * (m + 1))) ||
       (rc = A(&c->hcol2, S * (m + 1))) || (rc = A(&c->scal, S)) || (rc = A(&c->resid, S)) ||
       (rc = A(&c->partial, S * nblk(n, RED_CHUNK) * 64)) || (rc = A(&c->nv, S)) || (rc = A(&c->status, S)) ||
-      (rc = A(&c->active, S)) || (rc = A(&c->active2, S)) || (rc = A(&c->t_dev, S)))
+      (rc = A(&c->active, S)) || (rc = A(&c->active2, S)) || (rc = A(&c->t_dev, S)) ||
+      (rc = A(&c->p_in, S * n)) || (rc = A(&c->p_out, S * n)))
     return cleanup(rc);
   if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
   *out = c;

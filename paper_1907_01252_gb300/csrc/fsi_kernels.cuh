@@ -262,12 +262,14 @@ __device__ inline bool jac_old_block_nonzero(bool solid, int ci, int cj) {
   return cj == ci || cj == ci - 2;
 }
 
-template <bool OLD>
+// TC: type of the B^T D B contraction and of the element matrices (double, or
+// float for the FP32 linear solver); the tangent D is always computed in FP64.
+template <bool OLD, typename TC = double>
 __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
                                                                const double* __restrict__ Uold, size_t stride,
                                                                double k, double theta, double lps_scale,
                                                                const uint8_t* __restrict__ active,
-                                                               double* __restrict__ Ke) {
+                                                               TC* __restrict__ Ke) {
   const int s = blockIdx.y;
   const int cell = blockIdx.x;
   if (!active[s]) return;
@@ -368,24 +370,24 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
   //   E[(ci,a)][(j,cj)] = w_q sum_b D_q[(ci,a)][(cj,b)] B_b(j,q)
   //   K[(i,ci)][(j,cj)] += sum_a B_a(i,q) E[(ci,a)][(j,cj)]
   // Field blocks (ci, cj) that vanish for the cell's material are skipped.
-  __shared__ double sE[15][45];
-  __shared__ double sB[3][9];
+  __shared__ TC sE[15][45];
+  __shared__ TC sB[3][9];
   constexpr int PER = (2025 + JAC_THREADS - 1) / JAC_THREADS;
-  double acc[PER];
+  TC acc[PER];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) acc[r] = 0.0;
+  for (int r = 0; r < PER; ++r) acc[r] = 0;
   for (int q = 0; q < 9; ++q) {
     const double wq = c_wq[q] * area;
     if (tid < 9) {
-      sB[0][tid] = c_phi[q][tid];
-      sB[1][tid] = c_dps[q][tid] * ihx;
-      sB[2][tid] = c_dpt[q][tid] * ihy;
+      sB[0][tid] = (TC)c_phi[q][tid];
+      sB[1][tid] = (TC)(c_dps[q][tid] * ihx);
+      sB[2][tid] = (TC)(c_dpt[q][tid] * ihy);
     }
     __syncthreads();
     for (int e = tid; e < 15 * 45; e += JAC_THREADS) {
       const int slot = e / 45, col = e % 45, j = col / 5, cj = col % 5;
       const double* Dr = sD[q][slot] + cj * 3;
-      sE[slot][col] = wq * (Dr[0] * sB[0][j] + Dr[1] * sB[1][j] + Dr[2] * sB[2][j]);
+      sE[slot][col] = (TC)(wq * (Dr[0] * c_phi[q][j] + Dr[1] * (c_dps[q][j] * ihx) + Dr[2] * (c_dpt[q][j] * ihy)));
     }
     __syncthreads();
 #pragma unroll
@@ -400,14 +402,14 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     }
     __syncthreads();
   }
-  double* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
+  TC* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int e = tid + r * JAC_THREADS;
     if (e >= 2025) continue;
     const int row = e / 45, col = e % 45;
     const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
-    double v = acc[r];
+    double v = (double)acc[r];
     if (!OLD && !solid && ci == 4 && cj == 4)
       v += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
     if (OLD && !solid && ci == 4 && cj < 2) {
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
         v += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
       }
     }
-    out[e] = v;
+    out[e] = (TC)v;
   }
 }
 
@@ -433,8 +435,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
 // fixed-order sum over the cells sharing both nodes, identity rows replaced.
 // identity_value: 1 for dR/dU (identity rows), 0 for dR/dU_old (those rows do
 // not depend on the old state).
-template <typename T>
-__global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const uint8_t* __restrict__ active,
+template <typename T, typename TK = double>
+__global__ void k_assemble_bsr(DevMesh m, const TK* __restrict__ Ke, const uint8_t* __restrict__ active,
                                T* __restrict__ A, double identity_value) {
   const int s = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,8 +453,8 @@ __global__ void k_assemble_bsr(DevMesh m, const double* __restrict__ Ke, const u
       if (code < 0) break;
       const int cell = code / 81, li = (code / 9) % 9, lj = code % 9;
       if (!row_takes(m.cell_flags[cell], nf, ci)) continue;
-      const double* src = Ke + ((size_t)s * m.n_cells + cell) * 2025 + (li * 5 + ci) * 45 + lj * 5;
-      for (int cj = 0; cj < 5; ++cj) acc[cj] += src[cj];
+      const TK* src = Ke + ((size_t)s * m.n_cells + cell) * 2025 + (li * 5 + ci) * 45 + lj * 5;
+      for (int cj = 0; cj < 5; ++cj) acc[cj] += (double)src[cj];
     }
   }
   T* dst = A + ((size_t)s * m.nnzb + b) * 25 + ci * 5;

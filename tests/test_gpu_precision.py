@@ -1,9 +1,11 @@
-"""Precision variant: FP32 linear solver (FGMRES, multigrid, Vanka, operator)
-inside the FP64 Newton loop, against the FP64 oracle through the C ABI.
+"""Precision variants against the FP64 oracle through the C ABI.
 
-The Newton residual stays FP64, so the converged step solves the same
-discrete equations: the target is <= 1e-8 relative error in the bar-tip
-displacement (and per field) against the FP64 oracle.
+precision = 1: the whole linear solver (FGMRES, multigrid, Vanka, operator) in
+FP32 inside the FP64 Newton loop; precision = 2: FP64 FGMRES on the FP64
+Jacobian with the multigrid preconditioner in FP32. The Newton residual stays
+FP64 in both, so the converged step solves the same discrete equations: the
+target is <= 1e-8 relative error in the bar-tip displacement (and per field);
+mode 2 keeps the FP64 tolerances and is held to the FP64 parity bar (1e-10).
 """
 import numpy as np
 import pytest
@@ -38,7 +40,11 @@ def tip_node(mesh):
     return i
 
 
-def test_fp32_solver_fine_propagator_matches_fp64_oracle():
+TOL = {1: 1e-8, 2: 1e-10}
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_solver_fine_propagator_matches_fp64_oracle(precision):
     from paper_1907_01252_gb300 import fsi
     w = wl.Workload("p32", nx=16, ny=4, T=0.5, n_slices=4, m_fine=4)
     mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
@@ -46,7 +52,7 @@ def test_fp32_solver_fine_propagator_matches_fp64_oracle():
     dt = w.T / w.n_slices
     U0 = np.zeros((2, mesh.n_nodes, 5))
     U0[1] = model.propagate(U0[0], 0.0, dt, 8)
-    ctx = fsi.Context(w, max_batch=2, precision=1)
+    ctx = fsi.Context(w, max_batch=2, precision=precision)
     dev = torch.tensor(U0.reshape(2, -1), dtype=torch.float64, device="cuda:0")
     Uf, stats = ctx.fsi_fine(dev, [0.0, dt])
     got = Uf.cpu().numpy().reshape(2, -1, 5)
@@ -54,23 +60,24 @@ def test_fp32_solver_fine_propagator_matches_fp64_oracle():
     for s in range(2):
         ref = model.propagate(U0[s], s * dt, (s + 1) * dt, w.m_fine)
         for name, sl in FIELDS.items():
-            assert rel(got[s], ref, sl) <= 1e-8, (s, name)
-        assert np.linalg.norm(got[s][tip, 2:4] - ref[tip, 2:4]) <= 1e-8 * np.linalg.norm(ref[tip, 2:4])
+            assert rel(got[s], ref, sl) <= TOL[precision], (s, name)
+        assert np.linalg.norm(got[s][tip, 2:4] - ref[tip, 2:4]) <= TOL[precision] * np.linalg.norm(ref[tip, 2:4])
     # batched equals single-slice runs bit for bit in FP32 too
     Us, _ = ctx.fsi_fine(dev[1:2].contiguous(), [dt])
     assert torch.equal(Us[0], Uf[1])
 
 
-def test_fp32_solver_coarse_step_matches_fp64_oracle():
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_solver_coarse_step_matches_fp64_oracle(precision):
     from paper_1907_01252_gb300 import fsi
     w = wl.SMALL_16x4
     mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
     model = of.FSIModel(mesh, w.material)
     U0 = model.propagate(np.zeros((mesh.n_nodes, 5)), 0.0, 0.1, 4)
     K = w.k_coarse
-    ctx = fsi.Context(w, max_batch=1, precision=1)
+    ctx = fsi.Context(w, max_batch=1, precision=precision)
     U1, stats = ctx.fsi_theta_step(torch.tensor(U0.reshape(1, -1), device="cuda:0"), [0.1], K, 1.0)
     got = U1.cpu().numpy().reshape(-1, 5)
     ref = model.step(U0, 0.1, K, 1.0)
     for name, sl in FIELDS.items():
-        assert rel(got, ref, sl) <= 1e-8, name
+        assert rel(got, ref, sl) <= TOL[precision], name
