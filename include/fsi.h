@@ -79,6 +79,11 @@ typedef struct fsi_params {
   int gmres_restart;       /* FGMRES restart length m */
   int gmres_maxit;         /* total FGMRES iterations per linear solve */
   double gmres_rtol;       /* relative residual reduction per linear solve */
+  double gmres_rtol_first; /* with newton_eta > 0: reduction of the first Newton
+                              correction of a step */
+  double newton_eta;       /* > 0: later Newton corrections stop once the linear
+                              residual is newton_eta x the Newton target (inexact
+                              Newton, per slice); 0: every solve to gmres_rtol */
   int mg_coarsest_max_dofs;/* coarsen the multigrid hierarchy until <= this */
   int mg_smooth;           /* Vanka sweeps before and after the coarse correction */
   double mg_omega;         /* Vanka damping */

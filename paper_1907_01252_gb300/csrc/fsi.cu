@@ -753,9 +753,10 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
 // FGMRES(m) with multigrid right preconditioning: solve A x = b per active
 // slice to ||b - A x|| <= rtol ||b||, vectors and operator in T (the
 // Hessenberg matrix and the rotations are kept in FP64). x is overwritten.
+// abs_target (optional, host [S]): stop a slice once ||b - A x|| <= max(abs_target[s], rtol ||b||).
 template <typename T, typename TP = T>
 int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rtol, fsi_stats* stats,
-           cudaStream_t st) {
+           cudaStream_t st, const double* abs_target = nullptr) {
   Level& L = c->lev[0];
   const size_t n = L.n;
   const int m = c->m;
@@ -776,6 +777,8 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
   CK(cudaMemcpyAsync(bnorm.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   int status = FSI_OK;
+  // the caller's mask, restored on exit (the cycles below narrow c->active)
+  const std::vector<uint8_t> act_entry = act;
   for (int s = 0; s < S; ++s)
     if (act[s] && !(bnorm[s] > 0.0)) {
       if (!std::isfinite(bnorm[s])) status = FSI_ENAN;
@@ -885,7 +888,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       for (int s = 0; s < S; ++s) {
         if (!cyc[s]) continue;
         ++its[s];
-        const bool conv = res[s] <= rtol * bnorm[s];
+        const bool conv = res[s] <= std::max(rtol * bnorm[s], abs_target ? abs_target[s] : 0.0);
         const bool bad = !std::isfinite(res[s]);
         if (conv || bad || j == m - 1 || its[s] >= c->prm.gmres_maxit) {
           fin[s] = 1;
@@ -917,6 +920,8 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       stats->max_gmres = std::max(stats->max_gmres, its[s]);
     }
   }
+  CK(cudaMemcpyAsync(c->active, act_entry.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act_entry);
   return status;
 }
 
@@ -925,7 +930,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
 // result is added to the FP64 iterate.
 template <typename T, typename TP = T>
 int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reuse, bool hierarchy_valid,
-                      double rtol, fsi_stats* stats, cudaStream_t st) {
+                      double rtol, fsi_stats* stats, cudaStream_t st, const double* abs_target) {
   Level& L = c->lev[0];
   const size_t n = L.n;
   T* b = reinterpret_cast<T*>(L.b);
@@ -938,7 +943,7 @@ int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reu
   // right-hand side -R in T (R itself is scratch inside the solver)
   LAUNCH(KI_AXPBY, (k_axpby<double, T>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, b, n);
   TRY(launch_check());
-  const int rc = fgmres<T, TP>(c, S, b, x, c->active, rtol, stats, st);
+  const int rc = fgmres<T, TP>(c, S, b, x, c->active, rtol, stats, st, abs_target);
   if (rc != FSI_OK && rc != FSI_EGMRES) return rc;
   LAUNCH(KI_AXPBY, (k_axpby<T, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, 1.0, x, n, 1.0, c->active, c->Uit, n);
   TRY(launch_check());
@@ -1000,17 +1005,30 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     if (!any) break;
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
+    // Inexact Newton forcing terms, per slice from its own residual history: the
+    // first correction is solved to gmres_rtol_first, later ones until the
+    // linearised residual is newton_eta times the Newton target (never looser
+    // than 1e-2, never tighter than gmres_rtol).
+    std::vector<double> target(S, 0.0);
+    double rtol_now = c->prm.gmres_rtol;
+    if (c->prm.newton_eta > 0.0) {
+      rtol_now = it == 0 ? std::max(c->prm.gmres_rtol, c->prm.gmres_rtol_first) : c->prm.gmres_rtol;
+      if (it > 0)
+        for (int s = 0; s < S; ++s)
+          target[s] = std::min(1e-2 * nr[s], c->prm.newton_eta * c->prm.newton_tol * std::max(r0[s], 1.0));
+    }
     // FP64 throughout, or the FP32 linear solver inside the FP64 Newton loop
     // (FP32 cannot reach FP64 tolerances: its relative tolerance is >= 1e-6)
     int rc;
     if (c->prm.precision == 1)        // all-FP32 linear solver (inner tolerance >= 1e-6)
-      rc = newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid, std::max(c->prm.gmres_rtol, 1e-6),
-                                    stats, st);
+      rc = newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid, std::max(rtol_now, 1e-6),
+                                    stats, st, target.data());
     else if (c->prm.precision == 2)   // FP64 FGMRES, FP32 multigrid preconditioner
-      rc = newton_correction<double, float>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol, stats,
-                                            st);
+      rc = newton_correction<double, float>(c, S, k, theta, it, reuse, hierarchy_valid, rtol_now, stats, st,
+                                            target.data());
     else
-      rc = newton_correction<double>(c, S, k, theta, it, reuse, hierarchy_valid, c->prm.gmres_rtol, stats, st);
+      rc = newton_correction<double>(c, S, k, theta, it, reuse, hierarchy_valid, rtol_now, stats, st,
+                                     target.data());
     CK(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int s = 0; s < S; ++s)

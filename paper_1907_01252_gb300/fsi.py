@@ -33,6 +33,7 @@ class fsi_params(C.Structure):
                 ("alpha0", C.c_double), ("T", C.c_double), ("n_slices", C.c_int), ("m_fine", C.c_int),
                 ("m_coarse", C.c_int), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int), ("gmres_rtol", C.c_double),
+                ("gmres_rtol_first", C.c_double), ("newton_eta", C.c_double),
                 ("mg_coarsest_max_dofs", C.c_int), ("mg_smooth", C.c_int), ("mg_omega", C.c_double),
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
@@ -180,6 +181,7 @@ class Context:
                  ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
                  m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
                  gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
+                 gmres_rtol_first=1e-6, newton_eta=0.0,
                  mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
                  mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
         p.update(overrides)

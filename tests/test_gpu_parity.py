@@ -136,6 +136,27 @@ def test_theta_step_matches_oracle_and_batch_is_bitwise_serial():
     assert stats["max_gmres"] < 200
 
 
+def test_batched_slices_with_different_krylov_counts_match_solo_runs():
+    """Slices of one batch whose FGMRES solves end at different iterations:
+    every slice keeps its own Newton correction, so the batch needs exactly the
+    Newton and FGMRES iterations of the solo runs and returns their bits."""
+    w = wl.SMALL_16x4
+    ctx = ctx_for(w, 2)
+    K = w.k_coarse
+    U = torch.zeros((1, ctx.n_dofs), dtype=torch.float64, device=DEV)
+    for i in range(4):                       # a developed state at t = 4K
+        U, _ = ctx.fsi_coarse(U, [i * K])
+    U0 = torch.cat([torch.zeros_like(U), U]).contiguous()
+    t0 = [0.0, 4 * K]
+    solo = [ctx.fsi_theta_step(U0[s:s + 1].contiguous(), [t0[s]], K, 1.0) for s in range(2)]
+    assert solo[0][1]["gmres_iters"] != solo[1][1]["gmres_iters"]
+    Ub, stats = ctx.fsi_theta_step(U0, t0, K, 1.0)
+    for key in ("newton_iters", "gmres_iters"):
+        assert stats[key] == solo[0][1][key] + solo[1][1][key], key
+    for s in range(2):
+        assert torch.equal(Ub[s], solo[s][0][0])
+
+
 def test_fine_and_coarse_propagators_match_oracle():
     w = wl.Workload("prop", nx=16, ny=4, T=0.5, n_slices=4, m_fine=4)
     mesh = oracle_mesh(w)
