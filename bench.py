@@ -329,6 +329,9 @@ def main():
                            "step": "parareal_iterate with 1 iteration: coarse predictor sweep + batched fine "
                                    "sweep of all slices + corrected coarse sweep",
                            "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
+                           "solver": {"newton_tol": w.newton_tol, "newton_eta": w.newton_eta,
+                                      "gmres_rtol_first": w.gmres_rtol_first, "gmres_rtol": w.gmres_rtol,
+                                      "gmres_restart": w.gmres_restart},
                            "serial_gpu_fine_steps_per_s": serial_rate,
                            "batched_vs_serial": value / serial_rate if serial_rate else None,
                            "newton_fine": st["fine"], "newton_coarse": st["coarse"]},

@@ -324,6 +324,7 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<int> rec_id;
+  std::vector<size_t> rec_ev;   // first of the record's two pool events
   std::vector<double> rec_work;
   double pending_work = 0.0;
   // launches replayed inside CUDA graphs: summed after every replay
@@ -357,6 +358,15 @@ void prof_grow_pool(size_t need) {
   }
 }
 
+// Inside a stream capture a plain event record only orders streams; the
+// external flag makes it an event-record node that replays can be timed by.
+inline void prof_record(cudaEvent_t e, cudaStream_t st) {
+  if (g_cap.on)
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, st);
+}
+
 inline void prof_pre(int id, cudaStream_t st) {
   if (g_cap.on) {
     g_cap.launches[id]++;
@@ -366,15 +376,16 @@ inline void prof_pre(int id, cudaStream_t st) {
   }
   if (!(g_prof.mask >> id & 1ull)) return;
   prof_grow_pool(2);
-  cudaEventRecord(g_prof.pool[g_prof.used], st);
+  prof_record(g_prof.pool[g_prof.used], st);
 }
 inline void prof_post(int id, cudaStream_t st) {
   if (!(g_prof.mask >> id & 1ull)) return;
-  cudaEventRecord(g_prof.pool[g_prof.used + 1], st);
+  prof_record(g_prof.pool[g_prof.used + 1], st);
   if (g_cap.on) {
     g_cap.recs.push_back({id, g_prof.used, g_prof.pending_work / std::max(1, g_cap.n_act)});
   } else {
     g_prof.rec_id.push_back(id);
+    g_prof.rec_ev.push_back(g_prof.used);
     g_prof.rec_work.push_back(g_prof.pending_work);
   }
   g_prof.used += 2;
@@ -878,7 +889,10 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       if (replayed)   // event times of timed kernels inside the graph, read before the next replay
         for (const CapRec& r : replayed->recs) {
           float e = 0.f;
-          CK(cudaEventElapsedTime(&e, g_prof.pool[r.ev], g_prof.pool[r.ev + 1]));
+          if (cudaEventElapsedTime(&e, g_prof.pool[r.ev], g_prof.pool[r.ev + 1]) != cudaSuccess) {
+            (void)cudaGetLastError();   // timing is best effort: never fails the solve
+            continue;
+          }
           g_prof.gms[r.id] += e;
           g_prof.gwork[r.id] += r.work_per_slice * c->n_act;
           g_prof.gcnt[r.id] += 1;
@@ -1036,7 +1050,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
         status = FSI_EJAC;
         act[s] = 0;
       }
-    if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed");
+    if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed: " + g_err);
     if (rc == FSI_EGMRES) status = FSI_EGMRES;
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1100,6 +1114,10 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
     return fail(FSI_EINVAL, "bad solver parameters (restart must be 1..63)");
   if (p->precision < 0 || p->precision > 2) return fail(FSI_EINVAL, "precision must be 0, 1 or 2");
+  if (!(p->gmres_rtol > 0.0 && p->gmres_rtol < 1.0)) return fail(FSI_EINVAL, "gmres_rtol must lie in (0, 1)");
+  if (!(p->newton_eta >= 0.0 && p->newton_eta < 1.0)) return fail(FSI_EINVAL, "newton_eta must lie in [0, 1)");
+  if (p->newton_eta > 0.0 && !(p->gmres_rtol_first > 0.0 && p->gmres_rtol_first < 1.0))
+    return fail(FSI_EINVAL, "gmres_rtol_first must lie in (0, 1)");
   if (p->mg_smoother != 0 && p->mg_smoother != 1) return fail(FSI_EINVAL, "mg_smoother must be 0 or 1");
   if (p->mg_smooth < 1 || !(p->mg_omega > 0) || p->mg_coarsest_max_dofs < 5 || !(p->mg_coarse_lps > 0))
     return fail(FSI_EINVAL, "bad multigrid parameters");
@@ -1499,6 +1517,7 @@ int fsi_profile_enable(unsigned long long kernel_mask) {
   g_prof.mask = kernel_mask;
   g_prof.used = 0;
   g_prof.rec_id.clear();
+  g_prof.rec_ev.clear();
   g_prof.rec_work.clear();
   for (int i = 0; i < KI_COUNT; ++i) g_prof.gms[i] = g_prof.gwork[i] = 0.0, g_prof.gcnt[i] = 0;
   ++g_prof.epoch;
@@ -1512,9 +1531,10 @@ int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
   long long cnt = 0;
   for (size_t r = 0; r < g_prof.rec_id.size(); ++r) {
     if (g_prof.rec_id[r] != kernel_id) continue;
-    CK(cudaEventSynchronize(g_prof.pool[2 * r + 1]));
+    const size_t ev = g_prof.rec_ev[r];
+    CK(cudaEventSynchronize(g_prof.pool[ev + 1]));
     float e = 0.f;
-    CK(cudaEventElapsedTime(&e, g_prof.pool[2 * r], g_prof.pool[2 * r + 1]));
+    CK(cudaEventElapsedTime(&e, g_prof.pool[ev], g_prof.pool[ev + 1]));
     ms += e;
     work += g_prof.rec_work[r];
     ++cnt;

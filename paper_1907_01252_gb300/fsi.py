@@ -181,7 +181,7 @@ class Context:
                  ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
                  m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
                  gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
-                 gmres_rtol_first=1e-6, newton_eta=0.0,
+                 gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
                  mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
                  mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
         p.update(overrides)

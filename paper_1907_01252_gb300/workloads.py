@@ -66,6 +66,10 @@ class Workload:
     gmres_restart: int = 50
     gmres_maxit: int = 2000
     gmres_rtol: float = 1e-12
+    # inexact Newton: first correction of a step to 1e-6, later ones until the
+    # linear residual is 1e-3 x the Newton target (0 disables: every solve to gmres_rtol)
+    gmres_rtol_first: float = 1e-6
+    newton_eta: float = 1e-3
     parareal_tol: float = 1e-8
     material: Material = Material()
     with_solid: bool = True

@@ -74,3 +74,5 @@ def test_bad_sizes_are_rejected():
         fsi.Context(W, max_batch=0)
     with pytest.raises(fsi.FsiError):
         fsi.Context(W, max_batch=1, gmres_restart=100)
+    with pytest.raises(fsi.FsiError):
+        fsi.Context(W, max_batch=1, newton_eta=1.5)

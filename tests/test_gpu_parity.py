@@ -157,6 +157,28 @@ def test_batched_slices_with_different_krylov_counts_match_solo_runs():
         assert torch.equal(Ub[s], solo[s][0][0])
 
 
+def test_inexact_newton_meets_the_parity_bar_with_fewer_krylov_iterations():
+    """Inexact Newton (the default forcing) against every solve to gmres_rtol:
+    both within 1e-10 of the oracle step, the inexact one with fewer FGMRES
+    iterations and the same Newton iteration count."""
+    w = wl.SMALL_16x4
+    mesh = oracle_mesh(w)
+    k = w.k_fine
+    model, states = developed_states(w, mesh, 12, k)
+    U0, t0, th = states[11], 12 * k, 0.5 + k
+    ref = model.step(U0, t0, k, th)
+    out = {}
+    for eta in (0.0, w.newton_eta):
+        ctx = ctx_for(w, 1, newton_eta=eta)
+        U1, st = ctx.fsi_theta_step(to_dev(U0[None]), [t0], k, th)
+        errs = rel_field_errors(U1.cpu().numpy().reshape(-1, 5), ref)
+        assert max(errs.values()) <= 1e-10, (eta, errs)
+        out[eta] = st
+    assert w.newton_eta > 0
+    assert out[w.newton_eta]["gmres_iters"] < out[0.0]["gmres_iters"]
+    assert out[w.newton_eta]["newton_iters"] == out[0.0]["newton_iters"]
+
+
 def test_fine_and_coarse_propagators_match_oracle():
     w = wl.Workload("prop", nx=16, ny=4, T=0.5, n_slices=4, m_fine=4)
     mesh = oracle_mesh(w)
