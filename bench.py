@@ -17,6 +17,13 @@ a Parareal pass), --unit coarse_step one single-slice coarse (theta = 1) step
 as in the sequential sweep, and --kernel-table prints the per-kernel
 CUDA-event times of the last warm-up step to stderr.
 
+--unit batch measures the batch runner instead: the first --instances
+problems of the seeded uneven batch (meshes 64x16 .. 192x48, random solid
+shear modulus and inflow, 16 .. 32 slices of 16 fine steps over T = 1), one
+Parareal iteration each, run concurrently by the library's worker threads with
+the worker count chosen by the library's autotuner (its timed candidate runs
+are the warm-up). value = fine time-steps of all problems per second.
+
 N > 1 runs N independent replicas (one per GPU, one rank each): the path
 does not shard, so there is no collective on the data path.
 """
@@ -50,7 +57,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step"])
+    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step", "batch"])
+    ap.add_argument("--instances", type=int, default=4,
+                    help="--unit batch: the first K problems of the seeded 48-problem uneven batch")
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
     ap.add_argument("--kernel-table", action="store_true")
     ap.add_argument("--no-precision-variant", action="store_true",
@@ -166,6 +175,44 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def bench_batch(args, torch, fsi, wl, dev):
+    """One line for the batch runner (see the module docstring)."""
+    ws = wl.uneven_batch()[:max(args.instances, 1)]
+    batch = fsi.Batch(ws, max_iter=1)
+    cands = [1, 2, 4, 8]
+    best, secs = batch.autotune([c for c in cands if c <= 2 * len(ws)])
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    l0 = fsi.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = batch.run(best)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    units = sum(w.n_slices * w.m_fine for w in ws)
+    value = units * args.steps / (ms / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": len(secs) + 1, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "uneven_batch_seed1907_first%d_of_48" % len(ws), "unit": "batch",
+                       "problems": [{"name": w.name, "n_dofs": fsi.mesh_size(w)[1], "slices": w.n_slices,
+                                     "mu_s": w.material.mu_s, "vbar": w.material.vbar,
+                                     "seconds": r["seconds"], "worker": r["worker"],
+                                     "fine_gmres": r["stats"]["fine"]["gmres_iters"]}
+                                    for w, r in zip(ws, res)],
+                       "step": "every problem: parareal_iterate with 1 iteration, problems concurrent",
+                       "workers": best, "autotune_seconds": dict(zip(map(str, cands), secs)),
+                       "one_worker_vs_best": secs[0] / min(secs)},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": fsi.launch_count() - l0}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -183,6 +230,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build_library()
+    if args.unit == "batch":
+        return bench_batch(args, torch, fsi, wl, dev)
     w = wl.LARGE_128x32
     N = w.n_slices
     fine_unit = args.unit in ("fine_step", "coarse_step")

@@ -26,7 +26,8 @@
  *     an iteration limit.
  *   - The context owns all workspace (allocated in fsi_setup for batches of
  *     up to params->max_batch slices). A context must not be used by two
- *     host threads at the same time.
+ *     host threads at the same time; different contexts may be used from
+ *     different threads concurrently, each on its own stream.
  */
 #ifndef FSI_H
 #define FSI_H
@@ -252,8 +253,68 @@ int fsi_set_material(fsi_ctx* ctx, double mu_s, double lambda_s, double vbar);
 int fsi_adjoint(fsi_ctx* ctx, const double* U0, double t0, int n_steps, double* J_out,
                 double* grad, fsi_stats* stats, void* stream);
 
+/* Sizes of the finest level of a mesh, on the host only (no GPU, no context):
+ * nodes, dofs (5 per node) and 5x5 blocks of the Jacobian's block pattern, as
+ * fsi_n_nodes / fsi_n_dofs / fsi_nnzb of a context built on the same mesh.
+ * Outputs: host ints. Errors: FSI_EINVAL (bad mesh, null output). */
+int fsi_mesh_size(const fsi_mesh* mesh, int* n_nodes, int* n_dofs, int* nnzb);
+
+/* ---- Batches of independent problems (beyond the paper, which solves one
+ * problem at a time) ----------------------------------------------------
+ * Many independent FSI problems of uneven meshes, materials and slice counts,
+ * each advanced by the Parareal iteration of Sec. 3 (parareal_iterate).
+ * Worker host threads, each with its own non-blocking CUDA stream, take the
+ * problems longest first (estimated cost: dofs x fine steps still iterated,
+ * plus the single-slice coarse steps weighted 8x) and run each in its own
+ * context, created and released around it; kernels of different workers run
+ * concurrently on the GPU. A problem's result is bit-identical to running it
+ * alone with parareal_iterate. A problem whose set-up runs out of device memory
+ * next to the others is run again after all workers finish, alone. */
+typedef struct fsi_instance {
+  fsi_mesh mesh;               /* host pointers, read during the call */
+  fsi_params params;           /* max_batch is ignored: taken as n_slices */
+  double* U;                   /* device [n_slices + 1][n_dofs], caller-owned;
+                                  in/out exactly as in parareal_iterate */
+  int max_iter;                /* Parareal iterations, as parareal_iterate */
+  double tol;                  /* increment tolerance, as parareal_iterate */
+  fsi_parareal_stats stats;    /* out; set history/history_len before the
+                                  call to record increments (host memory) */
+  int status;                  /* out: FSI_OK or this problem's error code */
+  int worker;                  /* out: worker thread that ran it */
+  double seconds;              /* out: host wall time of set-up, Parareal
+                                  and release of this problem */
+} fsi_instance;
+
+/* The schedule the batch runner follows, on the host only: order[n] = the
+ * problems longest first (ties by index), cost[n] = estimated cost,
+ * worker[n] = the worker each problem gets when every worker runs exactly the
+ * estimate (greedy: next problem to the least loaded worker, ties by index),
+ * makespan (may be NULL) = the largest worker load of that schedule.
+ * Errors: FSI_EINVAL (n < 0, workers < 1, null outputs, a bad mesh). */
+int fsi_batch_plan(const fsi_instance* inst, int n, int workers, int* order, int* worker,
+                   double* cost, double* makespan);
+
+/* Run the batch with `workers` concurrent workers (at most n are started).
+ * The workers start after the work already queued on `stream`, and `stream`
+ * continues after all of theirs. Returns FSI_OK when every problem succeeded,
+ * otherwise the first failing problem's code (its message names the problem);
+ * every problem's own status is in inst[i].status either way.
+ * Errors: FSI_EINVAL (bad arguments: nothing runs), FSI_ECUDA, the problems' codes. */
+int fsi_batch_parareal(fsi_instance* inst, int n, int workers, void* stream);
+
+/* Autotuner for the worker count: one untimed run with candidates[0] (module
+ * loading, CUDA graph capture), then one timed run per candidate (host wall
+ * time between stream synchronisations). seconds[n_candidates] receives the
+ * times, *best the fastest worker count. Every run recomputes the same results
+ * from U[0] of each problem, so inst holds the results on return.
+ * Errors: FSI_EINVAL, and those of fsi_batch_parareal. */
+int fsi_batch_autotune(fsi_instance* inst, int n, const int* candidates, int n_candidates,
+                       double* seconds, int* best, void* stream);
+
 /* Measurement hooks (the paper has no counterpart; they serve benchmarking).
- * Process-wide, for one host thread. Every kernel launch of the library is
+ * Process-wide; counts and timings include every host thread's launches
+ * (profile_enable and profile_read themselves must not run while another
+ * thread is inside the library). Every kernel launch of the library is
  * counted per kernel id (0 .. fsi_kernel_count()-1, names from
  * fsi_kernel_name). fsi_profile_enable(mask) clears the timing records and
  * brackets each later launch of the kernels whose id bit is set with two CUDA

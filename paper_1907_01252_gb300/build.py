@@ -8,8 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfsi.so")
-SOURCES = ["fsi.cu"]
-HEADERS = ["fsi_kernels.cuh", "fsi_element.cuh", os.path.join("..", "..", "include", "fsi.h")]
+SOURCES = ["fsi.cu", "batch.cpp"]
+HEADERS = ["fsi_kernels.cuh", "fsi_element.cuh", "fsi_internal.h", os.path.join("..", "..", "include", "fsi.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -35,7 +35,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-pthread",
            "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES]
     if verbose:
         cmd.insert(4, "-Xptxas=-v")

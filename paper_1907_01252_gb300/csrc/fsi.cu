@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -26,6 +27,7 @@
 #include <vector>
 
 #include "../../include/fsi.h"
+#include "fsi_internal.h"
 #include "fsi_kernels.cuh"
 
 namespace {
@@ -52,7 +54,7 @@ int fail(int code, const std::string& msg) {
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-int g_nact = 0;   // active slices of the current launch sequence (work accounting only)
+thread_local int g_nact = 0;   // active slices of the current launch sequence (work accounting only)
 
 template <typename V>
 int count_active(const V& v) {
@@ -278,7 +280,9 @@ namespace {
 // ---------------------------------------------------------------------------
 // Launch accounting: every kernel launch of the library goes through LAUNCH,
 // which counts it and, when timing is enabled for its id, brackets it with
-// CUDA events on the launching stream (process-wide, one host thread).
+// CUDA events on the launching stream. Counters are process-wide atomics;
+// timing records are kept under a mutex, so contexts driven by different host
+// threads (the batch runner) can be counted and timed together.
 // ---------------------------------------------------------------------------
 enum KernelId {
   KI_ADD_BASIS,
@@ -318,21 +322,22 @@ enum KernelId {
 const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar"};
 
 struct Profiler {
-  unsigned long long mask = 0;
-  long long launches[KI_COUNT] = {};
-  long long total = 0;
+  std::atomic<unsigned long long> mask{0};
+  std::atomic<long long> launches[KI_COUNT] = {};
+  std::atomic<long long> total{0};
+  std::mutex mu;   // guards the members below
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<int> rec_id;
   std::vector<size_t> rec_ev;   // first of the record's two pool events
   std::vector<double> rec_work;
-  double pending_work = 0.0;
   // launches replayed inside CUDA graphs: summed after every replay
   double gms[KI_COUNT] = {}, gwork[KI_COUNT] = {};
   long long gcnt[KI_COUNT] = {};
-  unsigned epoch = 1;   // bumped by fsi_profile_enable: graphs captured earlier are re-captured
+  std::atomic<unsigned> epoch{1};   // bumped by fsi_profile_enable: graphs captured earlier are re-captured
 };
 Profiler g_prof;
+thread_local double g_pending_work = 0.0;   // algorithmic flops of the launch being issued
 
 // A timed launch recorded while a CUDA graph is being captured.
 struct CapRec {
@@ -346,9 +351,9 @@ struct Capture {
   std::vector<CapRec> recs;
   long long launches[KI_COUNT] = {};
 };
-Capture g_cap;
+thread_local Capture g_cap;
 
-void prof_grow_pool(size_t need) {
+void prof_grow_pool_locked(size_t need) {
   while (g_prof.used + need > g_prof.pool.size()) {
     for (int i = 0; i < 256; ++i) {
       cudaEvent_t e;
@@ -367,43 +372,56 @@ inline void prof_record(cudaEvent_t e, cudaStream_t st) {
     cudaEventRecord(e, st);
 }
 
-inline void prof_pre(int id, cudaStream_t st) {
+void prof_grow_pool(size_t need) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_grow_pool_locked(need);
+}
+
+constexpr size_t kNoEvent = ~size_t(0);
+
+// Counts the launch; when its id is timed, reserves an event pair, records the
+// first event and returns its index (kNoEvent otherwise).
+inline size_t prof_pre(int id, cudaStream_t st) {
   if (g_cap.on) {
     g_cap.launches[id]++;
   } else {
-    g_prof.launches[id]++;
-    g_prof.total++;
+    g_prof.launches[id].fetch_add(1, std::memory_order_relaxed);
+    g_prof.total.fetch_add(1, std::memory_order_relaxed);
   }
-  if (!(g_prof.mask >> id & 1ull)) return;
-  prof_grow_pool(2);
-  prof_record(g_prof.pool[g_prof.used], st);
+  if (!(g_prof.mask.load(std::memory_order_relaxed) >> id & 1ull)) return kNoEvent;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_grow_pool_locked(2);
+  const size_t ev = g_prof.used;
+  g_prof.used += 2;
+  prof_record(g_prof.pool[ev], st);
+  return ev;
 }
-inline void prof_post(int id, cudaStream_t st) {
-  if (!(g_prof.mask >> id & 1ull)) return;
-  prof_record(g_prof.pool[g_prof.used + 1], st);
+inline void prof_post(int id, size_t ev, cudaStream_t st) {
+  if (ev == kNoEvent) return;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  prof_record(g_prof.pool[ev + 1], st);
   if (g_cap.on) {
-    g_cap.recs.push_back({id, g_prof.used, g_prof.pending_work / std::max(1, g_cap.n_act)});
+    g_cap.recs.push_back({id, ev, g_pending_work / std::max(1, g_cap.n_act)});
   } else {
     g_prof.rec_id.push_back(id);
-    g_prof.rec_ev.push_back(g_prof.used);
-    g_prof.rec_work.push_back(g_prof.pending_work);
+    g_prof.rec_ev.push_back(ev);
+    g_prof.rec_work.push_back(g_pending_work);
   }
-  g_prof.used += 2;
 }
 
 // LAUNCH_W also records the algorithmic FP64 flops of the launch.
 #define LAUNCH_W(work, id, kern, grid, block, smem, st, ...) \
   do {                                                       \
-    g_prof.pending_work = (work);                            \
+    g_pending_work = (work);                                 \
     LAUNCH(id, kern, grid, block, smem, st, __VA_ARGS__);    \
-    g_prof.pending_work = 0.0;                               \
+    g_pending_work = 0.0;                                    \
   } while (0)
 
 #define LAUNCH(id, kern, grid, block, smem, st, ...) \
   do {                                               \
-    prof_pre(id, st);                                \
+    const size_t ev_ = prof_pre(id, st);             \
     kern<<<grid, block, smem, st>>>(__VA_ARGS__);    \
-    prof_post(id, st);                               \
+    prof_post(id, ev_, st);                          \
   } while (0)
 
 }  // namespace
@@ -544,7 +562,24 @@ int setup_transfer(Level& C, const Level& F) {
 
 // Reference-cell tables: 3-point Gauss rule on [0, 1], Q2 basis, Q1 vertex
 // projection for the local projection stabilisation.
+int upload_tables_once();
+
+// The basis tables live in constant memory: uploaded once per device and
+// process (contexts set up from several host threads share them).
 int upload_tables() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return FSI_OK;
+  TRY(upload_tables_once());
+  CK(cudaStreamSynchronize(cudaStreamLegacy));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return FSI_OK;
+}
+
+int upload_tables_once() {
   const double gp[3] = {0.5 - std::sqrt(0.15), 0.5, 0.5 + std::sqrt(0.15)};
   const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
   auto L = [](int a, double s) { return lag2(a, s); };
@@ -886,7 +921,8 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       }
       CK(cudaMemcpyAsync(res.data(), c->resid, S * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (replayed)   // event times of timed kernels inside the graph, read before the next replay
+      if (replayed && !replayed->recs.empty()) {   // timed kernels inside the graph, read before the next replay
+        std::lock_guard<std::mutex> lk(g_prof.mu);
         for (const CapRec& r : replayed->recs) {
           float e = 0.f;
           if (cudaEventElapsedTime(&e, g_prof.pool[r.ev], g_prof.pool[r.ev + 1]) != cudaSuccess) {
@@ -897,6 +933,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
           g_prof.gwork[r.id] += r.work_per_slice * c->n_act;
           g_prof.gcnt[r.id] += 1;
         }
+      }
       std::vector<uint8_t> fin(S, 0);
       bool any_fin = false, any_left = false;
       for (int s = 0; s < S; ++s) {
@@ -1101,14 +1138,32 @@ int propagate_chunked(fsi_ctx* c, int S, const double* U0, const double* t0, dou
   return FSI_OK;
 }
 
-int validate(const fsi_mesh* mesh, const fsi_params* p) {
-  if (!mesh || !p) return fail(FSI_EINVAL, "null mesh or params");
+int validate_mesh(const fsi_mesh* mesh) {
+  if (!mesh) return fail(FSI_EINVAL, "null mesh");
   if (mesh->n_xseg < 1 || mesh->n_yseg < 1 || !mesh->x_breaks || !mesh->y_breaks || !mesh->nx_seg || !mesh->ny_seg)
     return fail(FSI_EINVAL, "empty mesh");
   for (int i = 0; i < mesh->n_xseg; ++i)
     if (mesh->nx_seg[i] < 1 || !(mesh->x_breaks[i + 1] > mesh->x_breaks[i])) return fail(FSI_EINVAL, "bad x segments");
   for (int i = 0; i < mesh->n_yseg; ++i)
     if (mesh->ny_seg[i] < 1 || !(mesh->y_breaks[i + 1] > mesh->y_breaks[i])) return fail(FSI_EINVAL, "bad y segments");
+  return FSI_OK;
+}
+
+// The finest level of the mesh hierarchy (host tables only).
+void finest_mesh(const fsi_mesh* mesh, HostMesh& h0) {
+  const double box[4] = {mesh->solid_x0, mesh->solid_x1, mesh->solid_y0, mesh->solid_y1};
+  std::vector<double> xb(mesh->x_breaks, mesh->x_breaks + mesh->n_xseg + 1);
+  std::vector<double> yb(mesh->y_breaks, mesh->y_breaks + mesh->n_yseg + 1);
+  h0.xseg.assign(mesh->nx_seg, mesh->nx_seg + mesh->n_xseg);
+  h0.yseg.assign(mesh->ny_seg, mesh->ny_seg + mesh->n_yseg);
+  h0.xv = axis_vertices(xb, h0.xseg);
+  h0.yv = axis_vertices(yb, h0.yseg);
+  build_mesh(h0, mesh->has_solid != 0, box);
+}
+
+int validate(const fsi_mesh* mesh, const fsi_params* p) {
+  if (!p) return fail(FSI_EINVAL, "null params");
+  TRY(validate_mesh(mesh));
   if (p->max_batch < 1 || p->n_slices < 1 || p->m_fine < 1 || p->m_coarse < 1 || !(p->T > 0))
     return fail(FSI_EINVAL, "bad time or batch parameters");
   if (p->gmres_restart < 1 || p->gmres_restart > 63 || p->gmres_maxit < 1 || p->newton_maxit < 1)
@@ -1276,7 +1331,20 @@ int na_scratch(double** out) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+int fsi_record_error(int code, const std::string& msg) { return fail(code, msg); }
+
 extern "C" {
+
+int fsi_mesh_size(const fsi_mesh* mesh, int* n_nodes, int* n_dofs, int* nnzb) {
+  if (!n_nodes || !n_dofs || !nnzb) return fail(FSI_EINVAL, "null output");
+  TRY(validate_mesh(mesh));
+  HostMesh h;
+  finest_mesh(mesh, h);
+  *n_nodes = h.n_nodes;
+  *n_dofs = 5 * h.n_nodes;
+  *nnzb = h.nnzb;
+  return FSI_OK;
+}
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
 
@@ -1309,14 +1377,8 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
               mesh->y_breaks[mesh->n_yseg] - mesh->y_breaks[0], mesh->y_breaks[0], p->alpha0};
   const double box[4] = {mesh->solid_x0, mesh->solid_x1, mesh->solid_y0, mesh->solid_y1};
   // level hierarchy
-  std::vector<double> xb(mesh->x_breaks, mesh->x_breaks + mesh->n_xseg + 1);
-  std::vector<double> yb(mesh->y_breaks, mesh->y_breaks + mesh->n_yseg + 1);
   HostMesh h0;
-  h0.xseg.assign(mesh->nx_seg, mesh->nx_seg + mesh->n_xseg);
-  h0.yseg.assign(mesh->ny_seg, mesh->ny_seg + mesh->n_yseg);
-  h0.xv = axis_vertices(xb, h0.xseg);
-  h0.yv = axis_vertices(yb, h0.yseg);
-  build_mesh(h0, mesh->has_solid != 0, box);
+  finest_mesh(mesh, h0);
   std::vector<HostMesh> hs{h0};
   while ((size_t)hs.back().n_nodes * 5 > (size_t)p->mg_coarsest_max_dofs) {
     const HostMesh& f = hs.back();
@@ -1356,7 +1418,9 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
       (rc = A(&c->active, S)) || (rc = A(&c->active2, S)) || (rc = A(&c->t_dev, S)) ||
       (rc = A(&c->p_in, S * n)) || (rc = A(&c->p_out, S * n)))
     return cleanup(rc);
-  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
+  // the tables were copied with synchronous copies on the legacy stream; wait
+  // for their DMA without waiting on other contexts' non-blocking streams
+  if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
   *out = c;
   return FSI_OK;
 }
@@ -1514,6 +1578,7 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
 }
 
 int fsi_profile_enable(unsigned long long kernel_mask) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
   g_prof.mask = kernel_mask;
   g_prof.used = 0;
   g_prof.rec_id.clear();
@@ -1529,6 +1594,7 @@ int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
     return fail(FSI_EINVAL, "bad kernel id or null output");
   double ms = 0.0, work = 0.0;
   long long cnt = 0;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
   for (size_t r = 0; r < g_prof.rec_id.size(); ++r) {
     if (g_prof.rec_id[r] != kernel_id) continue;
     const size_t ev = g_prof.rec_ev[r];
@@ -1546,8 +1612,8 @@ int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
 }
 
 long long fsi_launch_count(int kernel_id) {
-  if (kernel_id < 0) return g_prof.total;
-  return kernel_id < KI_COUNT ? g_prof.launches[kernel_id] : -1;
+  if (kernel_id < 0) return g_prof.total.load();
+  return kernel_id < KI_COUNT ? g_prof.launches[kernel_id].load() : -1LL;
 }
 
 int fsi_kernel_count(void) { return KI_COUNT; }

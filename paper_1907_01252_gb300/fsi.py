@@ -61,6 +61,12 @@ class fsi_parareal_stats(C.Structure):
         return d
 
 
+class fsi_instance(C.Structure):
+    _fields_ = [("mesh", fsi_mesh), ("params", fsi_params), ("U", C.c_void_p), ("max_iter", C.c_int),
+                ("tol", C.c_double), ("stats", fsi_parareal_stats), ("status", C.c_int), ("worker", C.c_int),
+                ("seconds", C.c_double)]
+
+
 # name -> (restype, argtypes); the exported symbols of include/fsi.h
 _VP, _I, _D = C.c_void_p, C.c_int, C.c_double
 SIGNATURES = {
@@ -83,6 +89,12 @@ SIGNATURES = {
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+    "fsi_mesh_size": (_I, [C.POINTER(fsi_mesh), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "fsi_batch_plan": (_I, [C.POINTER(fsi_instance), _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D),
+                            C.POINTER(_D)]),
+    "fsi_batch_parareal": (_I, [C.POINTER(fsi_instance), _I, _I, _VP]),
+    "fsi_batch_autotune": (_I, [C.POINTER(fsi_instance), _I, C.POINTER(_I), _I, C.POINTER(_D), C.POINTER(_I),
+                                _VP]),
     "fsi_profile_enable": (_I, [C.c_ulonglong]),
     "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
     "fsi_launch_count": (C.c_longlong, [_I]),
@@ -163,28 +175,47 @@ def _dbl(arr):
     return a, a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _mesh_struct(w: wl.Workload):
+    """(fsi_mesh, arrays it points into) for a workload's interface-fitted mesh."""
+    xb = (C.c_double * len(wl.X_BREAKS))(*wl.X_BREAKS)
+    yb = (C.c_double * len(wl.Y_BREAKS))(*wl.Y_BREAKS)
+    nxs = (C.c_int * len(w.nx_seg))(*w.nx_seg)
+    nys = (C.c_int * len(w.ny_seg))(*w.ny_seg)
+    (sx0, sx1), (sy0, sy1) = wl.SOLID_BOX
+    mesh = fsi_mesh(len(w.nx_seg), xb, nxs, len(w.ny_seg), yb, nys, int(w.with_solid), sx0, sx1, sy0, sy1)
+    return mesh, (xb, yb, nxs, nys)
+
+
+def _params(w: wl.Workload, max_batch: int, overrides):
+    m = w.material
+    p = dict(rho_f=m.rho_f, nu_f=m.nu_f, rho_s=m.rho_s, mu_s=m.mu_s, lambda_s=m.lambda_s, vbar=m.vbar,
+             ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
+             m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
+             gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
+             gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
+             mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
+             mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
+    p.update(overrides)
+    return p
+
+
+def mesh_size(w: wl.Workload):
+    """(n_nodes, n_dofs, nnzb) of a workload's finest mesh, computed on the host (no GPU)."""
+    lib = load_library()
+    mesh, keep = _mesh_struct(w)
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.fsi_mesh_size(C.byref(mesh), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
 class Context:
     """An fsi_ctx built for a workload (mesh from the break points, materials, solver parameters)."""
 
     def __init__(self, workload: wl.Workload, max_batch: int = 1, **overrides):
         lib = load_library()
         w = workload
-        m = w.material
-        xb = (C.c_double * len(wl.X_BREAKS))(*wl.X_BREAKS)
-        yb = (C.c_double * len(wl.Y_BREAKS))(*wl.Y_BREAKS)
-        nxs = (C.c_int * len(w.nx_seg))(*w.nx_seg)
-        nys = (C.c_int * len(w.ny_seg))(*w.ny_seg)
-        (sx0, sx1), (sy0, sy1) = wl.SOLID_BOX
-        self._mesh = fsi_mesh(len(w.nx_seg), xb, nxs, len(w.ny_seg), yb, nys, int(w.with_solid), sx0, sx1, sy0, sy1)
-        self._keep = (xb, yb, nxs, nys)
-        p = dict(rho_f=m.rho_f, nu_f=m.nu_f, rho_s=m.rho_s, mu_s=m.mu_s, lambda_s=m.lambda_s, vbar=m.vbar,
-                 ramp_t=m.ramp_t, theta0=m.theta0, alpha0=m.alpha0, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine,
-                 m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
-                 gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
-                 gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
-                 mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
-                 mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
-        p.update(overrides)
+        self._mesh, self._keep = _mesh_struct(w)
+        p = _params(w, max_batch, overrides)
         self.params = p
         self._params = fsi_params(**p)
         h = C.c_void_p()
@@ -330,3 +361,85 @@ def tip_functional(ctx: Context, U0, t0, n_steps):
             return gout * grad
 
     return _TipFunctional.apply
+
+
+class Batch:
+    """Independent problems (each a workload with its own mesh, material and
+    slice count) advanced by the library's batch runner (fsi_batch_parareal).
+
+    states: one device tensor [n_slices + 1][n_dofs] per problem (U[0] is the
+    initial state; zeros from rest when omitted). Each run overwrites
+    U[1:] from U[0], as parareal_iterate does. With device_states=False no
+    device memory is touched and only plan() may be called (host only)."""
+
+    def __init__(self, workloads, states=None, max_iter=1, tol=0.0, history=False, device_states=True,
+                 **overrides):
+        self.lib = load_library()
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        self._inst = (fsi_instance * max(n, 1))()
+        self._keep = []
+        self.states = []
+        self._hist = []
+        for i, w in enumerate(self.workloads):
+            mesh, keep = _mesh_struct(w)
+            self._keep.append(keep)
+            nd = mesh_size(w)[1]
+            if not device_states:
+                U = None
+            elif states is None:
+                import torch
+                U = torch.zeros((w.n_slices + 1, nd), dtype=torch.float64, device="cuda")
+            else:
+                import torch
+                U = states[i]
+                if tuple(U.shape) != (w.n_slices + 1, nd) or U.dtype != torch.float64 or not U.is_contiguous():
+                    raise ValueError("state %d must be a contiguous float64 [%d, %d] tensor" % (i, w.n_slices + 1, nd))
+            self.states.append(U)
+            I = self._inst[i]
+            I.mesh = mesh
+            I.params = fsi_params(**_params(w, w.n_slices, overrides))
+            I.U = U.data_ptr() if U is not None else None
+            I.max_iter = max_iter
+            I.tol = tol
+            if history:
+                h = np.zeros((max(max_iter, 1), 3))
+                self._hist.append(h)
+                I.stats.history = h.ctypes.data_as(C.POINTER(C.c_double))
+                I.stats.history_len = h.shape[0]
+
+    def __len__(self):
+        return len(self.workloads)
+
+    def plan(self, workers):
+        """The runner's longest-first schedule: order, planned worker, estimated cost, makespan."""
+        n = len(self)
+        order, worker = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+        cost, mk = (C.c_double * max(n, 1))(), C.c_double()
+        _check(self.lib.fsi_batch_plan(self._inst, n, workers, order, worker, cost, C.byref(mk)))
+        return {"order": list(order)[:n], "worker": list(worker)[:n], "cost": list(cost)[:n],
+                "makespan": mk.value}
+
+    def run(self, workers):
+        """Run every problem; raises FsiError if any failed (per-problem results in results())."""
+        _check(self.lib.fsi_batch_parareal(self._inst, len(self), workers, _stream()))
+        return self.results()
+
+    def autotune(self, candidates):
+        """(best worker count, seconds per candidate) from the library's autotuner."""
+        cand = (C.c_int * len(candidates))(*candidates)
+        secs = (C.c_double * len(candidates))()
+        best = C.c_int()
+        _check(self.lib.fsi_batch_autotune(self._inst, len(self), cand, len(candidates), secs, C.byref(best),
+                                           _stream()))
+        return best.value, list(secs)
+
+    def results(self):
+        out = []
+        for i in range(len(self)):
+            I = self._inst[i]
+            d = {"status": I.status, "worker": I.worker, "seconds": I.seconds, "stats": I.stats.as_dict()}
+            if self._hist:
+                d["history"] = self._hist[i][:max(I.stats.iterations, 0)].tolist()
+            out.append(d)
+        return out

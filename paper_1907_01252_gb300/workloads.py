@@ -107,6 +107,24 @@ LARGE_128x32 = Workload("fsi2d_q2_128x32_T2_64x32", nx=128, ny=32, T=2.0, n_slic
 WORKLOADS = {w.name: w for w in (SMALL_16x4, LARGE_128x32)}
 
 
+def uneven_batch(n=48, seed=1907, ny_range=(16, 48), slice_range=(16, 32), T=1.0, m_fine=16):
+    """n independent instances of the channel problem with uneven meshes and
+    materials, seeded: ny uniform on ny_range with nx = 4 ny; mu_s log-uniform
+    on [2e5, 2e6] with lambda_s = 4 mu_s (Poisson ratio 0.4, as in the base
+    material); mean inflow uniform on [0.5, 1.5]; slices uniform on
+    slice_range; interval T with m_fine fine steps and one coarse step per slice."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        mu = float(np.exp(rng.uniform(math.log(2e5), math.log(2e6))))
+        vbar = float(rng.uniform(0.5, 1.5))
+        slices = int(rng.integers(slice_range[0], slice_range[1] + 1))
+        out.append(Workload("uneven%02d_%dx%d" % (i, 4 * ny, ny), nx=4 * ny, ny=ny, T=T, n_slices=slices,
+                            m_fine=m_fine, material=Material(mu_s=mu, lambda_s=4.0 * mu, vbar=vbar)))
+    return out
+
+
 def random_state(n_nodes, seed, v_scale=1.0, u_scale=2e-3, p_scale=100.0):
     """Seeded random nodal state [n_nodes, 5] = (v_x, v_y, u_x, u_y, p).
 
