@@ -312,6 +312,25 @@ def main():
     torch.cuda.synchronize()
     serial_rate = nser / (time.perf_counter() - s0) if nser else None
 
+    # the paper's speedup model, Eq. (eq:speedup), S = 1 / (r + (K / N)(1 + r)), with r the measured
+    # cost of one coarse slice step over one serial fine slice (m_fine single-slice fine steps)
+    model = None
+    if serial_rate:
+        ncs = 3
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        cur = Us
+        for j in range(ncs):
+            cur, _ = ctx.fsi_theta_step(cur, [t0 + j * w.k_coarse], w.k_coarse, 1.0)
+        torch.cuda.synchronize()
+        t_coarse = (time.perf_counter() - s0) / ncs
+        t_fine_slice = w.m_fine / serial_rate
+        r = t_coarse / t_fine_slice
+        model = {"r": r, "K": 1, "N": N, "S": 1.0 / (r + (1.0 / N) * (1.0 + r)),
+                 "coarse_step_s": t_coarse, "serial_fine_slice_s": t_fine_slice,
+                 "note": "model speedup with one processor per slice; the measured batched/serial ratio is "
+                         "the pass's speedup over the serial fine solve on the same GPU"}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e and not fine_unit:
@@ -331,31 +350,48 @@ def main():
         e2e = {"value": N * w.m_fine * args.steps / (ems / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": h_in.numel() * 8, "d2h_bytes_per_step": h_out.numel() * 8}
 
-    # the precision variant (FP64 FGMRES with the multigrid preconditioner in FP32,
-    # FP64 residual / J / correction) on the same Parareal pass, timed the same
-    # way after one warm-up pass
-    variant = None
+    # precision variants on the same Parareal pass (one warm-up pass each), with
+    # their relative error against the FP64 pass just run (U holds its result)
+    variants = []
     if not args.no_precision_variant and not fine_unit:
-        ctx32 = fsi.Context(w, max_batch=N, precision=2)
+        U64 = U.clone().view(N + 1, -1, 5)
+        tip = wl.tip_node(w)
+        desc = {1: "FP32 linear solver (FGMRES, multigrid, Vanka, operator) inside the FP64 Newton loop (Newton "
+                   "tolerance 1e-11); "
+                   "FP64 residual, J = det F, Parareal correction",
+                2: "FP64 FGMRES preconditioned by an FP32 multigrid V-cycle (FP32 Vanka, transfers, level "
+                   "operators); FP64 residual, J = det F, Parareal correction"}
+        for prec in (1, 2):
+            # the FP32 solver meets the 1e-8 target at a Newton tolerance of 1e-11 (1e-10 leaves ~7e-8)
+            ctxv = fsi.Context(w, max_batch=N, precision=prec, **({"newton_tol": 1e-11} if prec == 1 else {}))
 
-        def step32():
-            U[1:].zero_()
-            _, s32 = ctx32.parareal_iterate(U, 1, 0.0)
-            return s32
-        step32()
-        torch.cuda.synchronize()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        for _ in range(args.steps):
-            s32 = step32()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        vms = b0.elapsed_time(b1)
-        variant = {"precision": "FP64 FGMRES preconditioned by an FP32 multigrid V-cycle (FP32 Vanka, transfers, "
-                                "level operators); FP64 residual, J = det F, Parareal correction",
-                   "value": N * w.m_fine * args.steps / (vms / 1000.0), "unit": UNIT,
-                   "ms_per_step": vms / args.steps, "newton_fine": s32["fine"], "newton_coarse": s32["coarse"]}
-        del ctx32
+            def stepv():
+                U[1:].zero_()
+                _, sv = ctxv.parareal_iterate(U, 1, 0.0)
+                return sv
+            stepv()
+            torch.cuda.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for _ in range(args.steps):
+                sv = stepv()
+            b1.record(stream)
+            torch.cuda.synchronize()
+            vms = b0.elapsed_time(b1)
+            Uv = U.view(N + 1, -1, 5)
+            err = {}
+            for name, sl in (("v", slice(0, 2)), ("u", slice(2, 4)), ("p", slice(4, 5))):
+                num = (Uv[1:, :, sl] - U64[1:, :, sl]).flatten(1).norm(dim=1)
+                den = U64[1:, :, sl].flatten(1).norm(dim=1)
+                err[name] = float((num / den).max())
+            tnum = (Uv[1:, tip, 2:4] - U64[1:, tip, 2:4]).norm(dim=1)
+            tden = U64[1:, tip, 2:4].norm(dim=1)
+            err["tip_displacement"] = float((tnum / tden).max())
+            variants.append({"precision": prec, "what": desc[prec],
+                             "value": N * w.m_fine * args.steps / (vms / 1000.0), "unit": UNIT,
+                             "ms_per_step": vms / args.steps, "max_rel_err_vs_fp64_pass": err,
+                             "newton_fine": sv["fine"], "newton_coarse": sv["coarse"]})
+            del ctxv
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -383,9 +419,10 @@ def main():
                                       "gmres_restart": w.gmres_restart},
                            "serial_gpu_fine_steps_per_s": serial_rate,
                            "batched_vs_serial": value / serial_rate if serial_rate else None,
+                           "paper_speedup_model": model,
                            "newton_fine": st["fine"], "newton_coarse": st["coarse"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "precision_variant": variant,
+                "precision_variants": variants,
                 "gpu_launches": launches}
         print(json.dumps(line))
     if dist:

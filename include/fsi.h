@@ -112,12 +112,18 @@ typedef struct fsi_params {
                               multigrid, Vanka, block-sparse operator) in FP32 inside
                               the FP64 Newton loop (inner tolerance >= 1e-6); the
                               Newton refinement only contracts while cond(J) times the
-                              FP32 unit roundoff stays below one, which large coarse
-                              steps violate. 2: FP64 FGMRES on the FP64 Jacobian,
+                              FP32 unit roundoff stays below one (large steps of stiff
+                              problems can violate it). 2: FP64 FGMRES on the FP64 Jacobian,
                               preconditioned by the multigrid V-cycle in FP32 (Vanka
                               inverses, transfers, level operators): GMRES-based
                               refinement, as accurate as 0. In every mode the Newton
                               residual, J = det F and the Parareal correction are FP64 */
+  int pipeline_chunk;      /* parareal_iterate: 0 runs the sweeps and the batched fine
+                              solves one after the other; > 0 pipelines them (a host
+                              thread runs the sequential coarse sweeps in a second,
+                              single-slice context on a high-priority stream while
+                              the fine solves run in batches of pipeline_chunk slices
+                              as soon as their inputs exist). Results are identical */
   int max_batch;           /* most slices advanced in one call */
 } fsi_params;
 
@@ -252,6 +258,16 @@ int fsi_set_material(fsi_ctx* ctx, double mu_s, double lambda_s, double vbar);
  * Errors: FSI_EINVAL (no tip node, n_steps < 1), solver errors as fsi_theta_step. */
 int fsi_adjoint(fsi_ctx* ctx, const double* U0, double t0, int n_steps, double* J_out,
                 double* grad, fsi_stats* stats, void* stream);
+
+/* Dense inverse of S independent n x n matrices, the solver of the coarsest
+ * multigrid level (Gauss-Jordan with partial pivoting, in place). A, inv:
+ * device [S][n][n] row-major; A is not modified; inv receives A^{-1}.
+ * method 0: on a thread-block cluster of 8 CTAs per matrix when its rows fit
+ * in the cluster's shared memory, else one CTA per matrix; method 1: always
+ * one CTA per matrix. Both choose the same pivots and give the same inverse.
+ * Allocates its own scratch; synchronises the stream.
+ * Errors: FSI_EINVAL, FSI_ENOMEM, FSI_EJAC (a singular matrix), FSI_ECUDA. */
+int fsi_dense_invert(int S, int n, const double* A, double* inv, int method, void* stream);
 
 /* Sizes of the finest level of a mesh, on the host only (no GPU, no context):
  * nodes, dofs (5 per node) and 5x5 blocks of the Jacobian's block pattern, as

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <thread>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -460,6 +462,14 @@ struct fsi_ctx {
   // Parareal workspace
   double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
   int red_blocks = 0;
+  // pipelined Parareal: the sweeps run in a single-slice context of the same
+  // mesh on their own stream; Uin holds the fine inputs of two iterations
+  std::vector<double> mesh_xb, mesh_yb;
+  std::vector<int> mesh_nx, mesh_ny;
+  fsi_mesh mesh_desc{};
+  fsi_ctx* sweep = nullptr;
+  cudaStream_t sweep_stream = nullptr;
+  double* Uin = nullptr;
 };
 
 namespace {
@@ -700,6 +710,38 @@ int dots(fsi_ctx* c, int S, size_t n, int nv, const T* V, size_t vstride, size_t
 
 // Multigrid setup for the Newton iterate U (level 0) and old state Uold; the
 // preconditioner's matrices and inverses are stored in T.
+// Inverse of S dense n x n matrices (the coarsest multigrid level): on a
+// thread-block cluster when its rows fit in the cluster's shared memory, else
+// on one CTA per slice with the matrix in global memory. D is overwritten.
+template <typename T>
+int dense_invert(int S, int n, T* D, int* perm, const uint8_t* act, T* inv, int* status, cudaStream_t st,
+                 int force_single = 0) {
+  const size_t smem = gjc_smem_bytes<T>(n);
+  if (!force_single && smem <= 200 * 1024) {
+    CK(cudaFuncSetAttribute((const void*)k_dense_invert_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(GJC_CTAS, S);
+    cfg.blockDim = dim3(GJC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = GJC_CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const size_t ev = prof_pre(KI_DENSE_INVERT, st);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_dense_invert_cluster<T>, n, (const T*)D, act, inv, status);
+    prof_post(KI_DENSE_INVERT, ev, st);
+    if (e != cudaSuccess) return fail(FSI_ECUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
+    return launch_check();
+  }
+  LAUNCH(KI_DENSE_INVERT, k_dense_invert<T>, (S), GJ_THREADS, n * sizeof(T), st, n, D, perm, act, inv, status);
+  return launch_check();
+}
+
 template <typename T>
 int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
              cudaStream_t st, bool keep_coarsest = false, bool transpose = false) {
@@ -734,7 +776,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
       const int n = (int)L.n;
       T* D = reinterpret_cast<T*>(L.D);
       LAUNCH(KI_DENSE_FROM_BSR, k_dense_from_bsr<T>, (dim3(nblk((size_t)n * n, 256), S)), 256, 0, st, L.dm, A, act, D);
-      LAUNCH(KI_DENSE_INVERT, k_dense_invert<T>, (S), GJ_THREADS, n * sizeof(T), st, n, D, L.perm, act, reinterpret_cast<T*>(L.Dinv), c->status);
+      TRY(dense_invert<T>(S, n, D, L.perm, act, reinterpret_cast<T*>(L.Dinv), c->status, st));
     } else {
       LAUNCH_W(2.0 * 45 * 45 * 45 * L.h.n_cells * (double)c->n_act, KI_VANKA_SETUP, k_vanka_setup<T>, (dim3(L.h.n_cells, S)), VK_THREADS, 0, st, L.dm, A, act, reinterpret_cast<T*>(L.KV), c->status);
     }
@@ -1171,6 +1213,7 @@ int validate(const fsi_mesh* mesh, const fsi_params* p) {
   if (p->precision < 0 || p->precision > 2) return fail(FSI_EINVAL, "precision must be 0, 1 or 2");
   if (!(p->gmres_rtol > 0.0 && p->gmres_rtol < 1.0)) return fail(FSI_EINVAL, "gmres_rtol must lie in (0, 1)");
   if (!(p->newton_eta >= 0.0 && p->newton_eta < 1.0)) return fail(FSI_EINVAL, "newton_eta must lie in [0, 1)");
+  if (p->pipeline_chunk < 0) return fail(FSI_EINVAL, "pipeline_chunk must be >= 0");
   if (p->newton_eta > 0.0 && !(p->gmres_rtol_first > 0.0 && p->gmres_rtol_first < 1.0))
     return fail(FSI_EINVAL, "gmres_rtol_first must lie in (0, 1)");
   if (p->mg_smoother != 0 && p->mg_smoother != 1) return fail(FSI_EINVAL, "mg_smoother must be 0 or 1");
@@ -1331,9 +1374,277 @@ int na_scratch(double** out) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+
+// Parareal correction of slice i (Eq. parareal:iteration, evaluated as
+// F + (C_new - C_old)): U[i+1] = Fv[i] + Cn - Cold[i]; folds the slice's
+// relative increments of v, u, p into inc.
+int correct_slice(fsi_ctx* c, int i, const double* Cn, double* U, double inc[3], cudaStream_t st) {
+  const size_t n = c->n;
+  const int nrb = c->red_blocks;
+  LAUNCH(KI_PARAREAL_CORRECT, k_parareal_correct, (nrb), RED_THREADS, 0, st, (int)n, c->Fv + (size_t)i * n, Cn,
+         c->Cold + (size_t)i * n, U + (size_t)(i + 1) * n, c->ppart);
+  TRY(launch_check());
+  std::vector<double> part(nrb * 6);
+  CK(cudaMemcpyAsync(part.data(), c->ppart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double a[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nrb; ++b)
+    for (int f = 0; f < 6; ++f) a[f] += part[b * 6 + f];
+  for (int f = 0; f < 3; ++f) {
+    const double rel = a[3 + f] > 0 ? std::sqrt(a[f] / a[3 + f]) : std::sqrt(a[f]);
+    if (!std::isfinite(rel)) return fail(FSI_EDIVERGE, "Parareal increment is not finite");
+    inc[f] = std::max(inc[f], rel);
+  }
+  return FSI_OK;
+}
+
+void record_iteration(fsi_parareal_stats& loc, int it, const double inc[3]) {
+  loc.increment_v = inc[0];
+  loc.increment_u = inc[1];
+  loc.increment_p = inc[2];
+  if (loc.history && it - 1 < loc.history_len)
+    for (int f = 0; f < 3; ++f) loc.history[(it - 1) * 3 + f] = inc[f];
+  loc.iterations = it;
+}
+
+// The predictor sweep, then per iteration the fine solves of every slice not
+// yet exact (batched) followed by the corrected coarse sweep.
+int parareal_serial(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parareal_stats& loc, cudaStream_t st) {
+  const int N = c->prm.n_slices;
+  const size_t n = c->n;
+  const double dt = c->prm.T / N;
+  std::vector<double> t(N);
+  for (int i = 0; i < N; ++i) t[i] = i * dt;
+  for (int i = 0; i < N; ++i) {
+    TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cold + (size_t)i * n, false, &loc.coarse, st));
+    CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    loc.coarse_steps += c->prm.m_coarse;
+  }
+  for (int it = 1; it <= max_iter && it <= N; ++it) {
+    const int first = it - 1;
+    const int S = N - first;
+    TRY(propagate_chunked(c, S, U + (size_t)first * n, &t[first], c->Fv + (size_t)first * n, true, &loc.fine, st));
+    loc.fine_steps += (long long)S * c->prm.m_fine;
+    double inc[3] = {0, 0, 0};
+    for (int i = first; i < N; ++i) {
+      const double* Cn;
+      if (i == first) {
+        Cn = c->Cold + (size_t)i * n;   // unchanged input: C(U_i^it) - C(U_i^(it-1)) = 0 exactly
+      } else {
+        TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cnew, false, &loc.coarse, st));
+        loc.coarse_steps += c->prm.m_coarse;
+        Cn = c->Cnew;
+      }
+      TRY(correct_slice(c, i, Cn, U, inc, st));
+      if (i != first)
+        CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    record_iteration(loc, it, inc);
+    if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
+  }
+  return FSI_OK;
+}
+
+// Pipelined Parareal (the paper's implementation of Sec. 3 starts a slice's
+// fine solve as soon as its coarse value exists; here on one GPU): a host
+// thread runs the sequential sweeps (the predictor, then each corrected sweep)
+// in a single-slice context on its own high-priority stream, while the calling
+// thread runs the fine solves in batches of pipeline_chunk slices on the
+// caller's stream, each batch as soon as its inputs exist. The fine inputs of
+// iteration it are kept in Uin[it % 2], so the corrected sweep may overwrite U
+// while later batches of the same iteration still run. Every slice sees the
+// arithmetic of parareal_serial, so the results agree bit for bit.
+int parareal_pipelined(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parareal_stats& loc,
+                       cudaStream_t st) {
+  const int N = c->prm.n_slices;
+  const size_t n = c->n;
+  const double dt = c->prm.T / N;
+  const int B = std::max(1, c->prm.pipeline_chunk);
+  const int K = std::min(max_iter, N);
+  if (!c->sweep) {
+    fsi_params p1 = c->prm;
+    p1.max_batch = 1;
+    p1.pipeline_chunk = 0;
+    fsi_ctx* sw = nullptr;
+    TRY(fsi_setup(&c->mesh_desc, &p1, &sw));
+    c->sweep = sw;
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&c->sweep_stream, cudaStreamNonBlocking, hi));
+  }
+  if (!c->Uin) TRY(dalloc(c->owned, &c->Uin, (size_t)2 * N * n));
+  fsi_ctx* sw = c->sweep;
+  sw->P = c->P;   // materials changed through fsi_set_material
+  cudaStream_t ss = c->sweep_stream;
+  std::vector<double> t(N);
+  for (int i = 0; i < N; ++i) t[i] = i * dt;
+  auto Uin = [&](int it, int i) { return c->Uin + ((size_t)(it % 2) * N + i) * n; };
+
+  // progress shared by the two threads, guarded by mu
+  std::mutex mu;
+  std::condition_variable cv;
+  int ready_it = 1, ready = 1;     // the fine inputs of iteration ready_it exist for slices < ready
+  int fine_it = 0, fine_done = 0;  // the fine results of iteration fine_it exist for slices < fine_done
+  int go_it = 1;                   // fine solves of iterations <= go_it may start
+  bool stop = false, abort = false;
+  int err = FSI_OK;
+  std::string err_msg;
+  auto fail_shared = [&](int rc) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (err == FSI_OK) err = rc, err_msg = fsi_last_error();
+    abort = true;
+    cv.notify_all();
+  };
+  fsi_stats coarse_stats{};
+  long long coarse_steps = 0;
+
+  // the sweeps start after the caller's queued work (U[0])
+  cudaEvent_t start;
+  CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CK(cudaEventRecord(start, st));
+  CK(cudaStreamWaitEvent(ss, start, 0));
+  CK(cudaEventDestroy(start));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+
+  std::thread sweeper([&] {
+    cudaSetDevice(dev);
+    auto body = [&]() -> int {
+      // predictor sweep U[i+1] = C(U[i]), which also gives the fine inputs of iteration 1
+      CK(cudaMemcpyAsync(Uin(1, 0), U, n * sizeof(double), cudaMemcpyDeviceToDevice, ss));
+      for (int i = 0; i < N; ++i) {
+        TRY(propagate_chunked(sw, 1, U + (size_t)i * n, &t[i], c->Cold + (size_t)i * n, false, &coarse_stats, ss));
+        CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ss));
+        if (i + 1 < N)
+          CK(cudaMemcpyAsync(Uin(1, i + 1), c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                             ss));
+        CK(cudaStreamSynchronize(ss));
+        coarse_steps += c->prm.m_coarse;
+        std::lock_guard<std::mutex> lk(mu);
+        if (abort) return FSI_OK;
+        ready = i + 2;
+        cv.notify_all();
+      }
+      for (int it = 1; it <= K; ++it) {
+        const int first = it - 1;
+        double inc[3] = {0, 0, 0};
+        for (int i = first; i < N; ++i) {
+          const double* Cn = c->Cold + (size_t)i * n;
+          if (i != first) {   // C of the corrected U[i], while later fine batches may still run
+            TRY(propagate_chunked(sw, 1, U + (size_t)i * n, &t[i], c->Cnew, false, &coarse_stats, ss));
+            coarse_steps += c->prm.m_coarse;
+            Cn = c->Cnew;
+          }
+          {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] { return abort || (fine_it == it && fine_done > i); });
+            if (abort) return FSI_OK;
+          }
+          TRY(correct_slice(c, i, Cn, U, inc, ss));
+          if (i != first)
+            CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, ss));
+          if (it < K && i + 1 < N)
+            CK(cudaMemcpyAsync(Uin(it + 1, i + 1), U + (size_t)(i + 1) * n, n * sizeof(double),
+                               cudaMemcpyDeviceToDevice, ss));
+          CK(cudaStreamSynchronize(ss));
+        }
+        record_iteration(loc, it, inc);
+        std::lock_guard<std::mutex> lk(mu);
+        if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol || it == K) {
+          stop = true;
+        } else {   // every input of iteration it + 1 (slices it .. N-1) exists
+          ready_it = it + 1;
+          ready = N;
+          go_it = it + 1;
+        }
+        cv.notify_all();
+        if (stop) break;
+      }
+      return FSI_OK;
+    };
+    const int rc = body();
+    if (rc != FSI_OK) fail_shared(rc);
+  });
+
+  // the fine solves, on the calling thread in batches of B slices
+  for (int it = 1; it <= K; ++it) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return abort || stop || go_it >= it; });
+      if (abort || go_it < it) break;
+      fine_it = it;
+      fine_done = it - 1;
+    }
+    bool failed = false;
+    for (int s0 = it - 1; s0 < N; s0 += B) {
+      const int s1 = std::min(N, s0 + B);
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return abort || (ready_it == it && ready >= s1); });
+        if (abort) {
+          failed = true;
+          break;
+        }
+      }
+      const int rc = propagate_chunked(c, s1 - s0, Uin(it, s0), &t[s0], c->Fv + (size_t)s0 * n, true, &loc.fine, st);
+      if (rc != FSI_OK) {
+        fail_shared(rc);
+        failed = true;
+        break;
+      }
+      loc.fine_steps += (long long)(s1 - s0) * c->prm.m_fine;
+      std::lock_guard<std::mutex> lk(mu);
+      fine_done = s1;
+      cv.notify_all();
+    }
+    if (failed) break;
+  }
+  sweeper.join();
+  loc.coarse = coarse_stats;
+  loc.coarse_steps = coarse_steps;
+  if (err != FSI_OK) return fail(err, err_msg);
+  return FSI_OK;
+}
+
+}  // namespace
+
 int fsi_record_error(int code, const std::string& msg) { return fail(code, msg); }
 
 extern "C" {
+
+int fsi_dense_invert(int S, int n, const double* A, double* inv, int method, void* stream) {
+  if (S < 1 || n < 1 || !A || !inv || method < 0 || method > 1) return fail(FSI_EINVAL, "bad dense inverse arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<void*> own;
+  double* D = nullptr;
+  int *perm = nullptr, *status = nullptr;
+  uint8_t* act = nullptr;
+  auto release = [&](int rc) {
+    cudaStreamSynchronize(st);
+    for (void* q : own) cudaFree(q);
+    return rc;
+  };
+  if (dalloc(own, &D, (size_t)S * n * n) || dalloc(own, &perm, (size_t)S * n) || dalloc(own, &status, S) ||
+      dalloc(own, &act, S))
+    return release(FSI_ENOMEM);
+  std::vector<uint8_t> ones(S, 1);
+  std::vector<int> zeros(S, 0), st_h(S);
+  int rc = FSI_OK;
+  if (cudaMemcpyAsync(D, A, (size_t)S * n * n * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(act, ones.data(), S, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(status, zeros.data(), S * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return release(fail(FSI_ECUDA, "dense inverse copies failed"));
+  rc = dense_invert<double>(S, n, D, perm, act, inv, status, st, method);
+  if (rc != FSI_OK) return release(rc);
+  if (cudaMemcpyAsync(st_h.data(), status, S * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return release(fail(FSI_ECUDA, "dense inverse failed"));
+  for (int s = 0; s < S; ++s)
+    if (st_h[s] != 0) return release(fail(FSI_EJAC, "singular matrix in the dense inverse"));
+  return release(FSI_OK);
+}
 
 int fsi_mesh_size(const fsi_mesh* mesh, int* n_nodes, int* n_dofs, int* nnzb) {
   if (!n_nodes || !n_dofs || !nnzb) return fail(FSI_EINVAL, "null output");
@@ -1350,6 +1661,8 @@ const char* fsi_last_error(void) { return g_err.c_str(); }
 
 void fsi_destroy(fsi_ctx* c) {
   if (!c) return;
+  if (c->sweep) fsi_destroy(c->sweep);
+  if (c->sweep_stream) cudaStreamDestroy(c->sweep_stream);
   for (auto& kv : c->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1371,6 +1684,15 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
     return rc;
   };
   c->prm = *p;
+  c->mesh_xb.assign(mesh->x_breaks, mesh->x_breaks + mesh->n_xseg + 1);
+  c->mesh_yb.assign(mesh->y_breaks, mesh->y_breaks + mesh->n_yseg + 1);
+  c->mesh_nx.assign(mesh->nx_seg, mesh->nx_seg + mesh->n_xseg);
+  c->mesh_ny.assign(mesh->ny_seg, mesh->ny_seg + mesh->n_yseg);
+  c->mesh_desc = *mesh;
+  c->mesh_desc.x_breaks = c->mesh_xb.data();
+  c->mesh_desc.y_breaks = c->mesh_yb.data();
+  c->mesh_desc.nx_seg = c->mesh_nx.data();
+  c->mesh_desc.ny_seg = c->mesh_ny.data();
   c->S = p->max_batch;
   c->m = p->gmres_restart;
   c->P = Phys{p->rho_f, p->nu_f, p->rho_s, p->mu_s, p->lambda_s, p->vbar, p->ramp_t,
@@ -1511,7 +1833,6 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
   cudaStream_t st = (cudaStream_t)stream;
   const int N = c->prm.n_slices;
   const size_t n = c->n;
-  const double dt = c->prm.T / N;
   fsi_parareal_stats loc{};
   if (stats) {
     loc.history = stats->history;
@@ -1523,56 +1844,12 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
         dalloc(c->owned, &c->Cnew, n) || dalloc(c->owned, &c->ppart, (size_t)c->red_blocks * 6))
       return FSI_ENOMEM;
   }
-  std::vector<double> t(N);
-  for (int i = 0; i < N; ++i) t[i] = i * dt;
-  // predictor sweep (iteration 0)
-  for (int i = 0; i < N; ++i) {
-    TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cold + (size_t)i * n, false, &loc.coarse, st));
-    CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    loc.coarse_steps += c->prm.m_coarse;
-  }
-  std::vector<double> part(c->red_blocks * 6);
-  int it = 0;
-  for (it = 1; it <= max_iter && it <= N; ++it) {
-    const int first = it - 1;
-    const int S = N - first;
-    // fine solves of every slice that is not yet exact, batched
-    TRY(propagate_chunked(c, S, U + (size_t)first * n, &t[first], c->Fv + (size_t)first * n, true, &loc.fine, st));
-    loc.fine_steps += (long long)S * c->prm.m_fine;
-    double inc[3] = {0, 0, 0};
-    for (int i = first; i < N; ++i) {
-      const double* Cn;
-      if (i == first) {
-        Cn = c->Cold + (size_t)i * n;   // unchanged input: C(U_i^it) - C(U_i^(it-1)) = 0 exactly
-      } else {
-        TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cnew, false, &loc.coarse, st));
-        loc.coarse_steps += c->prm.m_coarse;
-        Cn = c->Cnew;
-      }
-      const int nrb = c->red_blocks;
-      LAUNCH(KI_PARAREAL_CORRECT, k_parareal_correct, (nrb), RED_THREADS, 0, st, (int)n, c->Fv + (size_t)i * n, Cn, c->Cold + (size_t)i * n, U + (size_t)(i + 1) * n, c->ppart);
-      TRY(launch_check());
-      if (i != first)
-        CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(part.data(), c->ppart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      double a[6] = {0, 0, 0, 0, 0, 0};
-      for (int b = 0; b < c->red_blocks; ++b)
-        for (int f = 0; f < 6; ++f) a[f] += part[b * 6 + f];
-      for (int f = 0; f < 3; ++f) {
-        const double rel = a[3 + f] > 0 ? std::sqrt(a[f] / a[3 + f]) : std::sqrt(a[f]);
-        if (!std::isfinite(rel)) return fail(FSI_EDIVERGE, "Parareal increment is not finite");
-        inc[f] = std::max(inc[f], rel);
-      }
-    }
-    loc.increment_v = inc[0];
-    loc.increment_u = inc[1];
-    loc.increment_p = inc[2];
-    if (loc.history && it - 1 < loc.history_len)
-      for (int f = 0; f < 3; ++f) loc.history[(it - 1) * 3 + f] = inc[f];
-    loc.iterations = it;
-    if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
-  }
+  int rc;
+  if (c->prm.pipeline_chunk > 0 && max_iter > 0 && N > 1)
+    rc = parareal_pipelined(c, U, max_iter, tol, loc, st);
+  else
+    rc = parareal_serial(c, U, max_iter, tol, loc, st);
+  if (rc != FSI_OK) return rc;
   if (stats) *stats = loc;
   return FSI_OK;
 }

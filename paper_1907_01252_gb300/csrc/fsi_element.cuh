@@ -64,6 +64,10 @@ struct QpDerived {
   double Jh;            // (J_{n-1} + J_n) / 2
   double w[2];          // u_n - u_{n-1}
   double M[2];          // Gh Bh w
+  // products shared by every direction of the linearisation
+  double invJ, invJ2;   // 1 / J, 1 / J^2
+  double Bw[2], Av[2];  // Bh w, A v
+  M2 GhBh, GA, AC, GtC, CGt;   // Gh Bh, G A, A C, G^T C, C G^T
 };
 
 __device__ inline void derive(const QpIn& q, QpDerived& d) {
@@ -83,9 +87,16 @@ __device__ inline void derive(const QpIn& q, QpDerived& d) {
   d.Jh = 0.5 * (d.J + d.Jo);
   d.w[0] = q.u[0] - q.uo[0];
   d.w[1] = q.u[1] - q.uo[1];
-  double t[2];
-  mv(d.Bh, d.w, t);
-  mv(d.Gh, t, d.M);
+  mv(d.Bh, d.w, d.Bw);
+  mv(d.Gh, d.Bw, d.M);
+  d.invJ = 1.0 / d.J;
+  d.invJ2 = d.invJ * d.invJ;
+  mv(d.A, q.v, d.Av);
+  d.GhBh = mul(d.Gh, d.Bh);
+  d.GA = mul(q.G, d.A);
+  d.AC = mul(d.A, d.C);
+  d.GtC = mul(tp(q.G), d.C);
+  d.CGt = mul(d.C, tp(q.G));
 }
 
 // First Piola stress of the St. Venant-Kirchhoff solid: F (2 mu E + lambda tr E I).
@@ -140,35 +151,29 @@ __device__ inline void qp_flux_lin(const Phys& P, const QpIn& q, const QpDerived
     const double dJ = trace(mul(d.A, dH));      // d det F = tr(adj(F) dF)
     const M2 dA = adj(dH);                       // adj is linear in 2D
     const M2 dC = tp(dA);
-    // ALE mass / domain convection term with midpoint means
+    // ALE mass / domain convection term with midpoint means:
+    // d(Gh Bh w) = dGh Bh w + Gh dBh w + Gh Bh dw, dBh = -Bh dFh Bh, dFh = dH / 2
     const double dJh = 0.5 * dJ;
-    const M2 dGh = 0.5 * dG;
-    const M2 dBh = -0.5 * mul(mul(d.Bh, dH), d.Bh);
     double t1[2], t2[2], t3[2], t4[2], dM[2];
-    mv(d.Bh, d.w, t1);
-    mv(dGh, t1, t2);
-    mv(dBh, d.w, t1);
-    mv(d.Gh, t1, t3);
-    mv(d.Bh, du, t1);
-    mv(d.Gh, t1, t4);
-    for (int c = 0; c < 2; ++c) dM[c] = t2[c] + t3[c] + t4[c];
+    mv(dG, d.Bw, t2);
+    mv(dH, d.Bw, t1);
+    mv(d.GhBh, t1, t3);
+    mv(d.GhBh, du, t4);
+    for (int c = 0; c < 2; ++c) dM[c] = 0.5 * t2[c] - 0.5 * t3[c] + t4[c];
     // convection G A v
-    double Av[2], dGAv[2], GdAv[2], GAdv[2];
-    mv(d.A, q.v, Av);
-    mv(dG, Av, dGAv);
+    double dGAv[2], GdAv[2], GAdv[2];
+    mv(dG, d.Av, dGAv);
     mv(dA, q.v, t1);
     mv(q.G, t1, GdAv);
-    mv(d.A, dv, t1);
-    mv(q.G, t1, GAdv);
+    mv(d.GA, dv, GAdv);
     for (int c = 0; c < 2; ++c) {
       out[c * 3] = rf * (dJh * ((q.v[c] - q.vo[c]) - d.M[c]) + d.Jh * (dv[c] - dM[c])) +
                    kt * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
     }
-    // stress (rho nu / J) Q - p C
-    M2 Gt = tp(q.G), dGt = tp(dG);
-    M2 dQ = mul(mul(dG, d.A), d.C) + mul(mul(q.G, dA), d.C) + mul(mul(q.G, d.A), dC) + mul(mul(dC, Gt), d.C) +
-            mul(mul(d.C, dGt), d.C) + mul(mul(d.C, Gt), dC);
-    M2 S = kt * ((rn / d.J) * dQ - (rn * dJ / (d.J * d.J)) * d.Q - dp * d.C - q.p * dC) - (kto * dp) * d.Co;
+    // stress (rho nu / J) Q - p C, Q = G A C + C G^T C
+    M2 dQ = mul(dG, d.AC) + mul(mul(q.G, dA), d.C) + mul(d.GA, dC) + mul(dC, d.GtC) +
+            mul(mul(d.C, tp(dG)), d.C) + mul(d.CGt, dC);
+    M2 S = kt * ((rn * d.invJ) * dQ - (rn * dJ * d.invJ2) * d.Q - dp * d.C - q.p * dC) - (kto * dp) * d.Co;
     out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
     M2 Hh = kt * dH;
     out[7] = Hh.a; out[8] = Hh.b; out[10] = Hh.c; out[11] = Hh.d;

@@ -9,6 +9,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "fsi_element.cuh"
 
 // --------------------------------------------------------------------------
@@ -237,7 +239,7 @@ __global__ void k_apply_dirichlet(DevMesh m, Phys P, double* __restrict__ U, siz
 // K[(i,ci),(j,cj)] = sum_q w_q sum_{a,b} B_a(i,q) D_q[(ci,a),(cj,b)] B_b(j,q)
 // with D_q the linearised flux (15 test slots x 15 trial directions).
 // --------------------------------------------------------------------------
-constexpr int JAC_THREADS = 128;
+constexpr int JAC_THREADS = 160;   // one round for the 9 x 15 tangent directions
 
 // Field blocks (test component ci, trial component cj) of the element
 // matrix that can be nonzero (the LPS pressure block is added separately).
@@ -366,13 +368,27 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     }
   }
   __syncthreads();
-  // Two-stage contraction, one quadrature point at a time:
+  // Two-stage contraction over the field blocks (ci, cj) that the cell's
+  // material couples, one quadrature point at a time:
   //   E[(ci,a)][(j,cj)] = w_q sum_b D_q[(ci,a)][(cj,b)] B_b(j,q)
   //   K[(i,ci)][(j,cj)] += sum_a B_a(i,q) E[(ci,a)][(j,cj)]
-  // Field blocks (ci, cj) that vanish for the cell's material are skipped.
+  // Work items run over the coupled blocks only (81 entries of K, 27 of E per
+  // block), so warps carry no structurally zero entries; the remaining blocks
+  // are zero or closed-form stabilisation terms, written separately.
   __shared__ TC sE[15][45];
   __shared__ TC sB[3][9];
-  constexpr int PER = (2025 + JAC_THREADS - 1) / JAC_THREADS;
+  __shared__ unsigned char sBlk[25];
+  __shared__ int sNb;
+  if (tid == 0) {
+    int nb = 0;
+    for (int b = 0; b < 25; ++b)
+      if (OLD ? jac_old_block_nonzero(solid, b / 5, b % 5) : jac_block_nonzero(solid, b / 5, b % 5))
+        sBlk[nb++] = (unsigned char)b;
+    sNb = nb;
+  }
+  __syncthreads();
+  const int nK = sNb * 81, nE = sNb * 27;
+  constexpr int PER = (16 * 81 + JAC_THREADS - 1) / JAC_THREADS;   // at most 16 coupled blocks
   TC acc[PER];
 #pragma unroll
   for (int r = 0; r < PER; ++r) acc[r] = 0;
@@ -383,49 +399,59 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
       sB[1][tid] = (TC)(c_dps[q][tid] * ihx);
       sB[2][tid] = (TC)(c_dpt[q][tid] * ihy);
     }
-    __syncthreads();
-    for (int e = tid; e < 15 * 45; e += JAC_THREADS) {
-      const int slot = e / 45, col = e % 45, j = col / 5, cj = col % 5;
-      const double* Dr = sD[q][slot] + cj * 3;
-      sE[slot][col] = (TC)(wq * (Dr[0] * c_phi[q][j] + Dr[1] * (c_dps[q][j] * ihx) + Dr[2] * (c_dpt[q][j] * ihy)));
+    for (int f = tid; f < nE; f += JAC_THREADS) {
+      const int blk = sBlk[f / 27], r = f % 27, a = r / 9, j = r % 9;
+      const int ci = blk / 5, cj = blk % 5;
+      const double* Dr = sD[q][ci * 3 + a] + cj * 3;
+      sE[ci * 3 + a][j * 5 + cj] =
+          (TC)(wq * (Dr[0] * c_phi[q][j] + Dr[1] * (c_dps[q][j] * ihx) + Dr[2] * (c_dpt[q][j] * ihy)));
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
       const int e = tid + r * JAC_THREADS;
-      if (e < 2025) {
-        const int row = e / 45, col = e % 45;
-        const int i = row / 5, ci = row % 5, cj = col % 5;
-        if (OLD ? jac_old_block_nonzero(solid, ci, cj) : jac_block_nonzero(solid, ci, cj))
-          acc[r] += sB[0][i] * sE[ci * 3][col] + sB[1][i] * sE[ci * 3 + 1][col] + sB[2][i] * sE[ci * 3 + 2][col];
+      if (e < nK) {
+        const int blk = sBlk[e / 81], w = e % 81, i = w / 9, j = w % 9;
+        const int ci = blk / 5, col = j * 5 + blk % 5;
+        acc[r] += sB[0][i] * sE[ci * 3][col] + sB[1][i] * sE[ci * 3 + 1][col] + sB[2][i] * sE[ci * 3 + 2][col];
       }
     }
     __syncthreads();
   }
   TC* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
+  // coupled blocks: the contraction, plus the outflow-edge term of the momentum rows
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int e = tid + r * JAC_THREADS;
-    if (e >= 2025) continue;
-    const int row = e / 45, col = e % 45;
-    const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
+    if (e >= nK) continue;
+    const int blk = sBlk[e / 81], w = e % 81, i = w / 9, j = w % 9;
+    const int ci = blk / 5, cj = blk % 5;
     double v = (double)acc[r];
-    if (!OLD && !solid && ci == 4 && cj == 4)
-      v += k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
-    if (OLD && !solid && ci == 4 && cj < 2) {
-      double mj = 0.0, ws = 0.0;   // d vbar / d v_{n-1} at local node j
-      for (int q = 0; q < 9; ++q) {
-        mj += c_wq[q] * c_phi[q][j];
-        ws += c_wq[q];
-      }
-      v += k * sSp[i] * sDalpha[cj] * (mj / ws);
-    }
     if (outflow && ci < 2 && cj < 4) {
       for (int q = 0; q < 3; ++q) {
         const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
         const double* Drow = sDe[q][ci] + cj * 3;
         v += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
       }
+    }
+    out[(i * 5 + ci) * 45 + j * 5 + cj] = (TC)v;
+  }
+  // the other blocks: zero, the stabilisation block (fluid p-p), or, for the
+  // old state, the derivative of the stabilisation weight (fluid p-v)
+  for (int e = tid; e < 2025; e += JAC_THREADS) {
+    const int row = e / 45, col = e % 45;
+    const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
+    if (OLD ? jac_old_block_nonzero(solid, ci, cj) : jac_block_nonzero(solid, ci, cj)) continue;
+    double v = 0.0;
+    if (!OLD && !solid && ci == 4 && cj == 4)
+      v = k * sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
+    if (OLD && !solid && ci == 4 && cj < 2) {
+      double mj = 0.0, ws = 0.0;   // d vbar / d v_{n-1} at local node j
+      for (int q = 0; q < 9; ++q) {
+        mj += c_wq[q] * c_phi[q][j];
+        ws += c_wq[q];
+      }
+      v = k * sSp[i] * sDalpha[cj] * (mj / ws);
     }
     out[e] = (TC)v;
   }
@@ -741,6 +767,122 @@ constexpr int GJ_THREADS = 1024;
 
 // In-place Gauss-Jordan inversion with partial pivoting of D[s] (n x n,
 // row-major); the inverse is written transposed to inv[s].
+// The same in-place Gauss-Jordan inversion on a thread-block cluster of
+// GJC_CTAS CTAs per slice: CTA c keeps rows [c rows_per, (c + 1) rows_per) in
+// shared memory; per pivot step the CTAs agree on the pivot (local maxima
+// exchanged through distributed shared memory), every CTA copies the pivot row
+// from its owner, the two rows are swapped, and each CTA eliminates its own
+// rows. Pivot choice, scaling and elimination are those of k_dense_invert, so
+// both kernels give the same inverse. Two cluster barriers per step; every
+// CTA of a cluster takes the same branches, so all reach every barrier.
+constexpr int GJC_CTAS = 8;
+constexpr int GJC_THREADS = 256;
+
+template <typename T>
+__host__ __device__ inline size_t gjc_smem_bytes(int n) {
+  const int rows_per = (n + GJC_CTAS - 1) / GJC_CTAS;
+  return ((size_t)rows_per * n + 2 * (size_t)n + 2) * sizeof(T) + ((size_t)n + 2) * sizeof(int);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GJC_THREADS) k_dense_invert_cluster(int n, const T* __restrict__ D,
+                                                                      const uint8_t* __restrict__ active,
+                                                                      T* __restrict__ inv, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = blockIdx.y;
+  if (!active[s]) return;   // uniform over the cluster (one slice per cluster)
+  const int rank = (int)cluster.block_rank();
+  const int rows_per = (n + GJC_CTAS - 1) / GJC_CTAS;
+  const int r0 = rank * rows_per, r1 = min(n, r0 + rows_per);
+  extern __shared__ __align__(16) unsigned char gjc_raw[];
+  T* rows = reinterpret_cast<T*>(gjc_raw);     // [rows_per][n], local row r - r0
+  T* prow = rows + (size_t)rows_per * n;       // [n] pivot row (copy)
+  T* tmp = prow + n;                           // [n] row kk, moving to row p
+  T* cand_v = tmp + n;                         // [1] local pivot candidate
+  int* cand_i = reinterpret_cast<int*>(cand_v + 2);   // [1]
+  int* pr = cand_i + 2;                        // [n] row permutation
+  __shared__ T red_v[GJC_THREADS / 32];
+  __shared__ int red_i[GJC_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const T* Ms = D + (size_t)s * n * n;
+  for (int e = tid; e < (r1 - r0) * n; e += GJC_THREADS) rows[e] = Ms[(size_t)r0 * n + e];
+  for (int r = tid; r < n; r += GJC_THREADS) pr[r] = r;
+  __syncthreads();
+  for (int kk = 0; kk < n; ++kk) {
+    // local candidate among rows >= kk
+    T best = -1;
+    int bi = n;
+    for (int r = max(kk, r0) + tid; r < r1; r += GJC_THREADS) {
+      const T a = fabs(rows[(size_t)(r - r0) * n + kk]);
+      if (a > best) { best = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      T b = red_v[0];
+      int ii = red_i[0];
+      for (int w = 1; w < GJC_THREADS / 32; ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
+      cand_v[0] = b;
+      cand_i[0] = ii;
+    }
+    cluster.sync();   // S1: candidates published; the previous step's writes are complete
+    // the pivot: largest candidate, ties to the lowest row (computed alike in every CTA)
+    T b = -1;
+    int p = n;
+    for (int c = 0; c < GJC_CTAS; ++c) {
+      const T v = *cluster.map_shared_rank(cand_v, c);
+      const int i = *cluster.map_shared_rank(cand_i, c);
+      if (v > b || (v == b && i < p)) { b = v; p = i; }
+    }
+    if (!(b > 0)) {   // singular (same decision in every CTA)
+      if (rank == 0 && tid == 0) status[s] = -6;
+      cluster.sync();   // the candidates may still be read remotely
+      return;
+    }
+    const int op = p / rows_per, ok = kk / rows_per;
+    const T* rp = cluster.map_shared_rank(rows, op) + (size_t)(p - op * rows_per) * n;
+    for (int c = tid; c < n; c += GJC_THREADS) prow[c] = rp[c];
+    if (p != kk && rank == op) {   // the owner of row p takes row kk's content
+      const T* rk = cluster.map_shared_rank(rows, ok) + (size_t)(kk - ok * rows_per) * n;
+      for (int c = tid; c < n; c += GJC_THREADS) tmp[c] = rk[c];
+    }
+    if (p != kk && tid == 0) { const int t1 = pr[kk]; pr[kk] = pr[p]; pr[p] = t1; }
+    cluster.sync();   // S2: every remote read of this step is done
+    const T d = T(1) / prow[kk];
+    __syncthreads();
+    for (int c = tid; c < n; c += GJC_THREADS) prow[c] = (c == kk) ? d : prow[c] * d;
+    if (p != kk && rank == op)
+      for (int c = tid; c < n; c += GJC_THREADS) rows[(size_t)(p - r0) * n + c] = tmp[c];
+    __syncthreads();
+    if (rank == ok)
+      for (int c = tid; c < n; c += GJC_THREADS) rows[(size_t)(kk - r0) * n + c] = prow[c];
+    // eliminate column kk from every other local row, one warp per row (every
+    // lane reads the row's factor before any lane overwrites column kk)
+    for (int lr = warp; lr < r1 - r0; lr += GJC_THREADS / 32) {
+      if (lr + r0 == kk) continue;
+      T* row = rows + (size_t)lr * n;
+      const T f = row[kk];
+      __syncwarp();
+      for (int c = lane; c < n; c += 32) row[c] = (c == kk) ? -f * d : row[c] - f * prow[c];
+    }
+    __syncthreads();
+  }
+  // undo the row permutation on the columns: inv[:, pr[c]] = M[:, c] (row-major)
+  T* out = inv + (size_t)s * n * n;
+  for (int e = tid; e < (r1 - r0) * n; e += GJC_THREADS) {
+    const int lr = e / n, c = e % n;
+    out[(size_t)(lr + r0) * n + pr[c]] = rows[e];
+  }
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 template <typename T>
 __global__ void __launch_bounds__(GJ_THREADS) k_dense_invert(int n, T* __restrict__ D, int* __restrict__ perm,
                                                              const uint8_t* __restrict__ active,

@@ -37,7 +37,8 @@ class fsi_params(C.Structure):
                 ("mg_coarsest_max_dofs", C.c_int), ("mg_smooth", C.c_int), ("mg_omega", C.c_double),
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
-                ("graph_max_batch", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int)]
+                ("graph_max_batch", C.c_int), ("precision", C.c_int), ("pipeline_chunk", C.c_int),
+                ("max_batch", C.c_int)]
 
 
 class fsi_stats(C.Structure):
@@ -89,6 +90,7 @@ SIGNATURES = {
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+    "fsi_dense_invert": (_I, [_I, _I, _VP, _VP, _I, _VP]),
     "fsi_mesh_size": (_I, [C.POINTER(fsi_mesh), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "fsi_batch_plan": (_I, [C.POINTER(fsi_instance), _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D),
                             C.POINTER(_D)]),
@@ -193,10 +195,19 @@ def _params(w: wl.Workload, max_batch: int, overrides):
              m_coarse=w.m_coarse, newton_tol=w.newton_tol, newton_maxit=w.newton_maxit,
              gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
              gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
-             mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.25, mg_reuse=2,
-             mg_rebuild_every=4, graph_max_batch=4, precision=0, max_batch=max_batch)
+             mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.5, mg_reuse=2,
+             mg_rebuild_every=4, graph_max_batch=4, precision=0, pipeline_chunk=0, max_batch=max_batch)
     p.update(overrides)
     return p
+
+
+def dense_invert(A, method=0):
+    """Inverse of a device batch [S, n, n] of float64 matrices by the library's
+    coarsest-level solver (method 0: cluster kernel when it fits, 1: one CTA per matrix)."""
+    import torch
+    inv = torch.empty_like(A)
+    _check(load_library().fsi_dense_invert(A.shape[0], A.shape[1], _ptr(A), _ptr(inv), method, _stream()))
+    return inv
 
 
 def mesh_size(w: wl.Workload):

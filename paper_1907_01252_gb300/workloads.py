@@ -107,6 +107,25 @@ LARGE_128x32 = Workload("fsi2d_q2_128x32_T2_64x32", nx=128, ny=32, T=2.0, n_slic
 WORKLOADS = {w.name: w for w in (SMALL_16x4, LARGE_128x32)}
 
 
+def node_axis(breaks, counts):
+    """Node coordinates of the Q2 mesh along one axis: 2 n + 1 uniform nodes per
+    segment of n cells, shared at the break points."""
+    out = [breaks[0]]
+    for (a, b), n in zip(zip(breaks[:-1], breaks[1:]), counts):
+        out.extend(a + (b - a) * (np.arange(1, 2 * n + 1) / (2 * n)))
+    return np.array(out)
+
+
+def tip_node(w):
+    """Index of the node at the top centre of the solid box (node (i, j) has id j * (2 nx + 1) + i)."""
+    xn, yn = node_axis(X_BREAKS, w.nx_seg), node_axis(Y_BREAKS, w.ny_seg)
+    (x0, x1), (_, y1) = SOLID_BOX
+    i, j = int(np.argmin(abs(xn - 0.5 * (x0 + x1)))), int(np.argmin(abs(yn - y1)))
+    if abs(xn[i] - 0.5 * (x0 + x1)) > 1e-12 or abs(yn[j] - y1) > 1e-12:
+        raise ValueError("no node at the bar tip")
+    return j * len(xn) + i
+
+
 def uneven_batch(n=48, seed=1907, ny_range=(16, 48), slice_range=(16, 32), T=1.0, m_fine=16):
     """n independent instances of the channel problem with uneven meshes and
     materials, seeded: ny uniform on ny_range with nx = 4 ny; mu_s log-uniform

@@ -89,3 +89,10 @@ def test_bad_plan_arguments_are_rejected(fsi):
     with pytest.raises(fsi.FsiError) as e:
         _plan(fsi, wl.uneven_batch(n=2), 0)
     assert e.value.code == fsi.FSI_EINVAL
+
+
+@pytest.mark.parametrize("w", [wl.SMALL_16x4, wl.LARGE_128x32])
+def test_tip_node_is_the_oracle_mesh_node_at_the_bar_tip(w):
+    mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
+    t = wl.tip_node(w)
+    assert abs(mesh.node_x[t] - 0.65) < 1e-12 and abs(mesh.node_y[t] - 0.2) < 1e-12

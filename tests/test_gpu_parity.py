@@ -219,6 +219,28 @@ def test_parareal_matches_oracle_iterates_and_reaches_serial():
             assert max(errs.values()) <= 1e-10, (iters, n, errs)
 
 
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_pipelined_parareal_is_bitwise_the_serial_schedule(chunk):
+    """The pipelined schedule (sweeps on a helper thread and stream, fine solves
+    in batches as their inputs appear) changes when things run, not what."""
+    w = wl.Workload("pipe", nx=16, ny=4, T=0.5, n_slices=5, m_fine=3)
+    ref_ctx = ctx_for(w, w.n_slices)
+    ctx = ctx_for(w, w.n_slices, pipeline_chunk=chunk)
+    for iters in (1, 3, w.n_slices):
+        U = torch.zeros((w.n_slices + 1, ref_ctx.n_dofs), dtype=torch.float64, device=DEV)
+        Ur, sr = ref_ctx.parareal_iterate(U.clone(), iters, 0.0)
+        Up, sp = ctx.parareal_iterate(U.clone(), iters, 0.0)
+        assert torch.equal(Up, Ur), iters
+        for key in ("iterations", "increment_v", "increment_u", "increment_p", "fine_steps", "coarse_steps"):
+            assert sp[key] == sr[key], (iters, key)
+        assert sp["fine"]["gmres_iters"] == sr["fine"]["gmres_iters"]
+        assert sp["coarse"]["gmres_iters"] == sr["coarse"]["gmres_iters"]
+    # a tolerance that stops early stops at the same iteration
+    Ur, sr = ref_ctx.parareal_iterate(torch.zeros_like(U), w.n_slices, 0.05)
+    Up, sp = ctx.parareal_iterate(torch.zeros_like(U), w.n_slices, 0.05)
+    assert sp["iterations"] == sr["iterations"] and torch.equal(Up, Ur)
+
+
 def test_multiplicative_smoother_step_matches_oracle():
     """The coloured multiplicative Vanka smoother changes only the preconditioner."""
     w = wl.SMALL_16x4
