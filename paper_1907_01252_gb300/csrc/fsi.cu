@@ -135,6 +135,11 @@ void build_mesh(HostMesh& m, bool has_solid, const double box[4]) {
       m.node_flags[n] = f;
       m.node_y[n] = m.yn[j];
     }
+  for (int c = 0; c < m.n_cells; ++c) {
+    bool dec = !(m.cell_flags[c] & CF_SOLID);
+    for (int l = 0; l < 9 && dec; ++l) dec = !(m.node_flags[m.cell_nodes[c * 9 + l]] & NF_IN_SOLID);
+    if (dec) m.cell_flags[c] |= CF_U_DECOUPLED;
+  }
   // node -> (cell, local) in ascending cell order
   m.node_cells.assign(m.n_nodes * 4, -1);
   std::vector<int> cnt(m.n_nodes, 0);
@@ -447,7 +452,7 @@ struct fsi_ctx {
   int n_act = 0;        // slices set in `active` (host mirror, for work accounting)
   int tip = -1;         // node at the top centre of the solid box (adjoint functional)
   // CUDA graphs of one FGMRES iteration for small batches, keyed by
-  // (scalar size, batch, Krylov index); captured on an internal stream
+  // (scalar sizes and transposition, batch, Krylov index); captured on an internal stream
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     unsigned epoch = 0;
@@ -468,6 +473,7 @@ struct fsi_ctx {
   std::vector<int> mesh_nx, mesh_ny;
   fsi_mesh mesh_desc{};
   fsi_ctx* sweep = nullptr;
+  bool transposed = false;   // the multigrid hierarchy holds transposed operators (adjoint solves)
   cudaStream_t sweep_stream = nullptr;
   double* Uin = nullptr;
 };
@@ -746,6 +752,7 @@ template <typename T>
 int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, double theta, const uint8_t* act,
              cudaStream_t st, bool keep_coarsest = false, bool transpose = false) {
   const int NL = (int)c->lev.size();
+  c->transposed = transpose;
   const double* Ul = U;
   const double* Uol = Uold;
   for (int l = 0; l < NL; ++l) {
@@ -810,7 +817,10 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
           TRY((spmv<T, true>(L, S, A, x, b, act, r, st, L.col_nodes[k], nn)));
           rr = r;
         }
-        LAUNCH_W(2.0 * 2025 * nc * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)nc * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, L.col_cells[k], nc);
+        if (c->transposed)   // transposed operators lack the displacement-row structure
+          LAUNCH_W(2.0 * 2025 * nc * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)nc * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, L.col_cells[k], nc);
+        else
+        LAUNCH_W(2.0 * 2025 * nc * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell_split<T>, (dim3(nblk((size_t)nc, VKS_CELLS), S)), VKS_THREADS, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, L.col_cells[k], nc);
         LAUNCH(KI_VANKA_SCATTER, k_vanka_scatter<T>, (dim3(nblk((size_t)nn * 5, 128), S)), 128, 0, st, L.h.n_cells, L.col_nodes[k], L.col_src[k], nn, cellbuf, om, L.n, act, x);
       }
       return launch_check();
@@ -820,7 +830,10 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
       TRY((spmv<T, true>(L, S, A, x, b, act, r, st)));
       rr = r;
     }
-    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, (const int*)nullptr, L.h.n_cells);
+    if (c->transposed)   // transposed operators lack the displacement-row structure
+      LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell<T>, (dim3(nblk((size_t)L.h.n_cells * 45, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, (const int*)nullptr, L.h.n_cells);
+    else
+    LAUNCH_W(2.0 * 2025 * L.h.n_cells * (double)c->n_act, KI_VANKA_CELL, k_vanka_cell_split<T>, (dim3(nblk((size_t)L.h.n_cells, VKS_CELLS), S)), VKS_THREADS, 0, st, L.dm, reinterpret_cast<const T*>(L.KV), rr, L.n, act, cellbuf, (const int*)nullptr, L.h.n_cells);
     LAUNCH(KI_VANKA_GATHER, k_vanka_gather<T>, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, cellbuf, om, L.n, act, x);
     return launch_check();
   };
@@ -925,7 +938,10 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
       };
       fsi_ctx::Graph* replayed = nullptr;
       if (S <= c->prm.graph_max_batch) {
-        fsi_ctx::Graph& ge = c->graphs[std::make_tuple((int)(sizeof(T) * 16 + sizeof(TP)), S, j)];
+        // the kernels a graph holds depend on the scalar types and on whether the
+        // operators are transposed (structured or generic Vanka apply)
+        fsi_ctx::Graph& ge =
+            c->graphs[std::make_tuple((int)(sizeof(T) * 16 + sizeof(TP)) * 2 + (c->transposed ? 1 : 0), S, j)];
         if (!ge.exec || ge.epoch != g_prof.epoch) {
           if (ge.exec) {
             cudaGraphExecDestroy(ge.exec);
