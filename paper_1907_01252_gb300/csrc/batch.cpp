@@ -19,6 +19,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -144,29 +145,36 @@ int fsi_batch_parareal(fsi_instance* inst, int n, int workers, void* stream) {
   std::vector<cudaStream_t> streams(W, nullptr);
   std::vector<std::thread> threads;
   threads.reserve(W);
-  for (int w = 0; w < W; ++w) {
-    threads.emplace_back([&, w] {
-      cudaSetDevice(dev);
-      if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+  auto worker_main = [&](int w) {
+    cudaSetDevice(dev);
+    if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (first_rc == FSI_OK) first_rc = FSI_ECUDA, first_msg = "worker stream creation failed";
+      streams[w] = nullptr;
+    } else {
+      cudaStreamWaitEvent(streams[w], start, 0);
+    }
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      if (!streams[w]) {   // no stream: leave the instance to the serial pass below
         std::lock_guard<std::mutex> lk(mu);
-        if (first_rc == FSI_OK) first_rc = FSI_ECUDA, first_msg = "worker stream creation failed";
-        streams[w] = nullptr;
-      } else {
-        cudaStreamWaitEvent(streams[w], start, 0);
+        deferred.push_back(order[k]);
+        continue;
       }
-      for (;;) {
-        const int k = next.fetch_add(1);
-        if (k >= n) break;
-        if (!streams[w]) {   // no stream: leave the instance to the serial pass below
-          std::lock_guard<std::mutex> lk(mu);
-          deferred.push_back(order[k]);
-          continue;
-        }
-        run_one(order[k], w, streams[w], true);
-      }
-    });
+      run_one(order[k], w, streams[w], true);
+    }
+  };
+  for (int w = 0; w < W; ++w) {
+    try {
+      threads.emplace_back(worker_main, w);
+    } catch (const std::system_error&) {   // fewer workers than asked for
+      break;
+    }
   }
   for (auto& t : threads) t.join();
+  // problems no worker took (no thread could be started) join the serial pass
+  for (int k = next.load(); k < n; ++k) deferred.push_back(order[k]);
   // instances that did not fit next to the others run one at a time
   std::sort(deferred.begin(), deferred.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   cudaStream_t s0 = nullptr;

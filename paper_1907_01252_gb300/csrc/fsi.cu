@@ -19,6 +19,7 @@
 #include <atomic>
 #include <cmath>
 #include <condition_variable>
+#include <system_error>
 #include <thread>
 #include <map>
 #include <mutex>
@@ -1524,7 +1525,8 @@ int parareal_pipelined(fsi_ctx* c, double* U, int max_iter, double tol, fsi_para
   int dev = 0;
   CK(cudaGetDevice(&dev));
 
-  std::thread sweeper([&] {
+  std::thread sweeper;
+  auto sweep_main = [&] {
     cudaSetDevice(dev);
     auto body = [&]() -> int {
       // predictor sweep U[i+1] = C(U[i]), which also gives the fine inputs of iteration 1
@@ -1582,7 +1584,12 @@ int parareal_pipelined(fsi_ctx* c, double* U, int max_iter, double tol, fsi_para
     };
     const int rc = body();
     if (rc != FSI_OK) fail_shared(rc);
-  });
+  };
+  try {
+    sweeper = std::thread(sweep_main);
+  } catch (const std::system_error&) {   // no thread to be had: the same iteration, unpipelined
+    return parareal_serial(c, U, max_iter, tol, loc, st);
+  }
 
   // the fine solves, on the calling thread in batches of B slices
   for (int it = 1; it <= K; ++it) {

@@ -96,3 +96,26 @@ def test_tip_node_is_the_oracle_mesh_node_at_the_bar_tip(w):
     mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
     t = wl.tip_node(w)
     assert abs(mesh.node_x[t] - 0.65) < 1e-12 and abs(mesh.node_y[t] - 0.2) < 1e-12
+
+
+def test_argument_errors_are_reported_before_any_device_work(fsi):
+    """These checks run on the host before any CUDA call, so they need no GPU."""
+    import ctypes as C
+    lib = fsi.load_library()
+    ws = wl.uneven_batch(n=2)
+    b = fsi.Batch(ws, max_iter=1, device_states=False)
+    # workers < 1, negative count, null states
+    assert lib.fsi_batch_parareal(b._inst, 2, 0, None) == fsi.FSI_EINVAL
+    assert lib.fsi_batch_parareal(b._inst, -1, 1, None) == fsi.FSI_EINVAL
+    assert lib.fsi_batch_parareal(b._inst, 2, 1, None) == fsi.FSI_EINVAL       # U pointers are NULL
+    assert "null state" in lib.fsi_last_error().decode()
+    assert lib.fsi_batch_parareal(b._inst, 0, 1, None) == fsi.FSI_OK           # nothing to do
+    cand = (C.c_int * 2)(1, 0)
+    secs = (C.c_double * 2)()
+    best = C.c_int()
+    assert lib.fsi_batch_autotune(b._inst, 2, cand, 2, secs, C.byref(best), None) == fsi.FSI_EINVAL
+    assert lib.fsi_dense_invert(0, 5, None, None, 0, None) == fsi.FSI_EINVAL
+    assert lib.fsi_dense_invert(1, 5, None, None, 2, None) == fsi.FSI_EINVAL
+    nodes, dofs, nnzb = C.c_int(), C.c_int(), C.c_int()
+    bad = fsi.fsi_mesh()
+    assert lib.fsi_mesh_size(C.byref(bad), C.byref(nodes), C.byref(dofs), C.byref(nnzb)) == fsi.FSI_EINVAL
