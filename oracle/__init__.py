@@ -19,6 +19,12 @@ Parity status (what pins each part lives in tests/test_oracle_*.py):
   * Parareal ........................... pinned (Dahlquist closed form,
                                           k = N reproduces the serial run)
   * speedup model ...................... pinned (value printed in Sec. 4.1)
+  * d-dimensional step (fsi_nd.py) ...... pinned: at d = 2 equal to fsi.py; at
+                                          d = 3 extrusion to 2D rows, y-z exchange
+                                          symmetry, helpers vs numpy, affine
+                                          divergence-free field, rigid solid
+                                          motion, Q1 kernel of the stabilisation,
+                                          inflow mean, finite differences, Newton
   * full FSI trajectory ................ parity unpinned: the paper prints no
                                           numbers for these workloads, so GPU vs
                                           oracle agreement is self-consistency.

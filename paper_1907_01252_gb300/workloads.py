@@ -107,6 +107,19 @@ LARGE_128x32 = Workload("fsi2d_q2_128x32_T2_64x32", nx=128, ny=32, T=2.0, n_slic
 WORKLOADS = {w.name: w for w in (SMALL_16x4, LARGE_128x32)}
 
 
+# 3D channel with an elastic plate on the bottom wall: channel [0, 1.5] x [0, 0.41] x [0, 0.41], plate
+# 0.05 x 0.2 x 0.3 at x in [0.4, 0.45] (the x position is not given; this is a reading), centred in z.
+X3_BREAKS = (0.0, 0.4, 0.45, 1.5)
+Y3_BREAKS = (0.0, 0.2, 0.41)
+Z3_BREAKS = (0.0, 0.055, 0.355, 0.41)
+SOLID_BOX_3D = ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355))
+
+
+def cells_per_segment_3d(nx, ny, nz):
+    """Cells per segment on the three axes of the 3D channel (32 x 8 x 8 -> 9/1/22, 4/4, 1/6/1)."""
+    return (cells_per_segment(X3_BREAKS, nx), cells_per_segment(Y3_BREAKS, ny), cells_per_segment(Z3_BREAKS, nz))
+
+
 def node_axis(breaks, counts):
     """Node coordinates of the Q2 mesh along one axis: 2 n + 1 uniform nodes per
     segment of n cells, shared at the break points."""
