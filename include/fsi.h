@@ -134,6 +134,12 @@ typedef struct fsi_stats {
   int max_newton;          /* most Newton iterations of one slice in one step */
   int max_gmres;           /* most FGMRES iterations of one slice in one solve */
   int status;              /* same code as the return value */
+  int* slice_status;       /* optional host array [slice_status_len] (NULL to skip):
+                              fsi_theta_step, fsi_fine and fsi_coarse set entry s of
+                              the call's S slices to FSI_OK, or to the first failure
+                              of slice s (FSI_ENAN, FSI_ENEWTON, FSI_EJAC, FSI_EGMRES);
+                              other entry points leave it alone */
+  int slice_status_len;
 } fsi_stats;
 
 typedef struct fsi_parareal_stats {

@@ -475,6 +475,10 @@ struct fsi_ctx {
   fsi_mesh mesh_desc{};
   fsi_ctx* sweep = nullptr;
   bool transposed = false;   // the multigrid hierarchy holds transposed operators (adjoint solves)
+  // per-slice outcome: the last FGMRES solve's code per slice (0, FSI_ENAN, FSI_EGMRES), and the
+  // index of the call's first slice within the caller's batch (fsi_stats.slice_status)
+  std::vector<int> slice_code;
+  int slice_offset = 0;
   cudaStream_t sweep_stream = nullptr;
   double* Uin = nullptr;
 };
@@ -881,9 +885,10 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
   int status = FSI_OK;
   // the caller's mask, restored on exit (the cycles below narrow c->active)
   const std::vector<uint8_t> act_entry = act;
+  c->slice_code.assign(S, 0);
   for (int s = 0; s < S; ++s)
     if (act[s] && !(bnorm[s] > 0.0)) {
-      if (!std::isfinite(bnorm[s])) status = FSI_ENAN;
+      if (!std::isfinite(bnorm[s])) status = c->slice_code[s] = FSI_ENAN;
       act[s] = 0;
     }
   auto any = [&]() { return std::any_of(act.begin(), act.end(), [](uint8_t a) { return a != 0; }); };
@@ -1007,8 +1012,8 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
           any_fin = true;
           if (conv || bad || its[s] >= c->prm.gmres_maxit) {
             act[s] = 0;
-            if (bad) status = FSI_ENAN;
-            else if (!conv) status = FSI_EGMRES;
+            if (bad) status = c->slice_code[s] = FSI_ENAN;
+            else if (!conv) status = c->slice_code[s] = FSI_EGMRES;
           }
         } else {
           any_left = true;
@@ -1082,7 +1087,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
   LAUNCH(KI_APPLY_DIRICHLET, k_apply_dirichlet, (dim3(nblk(L.h.n_nodes, 128), S)), 128, 0, st, L.dm, c->P, c->Uit, n, c->t_dev, c->active);
   TRY(launch_check());
   std::vector<double> r0(S, 0.0), nr(S);
-  std::vector<int> nit(S, 0);
+  std::vector<int> nit(S, 0), why(S, 0);   // why: first failure code per slice
   int status = FSI_OK;
   for (int it = 0;; ++it) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
@@ -1095,7 +1100,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     for (int s = 0; s < S; ++s) {
       if (!act[s]) continue;
       if (!std::isfinite(nr[s])) {
-        status = FSI_ENAN;
+        status = why[s] = FSI_ENAN;
         act[s] = 0;
         continue;
       }
@@ -1106,6 +1111,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
       }
       if (it >= c->prm.newton_maxit) {
         status = FSI_ENEWTON;
+        if (!why[s]) why[s] = FSI_ENEWTON;
         act[s] = 0;
         continue;
       }
@@ -1141,11 +1147,13 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
                                      target.data());
     CK(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s) {
       if (act[s] && st_h[s] != 0) {
-        status = FSI_EJAC;
+        status = why[s] = FSI_EJAC;
         act[s] = 0;
       }
+      if (act[s] && !why[s] && (int)c->slice_code.size() == S && c->slice_code[s]) why[s] = c->slice_code[s];
+    }
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed: " + g_err);
     if (rc == FSI_EGMRES) status = FSI_EGMRES;
   }
@@ -1154,6 +1162,9 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     for (int s = 0; s < S; ++s) {
       stats->newton_iters += nit[s];
       stats->max_newton = std::max(stats->max_newton, nit[s]);
+      const int idx = c->slice_offset + s;
+      if (stats->slice_status && idx < stats->slice_status_len && !stats->slice_status[idx])
+        stats->slice_status[idx] = why[s];
     }
     stats->status = status;
   }
@@ -1190,9 +1201,13 @@ int propagate(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1,
 int propagate_chunked(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, bool fine, fsi_stats* stats,
                       cudaStream_t st) {
   const int m = fine ? c->prm.m_fine : c->prm.m_coarse;
+  const int base = c->slice_offset;
   for (int s0 = 0; s0 < S; s0 += c->S) {
     const int b = std::min(c->S, S - s0);
-    TRY(propagate(c, b, U0 + (size_t)s0 * c->n, t0 + s0, U1 + (size_t)s0 * c->n, m, fine, stats, st));
+    c->slice_offset = base + s0;
+    const int rc = propagate(c, b, U0 + (size_t)s0 * c->n, t0 + s0, U1 + (size_t)s0 * c->n, m, fine, stats, st);
+    c->slice_offset = base;
+    if (rc != FSI_OK) return rc;
   }
   return FSI_OK;
 }
@@ -1821,10 +1836,24 @@ int fsi_bsr_spmv(fsi_ctx* c, int S, const double* vals, const double* x, double*
   return FSI_OK;
 }
 
+// Resets the statistics of a call, keeping the caller's per-slice array
+// (cleared for the call's S slices).
+static void reset_stats(fsi_ctx* c, fsi_stats* stats, int S) {
+  c->slice_offset = 0;
+  if (!stats) return;
+  int* ss = stats->slice_status;
+  const int len = stats->slice_status_len;
+  *stats = fsi_stats{};
+  stats->slice_status = ss;
+  stats->slice_status_len = len;
+  if (ss)
+    for (int s = 0; s < std::min(S, len); ++s) ss[s] = FSI_OK;
+}
+
 int fsi_theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, double k, double theta,
                    double* U_new, fsi_stats* stats, void* stream) {
   if (!c || !U_old || !t_old || !U_new) return fail(FSI_EINVAL, "null argument");
-  if (stats) *stats = fsi_stats{};
+  reset_stats(c, stats, S);
   // a single step may be large: keep at most the coarsest inverse across Newton iterations
   int rc = theta_step(c, S, U_old, t_old, k, theta, U_new, stats, (cudaStream_t)stream, std::min(c->prm.mg_reuse, 1),
                       false);
@@ -1835,7 +1864,7 @@ int fsi_theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, 
 int fsi_fine(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, fsi_stats* stats, void* stream) {
   if (!c || !U0 || !t0 || !U1) return fail(FSI_EINVAL, "null argument");
   if (S < 1) return fail(FSI_EINVAL, "empty batch");
-  if (stats) *stats = fsi_stats{};
+  reset_stats(c, stats, S);
   int rc = propagate_chunked(c, S, U0, t0, U1, true, stats, (cudaStream_t)stream);
   if (stats) stats->status = rc;
   return rc;
@@ -1844,7 +1873,7 @@ int fsi_fine(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, 
 int fsi_coarse(fsi_ctx* c, int S, const double* U0, const double* t0, double* U1, fsi_stats* stats, void* stream) {
   if (!c || !U0 || !t0 || !U1) return fail(FSI_EINVAL, "null argument");
   if (S < 1) return fail(FSI_EINVAL, "empty batch");
-  if (stats) *stats = fsi_stats{};
+  reset_stats(c, stats, S);
   int rc = propagate_chunked(c, S, U0, t0, U1, false, stats, (cudaStream_t)stream);
   if (stats) stats->status = rc;
   return rc;

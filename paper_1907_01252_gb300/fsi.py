@@ -43,10 +43,11 @@ class fsi_params(C.Structure):
 
 class fsi_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_longlong), ("gmres_iters", C.c_longlong), ("max_newton", C.c_int),
-                ("max_gmres", C.c_int), ("status", C.c_int)]
+                ("max_gmres", C.c_int), ("status", C.c_int), ("slice_status", C.POINTER(C.c_int)),
+                ("slice_status_len", C.c_int)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("slice_status")}
 
 
 class fsi_parareal_stats(C.Structure):
@@ -306,30 +307,40 @@ class Context:
         _check(self.lib.fsi_bsr_spmv(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
         return y
 
+    def _propagator_call(self, fn, S, *args):
+        """Call a propagator entry point with a per-slice status array; the statuses
+        are in the returned dict (and on the FsiError raised on failure)."""
+        ss = np.zeros(S, dtype=np.int32)
+        st = fsi_stats()
+        st.slice_status = ss.ctypes.data_as(C.POINTER(C.c_int))
+        st.slice_status_len = S
+        rc = fn(self.handle, S, *args, C.byref(st), _stream())
+        if rc != FSI_OK:
+            err = FsiError(rc, self.lib.fsi_last_error().decode())
+            err.slice_status = ss.tolist()
+            raise err
+        d = st.as_dict()
+        d["slice_status"] = ss.tolist()
+        return d
+
     def fsi_theta_step(self, U_old, t_old, k, theta, U_new=None):
         import torch
         U_new = torch.empty_like(U_old) if U_new is None else U_new
-        st = fsi_stats()
         t, tp = _dbl(t_old)
-        _check(self.lib.fsi_theta_step(self.handle, U_old.shape[0], _ptr(U_old), tp, k, theta, _ptr(U_new),
-                                       C.byref(st), _stream()))
-        return U_new, st.as_dict()
+        d = self._propagator_call(self.lib.fsi_theta_step, U_old.shape[0], _ptr(U_old), tp, k, theta, _ptr(U_new))
+        return U_new, d
 
     def fsi_fine(self, U0, t0, U1=None):
         import torch
         U1 = torch.empty_like(U0) if U1 is None else U1
-        st = fsi_stats()
         t, tp = _dbl(t0)
-        _check(self.lib.fsi_fine(self.handle, U0.shape[0], _ptr(U0), tp, _ptr(U1), C.byref(st), _stream()))
-        return U1, st.as_dict()
+        return U1, self._propagator_call(self.lib.fsi_fine, U0.shape[0], _ptr(U0), tp, _ptr(U1))
 
     def fsi_coarse(self, U0, t0, U1=None):
         import torch
         U1 = torch.empty_like(U0) if U1 is None else U1
-        st = fsi_stats()
         t, tp = _dbl(t0)
-        _check(self.lib.fsi_coarse(self.handle, U0.shape[0], _ptr(U0), tp, _ptr(U1), C.byref(st), _stream()))
-        return U1, st.as_dict()
+        return U1, self._propagator_call(self.lib.fsi_coarse, U0.shape[0], _ptr(U0), tp, _ptr(U1))
 
     def parareal_iterate(self, U, max_iter, tol, history=False):
         """U: device [n_slices + 1, n_dofs]; U[0] is the initial state. In place.

@@ -38,8 +38,15 @@ def test_nan_slice_reports_enan_and_spares_the_other_slice():
     with pytest.raises(fsi.FsiError) as e:
         ctx.fsi_theta_step(U, [0.0, 0.0], k, 0.5 + k, U_new=(out := torch.empty_like(U)))
     assert e.value.code == fsi.FSI_ENAN
-    alone, _ = ctx.fsi_theta_step(U[:1].contiguous(), [0.0], k, 0.5 + k)
+    assert e.value.slice_status == [fsi.FSI_OK, fsi.FSI_ENAN]
+    alone, st = ctx.fsi_theta_step(U[:1].contiguous(), [0.0], k, 0.5 + k)
+    assert st["slice_status"] == [fsi.FSI_OK]
     assert torch.equal(out[0], alone[0])
+    # the fine propagator on a context of one slice runs the two slices as two batches:
+    # the second batch's statuses land at its offset
+    with pytest.raises(fsi.FsiError) as e:
+        ctx_for(S=1).fsi_fine(U, [0.0, 0.0])
+    assert e.value.slice_status == [fsi.FSI_OK, fsi.FSI_ENAN]
 
 
 def test_newton_iteration_limit_reports_enewton():
@@ -49,6 +56,7 @@ def test_newton_iteration_limit_reports_enewton():
     with pytest.raises(fsi.FsiError) as e:
         ctx.fsi_theta_step(U, [0.0], W.k_coarse, 1.0)       # a large step needs more than one iteration
     assert e.value.code == fsi.FSI_ENEWTON
+    assert e.value.slice_status == [fsi.FSI_ENEWTON]
 
 
 def test_gmres_iteration_limit_reports_egmres():
