@@ -1,0 +1,323 @@
+// Element physics of the monolithic ALE fluid-structure step in 3D: hexahedral
+// Q2 cells (27 nodes, 3 x 3 x 3 Gauss points), 7 unknowns per node
+// (v_x, v_y, v_z, u_x, u_y, u_z, p).
+//
+// Sec. 2 of Margenberg & Richter: ALE fluid, Eq. (ALE) with the stress of
+// Eq. (ALE:stress); St. Venant-Kirchhoff solid, Eq. (stress); the shifted
+// Crank-Nicolson step of Sec. 2.3 with the forms of Eq. (semiforms). The 2D
+// kernels use the same readings; in 3D the adjugate A = J F^{-1} and the
+// cofactor C = A^T are quadratic in grad u, and the terms keep the 2D shape:
+//   J grad v F^{-1} v          = G A v
+//   J sigma_f F^{-T}           = (rho nu / J)(G A C + C G^T C) - p C
+//   J F^{-1} : grad v^T        = tr(G A)
+//   outflow correction          = -(rho nu / J) C G^T C n,   n = e_x
+// Fluxes are written per test slot: out[c * 4 + a], a = 0 the test function
+// value, a = 1, 2, 3 its x / y / z derivative; c = 0-2 momentum, 3-5
+// displacement rows (kinematic on solid cells, harmonic extension on fluid
+// cells), 6 the divergence row.
+//
+// Everything here is __host__ __device__: the CUDA kernels and host-side checks
+// compile the same code.
+#pragma once
+
+#include <cmath>
+
+#ifdef __CUDACC__
+#define FSI3_HD __host__ __device__
+#else
+#define FSI3_HD
+#endif
+
+namespace fsi3 {
+
+struct M3 {
+  double m[3][3];
+};
+
+FSI3_HD inline M3 eye3() {
+  M3 r{};
+  r.m[0][0] = r.m[1][1] = r.m[2][2] = 1.0;
+  return r;
+}
+FSI3_HD inline M3 add(const M3& x, const M3& y) {
+  M3 r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r.m[i][j] = x.m[i][j] + y.m[i][j];
+  return r;
+}
+FSI3_HD inline M3 scale(double s, const M3& x) {
+  M3 r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r.m[i][j] = s * x.m[i][j];
+  return r;
+}
+FSI3_HD inline M3 mul(const M3& x, const M3& y) {
+  M3 r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r.m[i][j] = x.m[i][0] * y.m[0][j] + x.m[i][1] * y.m[1][j] + x.m[i][2] * y.m[2][j];
+  return r;
+}
+FSI3_HD inline M3 tp(const M3& x) {
+  M3 r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r.m[i][j] = x.m[j][i];
+  return r;
+}
+FSI3_HD inline double det(const M3& x) {
+  const double (*a)[3] = x.m;
+  return a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+         a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+}
+// adj(x): x adj(x) = det(x) I
+FSI3_HD inline M3 adj(const M3& x) {
+  const double (*a)[3] = x.m;
+  M3 r;
+  r.m[0][0] = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+  r.m[0][1] = a[0][2] * a[2][1] - a[0][1] * a[2][2];
+  r.m[0][2] = a[0][1] * a[1][2] - a[0][2] * a[1][1];
+  r.m[1][0] = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+  r.m[1][1] = a[0][0] * a[2][2] - a[0][2] * a[2][0];
+  r.m[1][2] = a[0][2] * a[1][0] - a[0][0] * a[1][2];
+  r.m[2][0] = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+  r.m[2][1] = a[0][1] * a[2][0] - a[0][0] * a[2][1];
+  r.m[2][2] = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+  return r;
+}
+FSI3_HD inline double trace(const M3& x) { return x.m[0][0] + x.m[1][1] + x.m[2][2]; }
+FSI3_HD inline void mv(const M3& x, const double* v, double* out) {
+  for (int i = 0; i < 3; ++i) out[i] = x.m[i][0] * v[0] + x.m[i][1] * v[1] + x.m[i][2] * v[2];
+}
+
+struct Phys3 {
+  double rho_f, nu_f, rho_s, mu_s, lambda_s;
+};
+
+// New and old values and gradients at one quadrature point.
+struct Qp3 {
+  double v[3], u[3], p;
+  M3 G, Hu;      // grad v, grad u at t_n
+  double vo[3], uo[3];
+  M3 Go, Huo;    // at t_{n-1}
+};
+
+// Residual fluxes at a volume quadrature point, out[28] (see the header).
+FSI3_HD inline void qp_flux3(const Phys3& P, const Qp3& q, bool solid, double k, double theta, double* out) {
+  for (int i = 0; i < 28; ++i) out[i] = 0.0;
+  const double kt = k * theta, kto = k * (1.0 - theta);
+  const M3 I = eye3();
+  const M3 F = add(I, q.Hu), Fo = add(I, q.Huo);
+  if (!solid) {
+    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+    const double J = det(F), Jo = det(Fo);
+    const M3 A = adj(F), Ao = adj(Fo), C = tp(A), Co = tp(Ao);
+    // ALE mass term with midpoint means: Jh ((v - vo) - Gh Fh^{-1} (u - uo))
+    M3 Gh = scale(0.5, add(q.G, q.Go));
+    M3 Fh = add(I, scale(0.5, add(q.Hu, q.Huo)));
+    const M3 Bh = scale(1.0 / det(Fh), adj(Fh));
+    const double Jh = 0.5 * (J + Jo);
+    double w[3], t[3], M[3], Av[3], GAv[3], Aov[3], GoAov[3];
+    for (int c = 0; c < 3; ++c) w[c] = q.u[c] - q.uo[c];
+    mv(Bh, w, t);
+    mv(Gh, t, M);
+    mv(A, q.v, Av);
+    mv(q.G, Av, GAv);
+    mv(Ao, q.vo, Aov);
+    mv(q.Go, Aov, GoAov);
+    for (int c = 0; c < 3; ++c)
+      out[c * 4] = rf * Jh * ((q.v[c] - q.vo[c]) - M[c]) + kt * rf * GAv[c] + kto * rf * GoAov[c];
+    // stress: (rho nu / J)(G A C + C G^T C) - p C, old geometry with the new pressure
+    const M3 Q = add(mul(mul(q.G, A), C), mul(mul(C, tp(q.G)), C));
+    const M3 Qo = add(mul(mul(q.Go, Ao), Co), mul(mul(Co, tp(q.Go)), Co));
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j)
+        out[c * 4 + 1 + j] = kt * ((rn / J) * Q.m[c][j] - q.p * C.m[c][j]) +
+                             kto * ((rn / Jo) * Qo.m[c][j] - q.p * Co.m[c][j]);
+    // harmonic mesh extension
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j) out[(3 + c) * 4 + 1 + j] = kt * q.Hu.m[c][j] + kto * q.Huo.m[c][j];
+    out[6 * 4] = k * trace(mul(q.G, A));
+  } else {
+    auto piola = [&](const M3& Fx) {
+      M3 E = scale(0.5, add(mul(tp(Fx), Fx), scale(-1.0, I)));
+      const double trE = trace(E);
+      M3 S = add(scale(2.0 * P.mu_s, E), scale(P.lambda_s * trE, I));
+      return mul(Fx, S);
+    };
+    const M3 S = add(scale(kt, piola(F)), scale(kto, piola(Fo)));
+    for (int c = 0; c < 3; ++c) {
+      out[c * 4] = P.rho_s * (q.v[c] - q.vo[c]);
+      out[(3 + c) * 4] = (q.u[c] - q.uo[c]) - (kt * q.v[c] + kto * q.vo[c]);
+      for (int j = 0; j < 3; ++j) out[c * 4 + 1 + j] = S.m[c][j];
+    }
+  }
+}
+
+// Do-nothing correction on the outflow face x = x_max (value slot of the
+// momentum rows): -k theta (rho nu / J) C G^T C e_x - k (1 - theta) (...)_{n-1}.
+FSI3_HD inline void face_flux3(const Phys3& P, const M3& G, const M3& Hu, const M3& Go, const M3& Huo, double k,
+                               double theta, double* out) {
+  const double rn = P.rho_f * P.nu_f;
+  const M3 I = eye3();
+  const M3 F = add(I, Hu), Fo = add(I, Huo);
+  const M3 C = tp(adj(F)), Co = tp(adj(Fo));
+  const M3 T = mul(mul(C, tp(G)), C), To = mul(mul(Co, tp(Go)), Co);
+  const double J = det(F), Jo = det(Fo);
+  for (int c = 0; c < 3; ++c) out[c] = -k * theta * rn / J * T.m[c][0] - k * (1.0 - theta) * rn / Jo * To.m[c][0];
+}
+
+// Reference tables of the Q2 hexahedron on the unit cube. Node l = a + 3 b + 9 c
+// and quadrature point q likewise (x fastest); the outflow face s_x = 1 has the
+// 9 Gauss points of its (y, z) plane. lps[a][l][m] = integral over the unit cube
+// of d_a kappa(phi_l) d_a kappa(phi_m), kappa = I - (Q1 vertex interpolation).
+struct Tables3 {
+  double phi[27][27], dphi[3][27][27];     // [q][l], [dir][q][l]
+  double wq[27];
+  double phi_f[9][27], dphi_f[3][9][27];   // outflow face
+  double wf[9];
+  double lps[3][27][27];
+};
+
+inline double lag2(int a, double s) {
+  return a == 0 ? (1 - s) * (1 - 2 * s) : (a == 1 ? 4 * s * (1 - s) : s * (2 * s - 1));
+}
+inline double dlag2(int a, double s) { return a == 0 ? 4 * s - 3 : (a == 1 ? 4 - 8 * s : 4 * s - 1); }
+
+inline void build_tables3(Tables3& T) {
+  const double gp[3] = {0.5 - std::sqrt(0.15), 0.5, 0.5 + std::sqrt(0.15)};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  auto idx = [](int l, int* a) { a[0] = l % 3; a[1] = (l / 3) % 3; a[2] = l / 9; };
+  for (int q = 0; q < 27; ++q) {
+    int qi[3];
+    idx(q, qi);
+    T.wq[q] = gw[qi[0]] * gw[qi[1]] * gw[qi[2]];
+    for (int l = 0; l < 27; ++l) {
+      int li[3];
+      idx(l, li);
+      double v[3], dv[3];
+      for (int a = 0; a < 3; ++a) {
+        v[a] = lag2(li[a], gp[qi[a]]);
+        dv[a] = dlag2(li[a], gp[qi[a]]);
+      }
+      T.phi[q][l] = v[0] * v[1] * v[2];
+      T.dphi[0][q][l] = dv[0] * v[1] * v[2];
+      T.dphi[1][q][l] = v[0] * dv[1] * v[2];
+      T.dphi[2][q][l] = v[0] * v[1] * dv[2];
+    }
+  }
+  for (int f = 0; f < 9; ++f) {
+    const int fy = f % 3, fz = f / 3;
+    T.wf[f] = gw[fy] * gw[fz];
+    for (int l = 0; l < 27; ++l) {
+      int li[3];
+      idx(l, li);
+      const double vx = lag2(li[0], 1.0), dx = dlag2(li[0], 1.0);
+      const double vy = lag2(li[1], gp[fy]), dy = dlag2(li[1], gp[fy]);
+      const double vz = lag2(li[2], gp[fz]), dz = dlag2(li[2], gp[fz]);
+      T.phi_f[f][l] = vx * vy * vz;
+      T.dphi_f[0][f][l] = dx * vy * vz;
+      T.dphi_f[1][f][l] = vx * dy * vz;
+      T.dphi_f[2][f][l] = vx * vy * dz;
+    }
+  }
+  // kappa(phi_l) gradients: subtract the Q1 vertex function for vertex nodes
+  double gk[3][27][27];   // [dir][q][l]
+  for (int q = 0; q < 27; ++q) {
+    int qi[3];
+    idx(q, qi);
+    for (int l = 0; l < 27; ++l) {
+      int li[3];
+      idx(l, li);
+      const bool vertex = li[0] != 1 && li[1] != 1 && li[2] != 1;
+      for (int d = 0; d < 3; ++d) {
+        double g1 = 0.0;
+        if (vertex) {
+          g1 = 1.0;
+          for (int a = 0; a < 3; ++a) {
+            const double s = gp[qi[a]];
+            const int vtx = li[a] / 2;   // 0 or 1
+            const double val = vtx ? s : 1 - s, der = vtx ? 1.0 : -1.0;
+            g1 *= (a == d) ? der : val;
+          }
+        }
+        gk[d][q][l] = T.dphi[d][q][l] - g1;
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int l = 0; l < 27; ++l)
+      for (int m = 0; m < 27; ++m) {
+        double s = 0.0;
+        for (int q = 0; q < 27; ++q) s += T.wq[q] * gk[d][q][l] * gk[d][q][m];
+        T.lps[d][l][m] = s;
+      }
+}
+
+// Residual contributions of one cell, Re[l * 7 + c] (before the row selection
+// of the assembly): Ue, Uo the cell's nodal values [27][7] at t_n and t_{n-1},
+// h the cell's edge lengths, alpha its stabilisation weight.
+FSI3_HD inline void cell_residual3(const Phys3& P, const Tables3& T, const double* Ue, const double* Uo,
+                                   const double* h, bool solid, bool outflow, double k, double theta, double alpha,
+                                   double* Re) {
+  for (int i = 0; i < 27 * 7; ++i) Re[i] = 0.0;
+  const double vol = h[0] * h[1] * h[2];
+  for (int q = 0; q < 27; ++q) {
+    Qp3 x{};
+    for (int l = 0; l < 27; ++l) {
+      const double ph = T.phi[q][l];
+      const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
+      for (int c = 0; c < 3; ++c) {
+        x.v[c] += ph * Ue[l * 7 + c];
+        x.u[c] += ph * Ue[l * 7 + 3 + c];
+        x.vo[c] += ph * Uo[l * 7 + c];
+        x.uo[c] += ph * Uo[l * 7 + 3 + c];
+        for (int j = 0; j < 3; ++j) {
+          x.G.m[c][j] += g[j] * Ue[l * 7 + c];
+          x.Hu.m[c][j] += g[j] * Ue[l * 7 + 3 + c];
+          x.Go.m[c][j] += g[j] * Uo[l * 7 + c];
+          x.Huo.m[c][j] += g[j] * Uo[l * 7 + 3 + c];
+        }
+      }
+      x.p += ph * Ue[l * 7 + 6];
+    }
+    double f[28];
+    qp_flux3(P, x, solid, k, theta, f);
+    const double W = T.wq[q] * vol;
+    for (int l = 0; l < 27; ++l) {
+      const double ph = T.phi[q][l];
+      const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
+      for (int c = 0; c < 7; ++c)
+        Re[l * 7 + c] += W * (ph * f[c * 4] + g[0] * f[c * 4 + 1] + g[1] * f[c * 4 + 2] + g[2] * f[c * 4 + 3]);
+    }
+  }
+  if (!solid) {   // local projection stabilisation of the divergence rows
+    const double s[3] = {vol / (h[0] * h[0]), vol / (h[1] * h[1]), vol / (h[2] * h[2])};
+    for (int l = 0; l < 27; ++l) {
+      double acc = 0.0;
+      for (int m = 0; m < 27; ++m)
+        acc += (s[0] * T.lps[0][l][m] + s[1] * T.lps[1][l][m] + s[2] * T.lps[2][l][m]) * Ue[m * 7 + 6];
+      Re[l * 7 + 6] += k * alpha * acc;
+    }
+  }
+  if (outflow && !solid) {
+    for (int f = 0; f < 9; ++f) {
+      M3 G{}, Hu{}, Go{}, Huo{};
+      for (int l = 0; l < 27; ++l) {
+        const double g[3] = {T.dphi_f[0][f][l] / h[0], T.dphi_f[1][f][l] / h[1], T.dphi_f[2][f][l] / h[2]};
+        for (int c = 0; c < 3; ++c)
+          for (int j = 0; j < 3; ++j) {
+            G.m[c][j] += g[j] * Ue[l * 7 + c];
+            Hu.m[c][j] += g[j] * Ue[l * 7 + 3 + c];
+            Go.m[c][j] += g[j] * Uo[l * 7 + c];
+            Huo.m[c][j] += g[j] * Uo[l * 7 + 3 + c];
+          }
+      }
+      double fo[3];
+      face_flux3(P, G, Hu, Go, Huo, k, theta, fo);
+      const double W = T.wf[f] * h[1] * h[2];
+      for (int l = 0; l < 27; ++l)
+        for (int c = 0; c < 3; ++c) Re[l * 7 + c] += W * T.phi_f[f][l] * fo[c];
+    }
+  }
+}
+
+}  // namespace fsi3

@@ -1,0 +1,67 @@
+"""The 3D element physics of the CUDA library (csrc/fsi_element3d.cuh, compiled
+for the host with the system C++ compiler) against the 3D oracle, cell by cell:
+residual contributions of fluid, solid and outflow cells on random states."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import fsi_nd as on
+from paper_1907_01252_gb300 import workloads as wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def host_lib(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("el3") / "libel3.so")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-o", out,
+                    os.path.join(HERE, "native", "element3d_host.cpp")], check=True)
+    lib = C.CDLL(out)
+    P = C.POINTER(C.c_double)
+    lib.fsi3_cell_residual_host.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P]
+    return lib
+
+
+def ptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def state(mesh, seed):
+    rng = np.random.default_rng(seed)
+    U = np.empty((mesh.n_nodes, 7))
+    U[:, 0:3] = rng.uniform(-1, 1, (mesh.n_nodes, 3))
+    U[:, 3:6] = 2e-3 * rng.uniform(-1, 1, (mesh.n_nodes, 3))
+    U[:, 6] = 100 * rng.uniform(-1, 1, mesh.n_nodes)
+    return U
+
+
+@pytest.mark.parametrize("seed,k,theta", [(1, 0.02, 0.52), (2, 1 / 16, 1.0)])
+def test_cell_residual_matches_the_3d_oracle(host_lib, seed, k, theta):
+    mesh = on.make_mesh_nd([(0.0, 0.4, 0.45, 0.9), (0.0, 0.2, 0.41), (0.0, 0.055, 0.355, 0.41)],
+                           [[2, 1, 2], [1, 1], [1, 1, 1]], ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355)))
+    assert mesh.cell_solid.sum() == 1 and len(mesh.outflow_cells) > 0
+    mat = wl.Material()
+    tab = on.CellTablesND(mesh)
+    U, Uo = state(mesh, seed), state(mesh, seed + 10)
+    alpha = on.stabilisation_weights_nd(mesh, tab, mat, Uo)
+    ref = on.element_residual_nd(mesh, tab, mat, U[mesh.cell_nodes], Uo[mesh.cell_nodes], k, theta, alpha)
+    phys = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s])
+    outflow = np.zeros(mesh.n_cells, dtype=bool)
+    outflow[mesh.outflow_cells] = True
+    scale = np.abs(ref).max(axis=(0, 1))
+    for c in range(mesh.n_cells):
+        Ue = np.ascontiguousarray(U[mesh.cell_nodes[c]])
+        Uoe = np.ascontiguousarray(Uo[mesh.cell_nodes[c]])
+        h = np.ascontiguousarray(mesh.h[c])
+        Re = np.zeros((27, 7))
+        host_lib.fsi3_cell_residual_host(ptr(phys), ptr(Ue), ptr(Uoe), ptr(h), int(mesh.cell_solid[c]),
+                                         int(outflow[c]), k, theta, float(alpha[c]), ptr(Re))
+        err = np.abs(Re - ref[c]).max(axis=0)
+        assert np.all(err <= 1e-12 * scale), (c, err / scale)
