@@ -165,6 +165,93 @@ FSI3_HD inline void face_flux3(const Phys3& P, const M3& G, const M3& Hu, const 
   for (int c = 0; c < 3; ++c) out[c] = -k * theta * rn / J * T.m[c][0] - k * (1.0 - theta) * rn / Jo * To.m[c][0];
 }
 
+// Directional derivative of qp_flux3 in the direction (dv, dG, du, dH, dp) of
+// the t_n unknowns, out[28]. In 3D the adjugate is quadratic in grad u:
+// d adj(F)[dH] = (tr(A dH) A - A dH A) / J (from adj F = J F^{-1}).
+FSI3_HD inline void qp_flux3_lin(const Phys3& P, const Qp3& q, bool solid, double k, double theta, const double* dv,
+                                 const M3& dG, const double* du, const M3& dH, double dp, double* out) {
+  for (int i = 0; i < 28; ++i) out[i] = 0.0;
+  const double kt = k * theta, kto = k * (1.0 - theta);
+  const M3 I = eye3();
+  const M3 F = add(I, q.Hu);
+  if (!solid) {
+    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+    const M3 Fo = add(I, q.Huo);
+    const double J = det(F), Jo = det(Fo);
+    const M3 A = adj(F), C = tp(A), Co = tp(adj(Fo));
+    const double dJ = trace(mul(A, dH));
+    const M3 dA = scale(1.0 / J, add(scale(dJ, A), scale(-1.0, mul(mul(A, dH), A))));
+    const M3 dC = tp(dA);
+    // mass term: Jh ((v - vo) - Gh Bh w), Bh = Fh^{-1}, dBh = -Bh (dH / 2) Bh
+    const M3 Gh = scale(0.5, add(q.G, q.Go));
+    const M3 Fh = add(I, scale(0.5, add(q.Hu, q.Huo)));
+    const M3 Bh = scale(1.0 / det(Fh), adj(Fh));
+    const double Jh = 0.5 * (J + Jo), dJh = 0.5 * dJ;
+    const M3 dBh = scale(-0.5, mul(mul(Bh, dH), Bh));
+    double w[3], Bw[3], M[3], t1[3], t2[3], t3[3], t4[3], dM[3];
+    for (int c = 0; c < 3; ++c) w[c] = q.u[c] - q.uo[c];
+    mv(Bh, w, Bw);
+    mv(Gh, Bw, M);
+    mv(dG, Bw, t1);                 // dGh Bh w = (dG / 2) Bh w
+    mv(dBh, w, t2);
+    mv(Gh, t2, t3);                 // Gh dBh w
+    mv(Bh, du, t2);
+    mv(Gh, t2, t4);                 // Gh Bh dw
+    for (int c = 0; c < 3; ++c) dM[c] = 0.5 * t1[c] + t3[c] + t4[c];
+    // convection G A v
+    double Av[3], dGAv[3], dAv[3], GdAv[3], Adv[3], GAdv[3];
+    mv(A, q.v, Av);
+    mv(dG, Av, dGAv);
+    mv(dA, q.v, dAv);
+    mv(q.G, dAv, GdAv);
+    mv(A, dv, Adv);
+    mv(q.G, Adv, GAdv);
+    for (int c = 0; c < 3; ++c)
+      out[c * 4] = rf * (dJh * ((q.v[c] - q.vo[c]) - M[c]) + Jh * (dv[c] - dM[c])) +
+                   kt * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
+    // stress (rho nu / J) Q - p C with Q = G A C + C G^T C; the old term depends on p only
+    const M3 Gt = tp(q.G), dGt = tp(dG);
+    const M3 Q = add(mul(mul(q.G, A), C), mul(mul(C, Gt), C));
+    M3 dQ = add(add(mul(mul(dG, A), C), mul(mul(q.G, dA), C)), mul(mul(q.G, A), dC));
+    dQ = add(dQ, add(add(mul(mul(dC, Gt), C), mul(mul(C, dGt), C)), mul(mul(C, Gt), dC)));
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j)
+        out[c * 4 + 1 + j] = kt * ((rn / J) * dQ.m[c][j] - (rn * dJ / (J * J)) * Q.m[c][j] - dp * C.m[c][j] -
+                                   q.p * dC.m[c][j]) -
+                             kto * dp * Co.m[c][j];
+    for (int c = 0; c < 3; ++c)
+      for (int j = 0; j < 3; ++j) out[(3 + c) * 4 + 1 + j] = kt * dH.m[c][j];
+    out[6 * 4] = k * (trace(mul(dG, A)) + trace(mul(q.G, dA)));
+  } else {
+    const double mu = P.mu_s, lam = P.lambda_s;
+    const M3 E = scale(0.5, add(mul(tp(F), F), scale(-1.0, I)));
+    const M3 Sig = add(scale(2.0 * mu, E), scale(lam * trace(E), I));
+    const M3 dE = scale(0.5, add(mul(tp(dH), F), mul(tp(F), dH)));
+    const M3 dSig = add(scale(2.0 * mu, dE), scale(lam * trace(dE), I));
+    const M3 S = scale(kt, add(mul(dH, Sig), mul(F, dSig)));
+    for (int c = 0; c < 3; ++c) {
+      out[c * 4] = P.rho_s * dv[c];
+      out[(3 + c) * 4] = du[c] - kt * dv[c];
+      for (int j = 0; j < 3; ++j) out[c * 4 + 1 + j] = S.m[c][j];
+    }
+  }
+}
+
+// Directional derivative of face_flux3 in the t_n gradients (dG, dH), out[3].
+FSI3_HD inline void face_flux3_lin(const Phys3& P, const M3& G, const M3& Hu, const M3& dG, const M3& dH, double k,
+                                   double theta, double* out) {
+  const double rn = P.rho_f * P.nu_f;
+  const M3 F = add(eye3(), Hu);
+  const double J = det(F);
+  const M3 A = adj(F), C = tp(A);
+  const double dJ = trace(mul(A, dH));
+  const M3 dC = tp(scale(1.0 / J, add(scale(dJ, A), scale(-1.0, mul(mul(A, dH), A)))));
+  const M3 Gt = tp(G);
+  const M3 T = mul(mul(C, Gt), C);
+  const M3 dT = add(add(mul(mul(dC, Gt), C), mul(mul(C, tp(dG)), C)), mul(mul(C, Gt), dC));
+  for (int c = 0; c < 3; ++c) out[c] = -k * theta * rn * (dT.m[c][0] / J - dJ / (J * J) * T.m[c][0]);
+}
+
 // Reference tables of the Q2 hexahedron on the unit cube. Node l = a + 3 b + 9 c
 // and quadrature point q likewise (x fastest); the outflow face s_x = 1 has the
 // 9 Gauss points of its (y, z) plane. lps[a][l][m] = integral over the unit cube
@@ -316,6 +403,109 @@ FSI3_HD inline void cell_residual3(const Phys3& P, const Tables3& T, const doubl
       const double W = T.wf[f] * h[1] * h[2];
       for (int l = 0; l < 27; ++l)
         for (int c = 0; c < 3; ++c) Re[l * 7 + c] += W * T.phi_f[f][l] * fo[c];
+    }
+  }
+}
+
+// Element matrix of one cell, Ke[(l * 7 + ci) * 189 + m * 7 + cj] = dRe[l, ci] / dUe[m, cj]
+// (before the row selection of the assembly), by the two-stage contraction
+// K += sum_q W B_l^T D_q B_m with the 28 x 28 tangent D_q of qp_flux3_lin.
+FSI3_HD inline void cell_jacobian3(const Phys3& P, const Tables3& T, const double* Ue, const double* Uo,
+                                   const double* h, bool solid, bool outflow, double k, double theta, double alpha,
+                                   double* Ke) {
+  for (int i = 0; i < 189 * 189; ++i) Ke[i] = 0.0;
+  const double vol = h[0] * h[1] * h[2];
+  for (int q = 0; q < 27; ++q) {
+    Qp3 x{};
+    for (int l = 0; l < 27; ++l) {
+      const double ph = T.phi[q][l];
+      const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
+      for (int c = 0; c < 3; ++c) {
+        x.v[c] += ph * Ue[l * 7 + c];
+        x.u[c] += ph * Ue[l * 7 + 3 + c];
+        x.vo[c] += ph * Uo[l * 7 + c];
+        x.uo[c] += ph * Uo[l * 7 + 3 + c];
+        for (int jj = 0; jj < 3; ++jj) {
+          x.G.m[c][jj] += g[jj] * Ue[l * 7 + c];
+          x.Hu.m[c][jj] += g[jj] * Ue[l * 7 + 3 + c];
+          x.Go.m[c][jj] += g[jj] * Uo[l * 7 + c];
+          x.Huo.m[c][jj] += g[jj] * Uo[l * 7 + 3 + c];
+        }
+      }
+      x.p += ph * Ue[l * 7 + 6];
+    }
+    double D[28][28];   // [test slot ci * 4 + a][trial direction cj * 4 + b]
+    for (int dir = 0; dir < 28; ++dir) {
+      const int cj = dir / 4, b = dir % 4;
+      double dv[3] = {0, 0, 0}, du[3] = {0, 0, 0}, dp = 0.0;
+      M3 dG{}, dH{};
+      if (cj < 3) {
+        if (b == 0) dv[cj] = 1.0;
+        else dG.m[cj][b - 1] = 1.0;
+      } else if (cj < 6) {
+        if (b == 0) du[cj - 3] = 1.0;
+        else dH.m[cj - 3][b - 1] = 1.0;
+      } else if (b == 0) {
+        dp = 1.0;
+      }
+      double o[28];
+      qp_flux3_lin(P, x, solid, k, theta, dv, dG, du, dH, dp, o);
+      for (int r = 0; r < 28; ++r) D[r][dir] = o[r];
+    }
+    const double W = T.wq[q] * vol;
+    double B[4][27];
+    for (int l = 0; l < 27; ++l) {
+      B[0][l] = T.phi[q][l];
+      for (int a = 0; a < 3; ++a) B[1 + a][l] = T.dphi[a][q][l] / h[a];
+    }
+    for (int ci = 0; ci < 7; ++ci)
+      for (int cj = 0; cj < 7; ++cj) {
+        double E[4][27];   // E[a][m] = sum_b D[ci a][cj b] B_b(m)
+        for (int a = 0; a < 4; ++a)
+          for (int m = 0; m < 27; ++m) {
+            double e = 0.0;
+            for (int b = 0; b < 4; ++b) e += D[ci * 4 + a][cj * 4 + b] * B[b][m];
+            E[a][m] = W * e;
+          }
+        for (int l = 0; l < 27; ++l)
+          for (int m = 0; m < 27; ++m) {
+            double acc = 0.0;
+            for (int a = 0; a < 4; ++a) acc += B[a][l] * E[a][m];
+            Ke[(l * 7 + ci) * 189 + m * 7 + cj] += acc;
+          }
+      }
+  }
+  if (!solid) {
+    const double s3[3] = {vol / (h[0] * h[0]), vol / (h[1] * h[1]), vol / (h[2] * h[2])};
+    for (int l = 0; l < 27; ++l)
+      for (int m = 0; m < 27; ++m)
+        Ke[(l * 7 + 6) * 189 + m * 7 + 6] +=
+            k * alpha * (s3[0] * T.lps[0][l][m] + s3[1] * T.lps[1][l][m] + s3[2] * T.lps[2][l][m]);
+  }
+  if (outflow && !solid) {
+    for (int f = 0; f < 9; ++f) {
+      M3 G{}, Hu{};
+      double gf[3][27];
+      for (int l = 0; l < 27; ++l) {
+        for (int a = 0; a < 3; ++a) gf[a][l] = T.dphi_f[a][f][l] / h[a];
+        for (int c = 0; c < 3; ++c)
+          for (int jj = 0; jj < 3; ++jj) {
+            G.m[c][jj] += gf[jj][l] * Ue[l * 7 + c];
+            Hu.m[c][jj] += gf[jj][l] * Ue[l * 7 + 3 + c];
+          }
+      }
+      const double W = T.wf[f] * h[1] * h[2];
+      for (int cj = 0; cj < 6; ++cj)
+        for (int b = 0; b < 3; ++b) {
+          M3 dG{}, dH{};
+          if (cj < 3) dG.m[cj][b] = 1.0;
+          else dH.m[cj - 3][b] = 1.0;
+          double o[3];
+          face_flux3_lin(P, G, Hu, dG, dH, k, theta, o);
+          for (int l = 0; l < 27; ++l)
+            for (int m = 0; m < 27; ++m)
+              for (int c = 0; c < 3; ++c) Ke[(l * 7 + c) * 189 + m * 7 + cj] += W * T.phi_f[f][l] * o[c] * gf[b][m];
+        }
     }
   }
 }

@@ -65,3 +65,35 @@ def test_cell_residual_matches_the_3d_oracle(host_lib, seed, k, theta):
                                          int(outflow[c]), k, theta, float(alpha[c]), ptr(Re))
         err = np.abs(Re - ref[c]).max(axis=0)
         assert np.all(err <= 1e-12 * scale), (c, err / scale)
+
+
+@pytest.mark.parametrize("seed,k,theta", [(3, 0.02, 0.52), (4, 1 / 16, 1.0)])
+def test_cell_jacobian_matches_the_3d_oracle_complex_step(host_lib, seed, k, theta):
+    """Hand-derived 3D tangent and contraction against the oracle's complex-step element matrices."""
+    P = C.POINTER(C.c_double)
+    host_lib.fsi3_cell_jacobian_host.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P]
+    mesh = on.make_mesh_nd([(0.0, 0.4, 0.45, 0.9), (0.0, 0.2, 0.41), (0.0, 0.055, 0.355, 0.41)],
+                           [[2, 1, 2], [1, 1], [1, 1, 1]], ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355)))
+    mat = wl.Material()
+    U, Uo = state(mesh, seed), state(mesh, seed + 10)
+    prob = on.StepProblemND(mesh, mat, Uo, 0.2, k, theta)
+    ref = prob.element_jacobians(U)                                 # [cell, 27, 7, 27, 7]
+    phys = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s])
+    outflow = np.zeros(mesh.n_cells, dtype=bool)
+    outflow[mesh.outflow_cells] = True
+    cells = [int(np.argmax(mesh.cell_solid)), int(mesh.outflow_cells[0]), 0]
+    for c in cells:
+        Ue = np.ascontiguousarray(U[mesh.cell_nodes[c]])
+        Uoe = np.ascontiguousarray(Uo[mesh.cell_nodes[c]])
+        h = np.ascontiguousarray(mesh.h[c])
+        Ke = np.zeros((189, 189))
+        host_lib.fsi3_cell_jacobian_host(ptr(phys), ptr(Ue), ptr(Uoe), ptr(h), int(mesh.cell_solid[c]),
+                                         int(outflow[c]), k, theta, float(prob.alpha[c]), ptr(Ke))
+        R = ref[c].reshape(189, 189)
+        # per field block: errors relative to the block's largest entry
+        for ci in range(7):
+            for cj in range(7):
+                blk_ref = R[ci::7, cj::7]
+                blk = Ke[ci::7, cj::7]
+                sc = max(np.abs(blk_ref).max(), 1e-300)
+                assert np.abs(blk - blk_ref).max() <= 1e-10 * max(sc, 1e-12 * np.abs(R).max()), (c, ci, cj)
