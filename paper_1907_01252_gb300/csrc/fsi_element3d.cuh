@@ -510,4 +510,20 @@ FSI3_HD inline void cell_jacobian3(const Phys3& P, const Tables3& T, const doubl
   }
 }
 
+// Stabilisation weight of a cell from its old state (the same reading as in
+// 2D): alpha = alpha0 h^2 / (rho_f nu_f + rho_f |vbar| h), vbar the Gauss mean
+// of v_{n-1} over the cell, h the cell diameter.
+FSI3_HD inline double stab_weight3(const Tables3& T, const double* Uo, const double* h, double alpha0, double rho_f,
+                                   double nu_f) {
+  double vb[3] = {0, 0, 0}, ws = 0.0;
+  for (int q = 0; q < 27; ++q) {
+    ws += T.wq[q];
+    for (int l = 0; l < 27; ++l)
+      for (int c = 0; c < 3; ++c) vb[c] += T.wq[q] * T.phi[q][l] * Uo[l * 7 + c];
+  }
+  const double sp = sqrt(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]) / ws;
+  const double hd = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+  return alpha0 * hd * hd / (rho_f * nu_f + rho_f * sp * hd);
+}
+
 }  // namespace fsi3

@@ -27,3 +27,67 @@ extern "C" int fsi3_cell_jacobian_host(const double* phys, const double* Ue, con
   fsi3::cell_jacobian3(P, T, Ue, Uo, h, solid != 0, outflow != 0, k, theta, alpha, Ke);
   return 0;
 }
+
+#include "../../paper_1907_01252_gb300/csrc/fsi_mesh3d.h"
+
+namespace {
+fsi3::HostMesh3 make_mesh(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys, int nyseg,
+                          const double* zb, const int* nzs, int nzseg, const double* box) {
+  fsi3::HostMesh3 m;
+  fsi3::build_mesh3(m, fsi3::axis_vertices3(xb, nxs, nxseg), fsi3::axis_vertices3(yb, nys, nyseg),
+                    fsi3::axis_vertices3(zb, nzs, nzseg), box);
+  return m;
+}
+fsi3::Mesh3View view(const fsi3::HostMesh3& m) {
+  return fsi3::Mesh3View{m.nnx, m.nny, m.nnz, m.n_nodes, m.n_cells, m.yn.data(), m.zn.data(),
+                         m.cell_flags.data(), m.node_flags.data(), m.node_cells.data(), m.y0, m.y1, m.z0, m.z1};
+}
+}  // namespace
+
+// Mesh tables: sizes_out = {n_nodes, n_cells, nnzb}; the arrays are filled when non-null.
+extern "C" int fsi3_mesh_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys, int nyseg,
+                              const double* zb, const int* nzs, int nzseg, const double* box, int* sizes_out,
+                              int* cell_nodes_out, unsigned char* node_flags_out, unsigned char* cell_flags_out) {
+  const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
+  sizes_out[0] = m.n_nodes;
+  sizes_out[1] = m.n_cells;
+  sizes_out[2] = m.nnzb;
+  if (cell_nodes_out) std::copy(m.cell_nodes.begin(), m.cell_nodes.end(), cell_nodes_out);
+  if (node_flags_out) std::copy(m.node_flags.begin(), m.node_flags.end(), node_flags_out);
+  if (cell_flags_out) std::copy(m.cell_flags.begin(), m.cell_flags.end(), cell_flags_out);
+  return 0;
+}
+
+// The assembled step residual R[n_nodes][7] of one slice, computed the way the
+// kernels will: per cell (stabilisation weight, cell residual), then per row
+// (fixed-order gather or identity row). mat = {rho_f, nu_f, rho_s, mu_s,
+// lambda_s, vbar, ramp_t, alpha0}.
+extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
+                                  int nyseg, const double* zb, const int* nzs, int nzseg, const double* box,
+                                  const double* mat, const double* U, const double* Uo, double t_new, double k,
+                                  double theta, double* R) {
+  static fsi3::Tables3 T;
+  static bool ready = false;
+  if (!ready) {
+    fsi3::build_tables3(T);
+    ready = true;
+  }
+  const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
+  const fsi3::Phys3 P{mat[0], mat[1], mat[2], mat[3], mat[4]};
+  std::vector<double> Re((size_t)m.n_cells * 27 * 7), Ue(189), Uoe(189);
+  for (int c = 0; c < m.n_cells; ++c) {
+    for (int l = 0; l < 27; ++l)
+      for (int f = 0; f < 7; ++f) {
+        Ue[l * 7 + f] = U[(size_t)m.cell_nodes[(size_t)c * 27 + l] * 7 + f];
+        Uoe[l * 7 + f] = Uo[(size_t)m.cell_nodes[(size_t)c * 27 + l] * 7 + f];
+      }
+    const double* h = &m.cell_h[(size_t)c * 3];
+    const bool solid = m.cell_flags[c] & fsi3::C3_SOLID, outflow = m.cell_flags[c] & fsi3::C3_OUTFLOW;
+    const double alpha = fsi3::stab_weight3(T, Uoe.data(), h, mat[7], mat[0], mat[1]);
+    fsi3::cell_residual3(P, T, Ue.data(), Uoe.data(), h, solid, outflow, k, theta, alpha, &Re[(size_t)c * 189]);
+  }
+  const fsi3::Mesh3View v = view(m);
+  for (int n = 0; n < m.n_nodes; ++n)
+    for (int c = 0; c < 7; ++c) R[(size_t)n * 7 + c] = fsi3::gather3(v, Re.data(), U, n, c, t_new, mat[5], mat[6]);
+  return 0;
+}

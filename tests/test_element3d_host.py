@@ -97,3 +97,61 @@ def test_cell_jacobian_matches_the_3d_oracle_complex_step(host_lib, seed, k, the
                 blk = Ke[ci::7, cj::7]
                 sc = max(np.abs(blk_ref).max(), 1e-300)
                 assert np.abs(blk - blk_ref).max() <= 1e-10 * max(sc, 1e-12 * np.abs(R).max()), (c, ci, cj)
+
+
+BREAKS3 = ((0.0, 0.4, 0.45, 0.9), (0.0, 0.2, 0.41), (0.0, 0.055, 0.355, 0.41))
+COUNTS3 = ((2, 1, 2), (1, 1), (1, 1, 1))
+BOX3 = ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355))
+
+
+def mesh_args(breaks=BREAKS3, counts=COUNTS3, box=BOX3):
+    keep = []
+    args = []
+    for br, cn in zip(breaks, counts):
+        b = np.ascontiguousarray(br, dtype=float)
+        c = np.ascontiguousarray(cn, dtype=np.int32)
+        keep += [b, c]
+        args += [ptr(b), c.ctypes.data_as(C.POINTER(C.c_int)), len(cn)]
+    bx = np.ascontiguousarray(np.ravel(box), dtype=float) if box is not None else None
+    keep.append(bx)
+    args.append(ptr(bx) if bx is not None else None)
+    return args, keep
+
+
+def test_3d_mesh_tables_match_the_oracle_mesh(host_lib):
+    oracle_mesh = on.make_mesh_nd(BREAKS3, COUNTS3, BOX3)
+    args, keep = mesh_args()
+    sizes = np.zeros(3, dtype=np.int32)
+    cn = np.zeros((oracle_mesh.n_cells, 27), dtype=np.int32)
+    nf = np.zeros(oracle_mesh.n_nodes, dtype=np.uint8)
+    cf = np.zeros(oracle_mesh.n_cells, dtype=np.uint8)
+    ip = lambda a: a.ctypes.data_as(C.c_void_p)
+    host_lib.fsi3_mesh_host(*args, ip(sizes), ip(cn), ip(nf), ip(cf))
+    nx, ny, nz = (sum(c) for c in COUNTS3)
+    assert sizes[0] == oracle_mesh.n_nodes and sizes[1] == oracle_mesh.n_cells
+    assert sizes[2] == (8 * nx + 1) * (8 * ny + 1) * (8 * nz + 1)          # Q2 pattern count per axis 8n + 1
+    assert np.array_equal(cn, oracle_mesh.cell_nodes)
+    assert np.array_equal((cf & 1).astype(bool), oracle_mesh.cell_solid)
+    assert np.array_equal((nf & 1).astype(bool), oracle_mesh.dir_v)
+    assert np.array_equal((nf & 2).astype(bool), oracle_mesh.dir_u)
+    assert np.array_equal((nf & 4).astype(bool), oracle_mesh.p_identity)
+    assert np.array_equal((nf & 8).astype(bool), oracle_mesh.node_in_solid)
+    assert np.array_equal((nf & 16).astype(bool), oracle_mesh.on_inflow)
+
+
+@pytest.mark.parametrize("seed,t_new,k,theta", [(5, 0.13, 0.02, 0.52), (6, 0.3, 1 / 16, 1.0)])
+def test_assembled_3d_residual_matches_the_oracle(host_lib, seed, t_new, k, theta):
+    """Per-cell residuals (with the stabilisation weights) and the fixed-order row gather,
+    run in host loops, against the oracle's assembled residual (identity rows included)."""
+    P = C.POINTER(C.c_double)
+    mesh = on.make_mesh_nd(BREAKS3, COUNTS3, BOX3)
+    mat = wl.Material(vbar=1.2)
+    U, Uo = state(mesh, seed), state(mesh, seed + 20)
+    ref = on.StepProblemND(mesh, mat, Uo, t_new, k, theta).residual(U)
+    args, keep = mesh_args()
+    m = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s, mat.vbar, mat.ramp_t, mat.alpha0])
+    R = np.zeros((mesh.n_nodes, 7))
+    host_lib.fsi3_residual_host(*args, ptr(m), ptr(np.ascontiguousarray(U)), ptr(np.ascontiguousarray(Uo)),
+                                C.c_double(t_new), C.c_double(k), C.c_double(theta), ptr(R))
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(np.abs(R - ref).max(axis=0) <= 1e-12 * scale), np.abs(R - ref).max(axis=0) / scale
