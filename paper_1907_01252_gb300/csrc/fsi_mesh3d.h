@@ -44,6 +44,8 @@ struct HostMesh3 {
   std::vector<uint8_t> cell_flags, node_flags;
   std::vector<int> node_cells;        // [node][8]: cell * 27 + local, ascending cells, -1 padded
   std::vector<int> rowptr, colidx;    // node block pattern (nodes sharing a cell)
+  std::vector<int> blk_row;           // [nnzb] row node of each block
+  std::vector<int> blk_src;           // [nnzb][8]: cell * 729 + li * 27 + lj, ascending cells, -1 padded
   double y0 = 0, y1 = 0, z0 = 0, z1 = 0;
 };
 
@@ -137,6 +139,19 @@ inline void build_mesh3(HostMesh3& m, const std::vector<double>& xv, const std::
     m.rowptr[n + 1] = (int)m.colidx.size();
   }
   m.nnzb = (int)m.colidx.size();
+  m.blk_row.assign(m.nnzb, 0);
+  for (int n = 0; n < m.n_nodes; ++n)
+    for (int b = m.rowptr[n]; b < m.rowptr[n + 1]; ++b) m.blk_row[b] = n;
+  m.blk_src.assign((size_t)m.nnzb * 8, -1);
+  std::vector<int> bcnt(m.nnzb, 0);
+  for (int c = 0; c < m.n_cells; ++c)
+    for (int li = 0; li < 27; ++li)
+      for (int lj = 0; lj < 27; ++lj) {
+        const int ni = m.cell_nodes[(size_t)c * 27 + li], nj = m.cell_nodes[(size_t)c * 27 + lj];
+        const int b = (int)(std::lower_bound(m.colidx.begin() + m.rowptr[ni], m.colidx.begin() + m.rowptr[ni + 1], nj) -
+                            m.colidx.begin());
+        m.blk_src[(size_t)b * 8 + bcnt[b]++] = c * 729 + li * 27 + lj;
+      }
 }
 
 // Read-only view of the tables, as the kernels see them (device or host pointers).
@@ -146,6 +161,7 @@ struct Mesh3View {
   const uint8_t *cell_flags, *node_flags;
   const int* node_cells;
   double y0, y1, z0, z1;
+  const int *blk_row, *colidx, *blk_src;
 };
 
 FSI3M_HD inline double inflow_ramp3(double t, double ramp_t) {
@@ -187,6 +203,23 @@ FSI3M_HD inline double gather3(const Mesh3View& m, const double* Re, const doubl
     if (code < 0) break;
     const int cell = code / 27, l = code % 27;
     if (row_takes3(m.cell_flags[cell], nf, c)) acc += Re[((size_t)cell * 27 + l) * 7 + c];
+  }
+  return acc;
+}
+
+// Entry (r, c) of Jacobian block b of one slice: the element matrices
+// Ke[cell][189][189] of the cells sharing the block's two nodes, in ascending
+// cell order, under the row rules; identity rows hold the unit diagonal.
+FSI3M_HD inline double assemble3(const Mesh3View& m, const double* Ke, int b, int r, int c) {
+  const int i = m.blk_row[b], j = m.colidx[b];
+  const uint8_t nf = m.node_flags[i];
+  if (identity_row3(nf, r)) return (i == j && r == c) ? 1.0 : 0.0;
+  double acc = 0.0;
+  for (int e = 0; e < 8; ++e) {
+    const int code = m.blk_src[(size_t)b * 8 + e];
+    if (code < 0) break;
+    const int cell = code / 729, li = (code / 27) % 27, lj = code % 27;
+    if (row_takes3(m.cell_flags[cell], nf, r)) acc += Ke[(size_t)cell * 189 * 189 + (size_t)(li * 7 + r) * 189 + lj * 7 + c];
   }
   return acc;
 }

@@ -40,7 +40,8 @@ fsi3::HostMesh3 make_mesh(const double* xb, const int* nxs, int nxseg, const dou
 }
 fsi3::Mesh3View view(const fsi3::HostMesh3& m) {
   return fsi3::Mesh3View{m.nnx, m.nny, m.nnz, m.n_nodes, m.n_cells, m.yn.data(), m.zn.data(),
-                         m.cell_flags.data(), m.node_flags.data(), m.node_cells.data(), m.y0, m.y1, m.z0, m.z1};
+                         m.cell_flags.data(), m.node_flags.data(), m.node_cells.data(), m.y0, m.y1, m.z0, m.z1,
+                         m.blk_row.data(), m.colidx.data(), m.blk_src.data()};
 }
 }  // namespace
 
@@ -89,5 +90,42 @@ extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, c
   const fsi3::Mesh3View v = view(m);
   for (int n = 0; n < m.n_nodes; ++n)
     for (int c = 0; c < 7; ++c) R[(size_t)n * 7 + c] = fsi3::gather3(v, Re.data(), U, n, c, t_new, mat[5], mat[6]);
+  return 0;
+}
+
+// The assembled Jacobian of one slice in 7 x 7 blocks (row-major), computed the
+// way the kernels will: element matrices per cell, then every block entry by
+// the fixed-order gather. rowptr_out [n_nodes + 1], colidx_out [nnzb],
+// vals_out [nnzb][49]; the sizes come from fsi3_mesh_host.
+extern "C" int fsi3_jacobian_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
+                                  int nyseg, const double* zb, const int* nzs, int nzseg, const double* box,
+                                  const double* mat, const double* U, const double* Uo, double k, double theta,
+                                  int* rowptr_out, int* colidx_out, double* vals_out) {
+  static fsi3::Tables3 T;
+  static bool ready = false;
+  if (!ready) {
+    fsi3::build_tables3(T);
+    ready = true;
+  }
+  const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
+  const fsi3::Phys3 P{mat[0], mat[1], mat[2], mat[3], mat[4]};
+  std::vector<double> Ke((size_t)m.n_cells * 189 * 189), Ue(189), Uoe(189);
+  for (int c = 0; c < m.n_cells; ++c) {
+    for (int l = 0; l < 27; ++l)
+      for (int f = 0; f < 7; ++f) {
+        Ue[l * 7 + f] = U[(size_t)m.cell_nodes[(size_t)c * 27 + l] * 7 + f];
+        Uoe[l * 7 + f] = Uo[(size_t)m.cell_nodes[(size_t)c * 27 + l] * 7 + f];
+      }
+    const double* h = &m.cell_h[(size_t)c * 3];
+    const bool solid = m.cell_flags[c] & fsi3::C3_SOLID, outflow = m.cell_flags[c] & fsi3::C3_OUTFLOW;
+    const double alpha = fsi3::stab_weight3(T, Uoe.data(), h, mat[7], mat[0], mat[1]);
+    fsi3::cell_jacobian3(P, T, Ue.data(), Uoe.data(), h, solid, outflow, k, theta, alpha, &Ke[(size_t)c * 189 * 189]);
+  }
+  const fsi3::Mesh3View v = view(m);
+  std::copy(m.rowptr.begin(), m.rowptr.end(), rowptr_out);
+  std::copy(m.colidx.begin(), m.colidx.end(), colidx_out);
+  for (int b = 0; b < m.nnzb; ++b)
+    for (int r = 0; r < 7; ++r)
+      for (int c = 0; c < 7; ++c) vals_out[(size_t)b * 49 + r * 7 + c] = fsi3::assemble3(v, Ke.data(), b, r, c);
   return 0;
 }
