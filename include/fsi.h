@@ -281,6 +281,28 @@ int fsi_dense_invert(int S, int n, const double* A, double* inv, int method, voi
  * Outputs: host ints. Errors: FSI_EINVAL (bad mesh, null output). */
 int fsi_mesh_size(const fsi_mesh* mesh, int* n_nodes, int* n_dofs, int* nnzb);
 
+/* 3D interface-fitted hexahedral mesh (the 3D channel of the uneven and 3D
+ * workloads): break points and cells per segment on the three axes, and an
+ * optional solid box. Host pointers, read during the call only. */
+typedef struct fsi_mesh3d {
+  int n_xseg;
+  const double* x_breaks; /* [n_xseg + 1], increasing */
+  const int* nx_seg;      /* [n_xseg], each >= 1 */
+  int n_yseg;
+  const double* y_breaks;
+  const int* ny_seg;
+  int n_zseg;
+  const double* z_breaks;
+  const int* nz_seg;
+  int has_solid;
+  double solid_box[6];    /* x0, x1, y0, y1, z0, z1 */
+} fsi_mesh3d;
+
+/* Sizes of a 3D mesh on the host only (no GPU): nodes of the Q2 hexahedra
+ * (2nx+1)(2ny+1)(2nz+1), dofs (7 per node: v, u, p) and 7 x 7 blocks of the
+ * Jacobian's node pattern. Errors: FSI_EINVAL (bad mesh, null output). */
+int fsi3d_mesh_size(const fsi_mesh3d* mesh, int* n_nodes, int* n_dofs, int* nnzb);
+
 /* ---- Batches of independent problems (beyond the paper, which solves one
  * problem at a time) ----------------------------------------------------
  * Many independent FSI problems of uneven meshes, materials and slice counts,

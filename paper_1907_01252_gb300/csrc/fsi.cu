@@ -31,6 +31,7 @@
 
 #include "../../include/fsi.h"
 #include "fsi_internal.h"
+#include "fsi_mesh3d.h"
 #include "fsi_kernels.cuh"
 
 namespace {
@@ -1682,6 +1683,25 @@ int fsi_dense_invert(int S, int n, const double* A, double* inv, int method, voi
   for (int s = 0; s < S; ++s)
     if (st_h[s] != 0) return release(fail(FSI_EJAC, "singular matrix in the dense inverse"));
   return release(FSI_OK);
+}
+
+int fsi3d_mesh_size(const fsi_mesh3d* mesh, int* n_nodes, int* n_dofs, int* nnzb) {
+  if (!mesh || !n_nodes || !n_dofs || !nnzb) return fail(FSI_EINVAL, "null argument");
+  const int ns[3] = {mesh->n_xseg, mesh->n_yseg, mesh->n_zseg};
+  const double* br[3] = {mesh->x_breaks, mesh->y_breaks, mesh->z_breaks};
+  const int* seg[3] = {mesh->nx_seg, mesh->ny_seg, mesh->nz_seg};
+  for (int a = 0; a < 3; ++a) {
+    if (ns[a] < 1 || !br[a] || !seg[a]) return fail(FSI_EINVAL, "empty 3D mesh axis");
+    for (int i = 0; i < ns[a]; ++i)
+      if (seg[a][i] < 1 || !(br[a][i + 1] > br[a][i])) return fail(FSI_EINVAL, "bad 3D mesh segments");
+  }
+  fsi3::HostMesh3 m;
+  fsi3::build_mesh3(m, fsi3::axis_vertices3(br[0], seg[0], ns[0]), fsi3::axis_vertices3(br[1], seg[1], ns[1]),
+                    fsi3::axis_vertices3(br[2], seg[2], ns[2]), mesh->has_solid ? mesh->solid_box : nullptr);
+  *n_nodes = m.n_nodes;
+  *n_dofs = 7 * m.n_nodes;
+  *nnzb = m.nnzb;
+  return FSI_OK;
 }
 
 int fsi_mesh_size(const fsi_mesh* mesh, int* n_nodes, int* n_dofs, int* nnzb) {

@@ -63,6 +63,13 @@ class fsi_parareal_stats(C.Structure):
         return d
 
 
+class fsi_mesh3d(C.Structure):
+    _fields_ = [("n_xseg", C.c_int), ("x_breaks", C.POINTER(C.c_double)), ("nx_seg", C.POINTER(C.c_int)),
+                ("n_yseg", C.c_int), ("y_breaks", C.POINTER(C.c_double)), ("ny_seg", C.POINTER(C.c_int)),
+                ("n_zseg", C.c_int), ("z_breaks", C.POINTER(C.c_double)), ("nz_seg", C.POINTER(C.c_int)),
+                ("has_solid", C.c_int), ("solid_box", C.c_double * 6)]
+
+
 class fsi_instance(C.Structure):
     _fields_ = [("mesh", fsi_mesh), ("params", fsi_params), ("U", C.c_void_p), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("stats", fsi_parareal_stats), ("status", C.c_int), ("worker", C.c_int),
@@ -93,6 +100,7 @@ SIGNATURES = {
     "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
     "fsi_dense_invert": (_I, [_I, _I, _VP, _VP, _I, _VP]),
     "fsi_mesh_size": (_I, [C.POINTER(fsi_mesh), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "fsi3d_mesh_size": (_I, [C.POINTER(fsi_mesh3d), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "fsi_batch_plan": (_I, [C.POINTER(fsi_instance), _I, _I, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D),
                             C.POINTER(_D)]),
     "fsi_batch_parareal": (_I, [C.POINTER(fsi_instance), _I, _I, _VP]),
@@ -218,6 +226,22 @@ def mesh_size(w: wl.Workload):
     a, b, c = C.c_int(), C.c_int(), C.c_int()
     _check(lib.fsi_mesh_size(C.byref(mesh), C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def mesh3d_size(breaks, counts, solid_box=None):
+    """(n_nodes, n_dofs, nnzb) of a 3D mesh (break points and cells per segment per axis), on the host."""
+    lib = load_library()
+    keep, vals = [], []
+    for br, cn in zip(breaks, counts):
+        b = (C.c_double * len(br))(*br)
+        c = (C.c_int * len(cn))(*cn)
+        keep += [b, c]
+        vals += [len(cn), b, c]
+    box = (C.c_double * 6)(*(np.ravel(solid_box) if solid_box is not None else np.zeros(6)))
+    mesh = fsi_mesh3d(*vals, int(solid_box is not None), box)
+    a, b2, c2 = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.fsi3d_mesh_size(C.byref(mesh), C.byref(a), C.byref(b2), C.byref(c2)))
+    return a.value, b2.value, c2.value
 
 
 class Context:

@@ -256,3 +256,19 @@ def test_3d_channel_mesh_of_the_32x8x8_workload():
     assert mesh.n_nodes == 65 * 17 * 17 == 18785 and mesh.n_dofs == 131495
     assert mesh.cell_solid.sum() == 1 * 4 * 6                  # the plate is resolved by cell faces
     assert np.isclose(mesh.axes[0][9], 0.4) and np.isclose(mesh.axes[0][10], 0.45)
+
+
+def test_library_3d_mesh_size_matches_the_oracle_mesh():
+    """fsi3d_mesh_size (host code of the CUDA library) against the oracle mesh and the Q2 pattern count."""
+    from paper_1907_01252_gb300 import build, fsi
+    build.build_library()
+    counts = wl.cells_per_segment_3d(32, 8, 8)
+    nodes, dofs, nnzb = fsi.mesh3d_size([wl.X3_BREAKS, wl.Y3_BREAKS, wl.Z3_BREAKS], counts, wl.SOLID_BOX_3D)
+    assert (nodes, dofs) == (18785, 131495)
+    assert nnzb == (8 * 32 + 1) * (8 * 8 + 1) * (8 * 8 + 1) == 1085825
+    small = ((2, 1, 2), (1, 1), (1, 1, 1))
+    br = ((0.0, 0.4, 0.45, 0.9), (0.0, 0.2, 0.41), (0.0, 0.055, 0.355, 0.41))
+    m = on.make_mesh_nd(br, small, ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355)))
+    n, d, b = fsi.mesh3d_size(br, small)
+    pairs = {(int(a), int(c)) for cell in m.cell_nodes for a in cell for c in cell}
+    assert (n, d, b) == (m.n_nodes, m.n_dofs, len(pairs))
