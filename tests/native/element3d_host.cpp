@@ -129,3 +129,55 @@ extern "C" int fsi3_jacobian_host(const double* xb, const int* nxs, int nxseg, c
       for (int c = 0; c < 7; ++c) vals_out[(size_t)b * 49 + r * 7 + c] = fsi3::assemble3(v, Ke.data(), b, r, c);
   return 0;
 }
+
+#include "../../paper_1907_01252_gb300/csrc/fsi_mg3d.h"
+
+// One multigrid transfer between the mesh and its coarsening, run in host loops
+// over the per-entry functions the kernels will call. sizes_out = {nnx_f, nny_f,
+// nnz_f, nnx_c, nny_c, nnz_c}; coords_out (optional) = fine x, y, z node
+// coordinates then coarse ones; flags_out (optional) = fine then coarse node
+// flags. mode 1: out[fine][7] = prolongation of in[coarse][7]; mode 2:
+// out[coarse][7] = restriction of in[fine][7]; mode 3: out[coarse][7] = the fine
+// state in[fine][7] evaluated at the coarse nodes; mode 0: sizes only.
+extern "C" int fsi3_transfer_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
+                                  int nyseg, const double* zb, const int* nzs, int nzseg, const double* box, int mode,
+                                  const double* in, double* out, int* sizes_out, double* coords_out,
+                                  unsigned char* flags_out) {
+  std::vector<double> vf[3] = {fsi3::axis_vertices3(xb, nxs, nxseg), fsi3::axis_vertices3(yb, nys, nyseg),
+                               fsi3::axis_vertices3(zb, nzs, nzseg)};
+  const std::vector<int> segf[3] = {std::vector<int>(nxs, nxs + nxseg), std::vector<int>(nys, nys + nyseg),
+                                    std::vector<int>(nzs, nzs + nzseg)};
+  std::vector<double> vc[3];
+  std::vector<int> segc[3];
+  for (int a = 0; a < 3; ++a) fsi3::coarsen_axis3(vf[a], segf[a], vc[a], segc[a]);
+  fsi3::HostMesh3 F, Cm;
+  fsi3::build_mesh3(F, vf[0], vf[1], vf[2], box);
+  fsi3::build_mesh3(Cm, vc[0], vc[1], vc[2], box);
+  const std::vector<double> xf[3] = {F.xn, F.yn, F.zn}, xc[3] = {Cm.xn, Cm.yn, Cm.zn};
+  fsi3::Transfer3 T;
+  fsi3::build_transfer3(T, vc, xc, vf, xf);
+  for (int a = 0; a < 3; ++a) {
+    sizes_out[a] = T.nn_f[a];
+    sizes_out[3 + a] = T.nn_c[a];
+  }
+  if (coords_out) {
+    for (int a = 0; a < 3; ++a) coords_out = std::copy(xf[a].begin(), xf[a].end(), coords_out);
+    for (int a = 0; a < 3; ++a) coords_out = std::copy(xc[a].begin(), xc[a].end(), coords_out);
+  }
+  if (flags_out) {
+    flags_out = std::copy(F.node_flags.begin(), F.node_flags.end(), flags_out);
+    std::copy(Cm.node_flags.begin(), Cm.node_flags.end(), flags_out);
+  }
+  const fsi3::Transfer3View v = fsi3::view(T);
+  if (mode == 1)
+    for (int n = 0; n < F.n_nodes; ++n)
+      for (int c = 0; c < 7; ++c) out[(size_t)n * 7 + c] = fsi3::prolong3(v, F.node_flags.data(), in, n, c);
+  else if (mode == 2)
+    for (int n = 0; n < Cm.n_nodes; ++n)
+      for (int c = 0; c < 7; ++c)
+        out[(size_t)n * 7 + c] = fsi3::restrict3(v, F.node_flags.data(), Cm.node_flags.data(), in, n, c);
+  else if (mode == 3)
+    for (int n = 0; n < Cm.n_nodes; ++n)
+      for (int c = 0; c < 7; ++c) out[(size_t)n * 7 + c] = fsi3::interp_state3(v, in, n, c);
+  return 0;
+}

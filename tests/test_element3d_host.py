@@ -183,3 +183,131 @@ def test_assembled_3d_jacobian_matches_the_oracle(host_lib):
             blk_ref, blk = ref[ci::7, cj::7], A[ci::7, cj::7]
             sc = max(np.abs(blk_ref).max(), 1e-12 * np.abs(ref).max())
             assert np.abs(blk - blk_ref).max() <= 1e-10 * sc, (ci, cj)
+
+
+# A finer mesh whose segments have odd and even cell counts, so the coarsening
+# pairs cells in some segments and keeps a single cell at the end of others.
+COUNTS3_FINE = ((4, 1, 3), (2, 3), (2, 2, 1))
+
+
+def coarse_counts(counts):
+    return tuple(tuple((n + 1) // 2 for n in seg) for seg in counts)
+
+
+def q2_axis(breaks, counts, paired=False):
+    """Q2 node coordinates of one axis: uniform cells per segment, a midpoint per cell.
+    paired: the coarsening of that axis instead (every second vertex of a segment, plus
+    its end when the count is odd, so the last coarse cell is one fine cell)."""
+    v = [breaks[0]]
+    for s, n in enumerate(counts):
+        keep = list(range(2, n + 1, 2)) + ([n] if n % 2 else []) if paired else range(1, n + 1)
+        v += [breaks[s] + (breaks[s + 1] - breaks[s]) * i / n for i in keep]
+    v = np.array(v)
+    x = np.empty(2 * len(v) - 1)
+    x[0::2], x[1::2] = v, 0.5 * (v[:-1] + v[1:])
+    return x
+
+
+def transfer(host_lib, mode, inp, n_out):
+    P = C.POINTER(C.c_double)
+    host_lib.fsi3_transfer_host.argtypes = [P, C.c_void_p, C.c_int] * 3 + [P, C.c_int, P, P, C.c_void_p, P,
+                                                                           C.c_void_p]
+    args, keep = mesh_args(counts=COUNTS3_FINE)
+    sizes = np.zeros(6, dtype=np.int32)
+    out = np.zeros((n_out, 7))
+    inp = np.ascontiguousarray(inp, dtype=float) if inp is not None else np.zeros(1)
+    coords = np.zeros(sum(2 * sum(c) + 1 for c in COUNTS3_FINE) +
+                      sum(2 * sum(c) + 1 for c in coarse_counts(COUNTS3_FINE)))
+    fine = on.make_mesh_nd(BREAKS3, COUNTS3_FINE, BOX3)
+    coarse = on.make_mesh_nd(BREAKS3, coarse_counts(COUNTS3_FINE), BOX3)
+    flags = np.zeros(fine.n_nodes + coarse.n_nodes, dtype=np.uint8)
+    host_lib.fsi3_transfer_host(*args, mode, ptr(inp), ptr(out), sizes.ctypes.data_as(C.c_void_p), ptr(coords),
+                                flags.ctypes.data_as(C.c_void_p))
+    return out, sizes, coords, flags, fine, coarse
+
+
+def identity_mask(mesh):
+    """[node][7] True on identity rows: Dirichlet velocity, Dirichlet displacement, p = 0."""
+    return np.concatenate([np.repeat(mesh.dir_v[:, None], 3, 1), np.repeat(mesh.dir_u[:, None], 3, 1),
+                           mesh.p_identity[:, None]], axis=1)
+
+
+def node_points(xs):
+    """[node][3] coordinates of the tensor node grid with x fastest."""
+    X, Y, Z = np.meshgrid(*xs, indexing="ij")
+    return np.stack([X.ravel(order="F"), Y.ravel(order="F"), Z.ravel(order="F")], axis=1)
+
+
+def triquadratic(pts, seed, cubic=False):
+    """A random field of degree <= 2 in each coordinate per component (plus x^3 if cubic)."""
+    rng = np.random.default_rng(seed)
+    coef = rng.normal(size=(3, 3, 3, 7))
+    x, y, z = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]
+    f = sum(coef[a, b, c] * x ** a * y ** b * z ** c for a in range(3) for b in range(3) for c in range(3))
+    return f + (x ** 3 if cubic else 0.0)
+
+
+def test_3d_coarse_level_and_node_flags(host_lib):
+    """The coarsened level pairs cells per segment (odd counts keep one cell) and takes
+    the oracle's node flags on both levels (flags depend on the topology alone)."""
+    _, sizes, coords, flags, fine, coarse = transfer(host_lib, 0, None, 1)
+    xs_f = [q2_axis(b, c) for b, c in zip(BREAKS3, COUNTS3_FINE)]
+    xs_c = [q2_axis(b, c, paired=True) for b, c in zip(BREAKS3, COUNTS3_FINE)]
+    assert list(sizes) == [len(x) for x in xs_f + xs_c]
+    assert np.allclose(coords, np.concatenate(xs_f + xs_c), rtol=0, atol=1e-15)
+    ff, fc = flags[:fine.n_nodes], flags[fine.n_nodes:]
+    for m, fl in ((fine, ff), (coarse, fc)):
+        assert np.array_equal((fl & 1).astype(bool), m.dir_v)
+        assert np.array_equal((fl & 2).astype(bool), m.dir_u)
+        assert np.array_equal((fl & 4).astype(bool), m.p_identity)
+
+
+def test_3d_prolongation_reproduces_triquadratics(host_lib):
+    """Q2 interpolation from the coarse level is exact for fields of degree <= 2 in each
+    coordinate (zero on the fine identity rows), and not for a cubic."""
+    _, sizes, coords, _, fine, coarse = transfer(host_lib, 0, None, 1)
+    split = np.cumsum(sizes)[:-1]
+    xs = np.split(coords, split)
+    pf, pc = node_points(xs[:3]), node_points(xs[3:])
+    for seed, cubic in ((1, False), (2, False), (3, True)):
+        Pf, _, _, _, _, _ = transfer(host_lib, 1, triquadratic(pc, seed, cubic), fine.n_nodes)
+        want = np.where(identity_mask(fine), 0.0, triquadratic(pf, seed, cubic))
+        err = np.abs(Pf - want).max() / np.abs(want).max()
+        assert (err > 1e-4) if cubic else (err < 1e-13), (seed, err)
+
+
+def test_3d_state_interpolation_is_exact_and_injects(host_lib):
+    """The fine state at the coarse nodes: exact for tri-quadratics and, the levels being
+    nested, a plain injection of the fine values at the coinciding nodes (bit-exact)."""
+    _, sizes, coords, _, fine, coarse = transfer(host_lib, 0, None, 1)
+    xs = np.split(coords, np.cumsum(sizes)[:-1])
+    pf, pc = node_points(xs[:3]), node_points(xs[3:])
+    f = triquadratic(pf, 4)
+    Uc, _, _, _, _, _ = transfer(host_lib, 3, f, coarse.n_nodes)
+    assert np.abs(Uc - triquadratic(pc, 4)).max() <= 1e-13 * np.abs(f).max()
+    rng = np.random.default_rng(5)
+    Uf = rng.normal(size=(fine.n_nodes, 7))
+    Uc, _, _, _, _, _ = transfer(host_lib, 3, Uf, coarse.n_nodes)
+    idx = [np.searchsorted(xs[a], xs[3 + a]) for a in range(3)]
+    for a in range(3):
+        assert np.array_equal(xs[a][idx[a]], xs[3 + a])
+    I, J, K = np.meshgrid(*idx, indexing="ij")
+    inj = (I + sizes[0] * (J + sizes[1] * K)).ravel(order="F")
+    assert np.array_equal(Uc, Uf[inj])
+
+
+def test_3d_restriction_is_the_masked_transpose(host_lib):
+    """<R r, x> = <r, P (x on the free coarse rows)> for random vectors; R is zero on the
+    coarse identity rows and ignores the fine identity rows."""
+    _, _, _, _, fine, coarse = transfer(host_lib, 0, None, 1)
+    rng = np.random.default_rng(6)
+    r = rng.normal(size=(fine.n_nodes, 7))
+    x = rng.normal(size=(coarse.n_nodes, 7))
+    Rr, _, _, _, _, _ = transfer(host_lib, 2, r, coarse.n_nodes)
+    Px, _, _, _, _, _ = transfer(host_lib, 1, np.where(identity_mask(coarse), 0.0, x), fine.n_nodes)
+    lhs, rhs = np.sum(Rr * x), np.sum(r * Px)
+    assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(Rr ** 2) * np.sum(x ** 2)), (lhs, rhs)
+    assert np.all(Rr[identity_mask(coarse)] == 0.0)
+    r2 = np.where(identity_mask(fine), 1e6 * rng.normal(size=r.shape), r)
+    Rr2, _, _, _, _, _ = transfer(host_lib, 2, r2, coarse.n_nodes)
+    assert np.array_equal(Rr, Rr2)
