@@ -34,7 +34,10 @@
 namespace fsi3 {
 
 enum : uint8_t { N3_DIR_V = 1, N3_DIR_U = 2, N3_P_ID = 4, N3_IN_SOLID = 8, N3_INFLOW = 16 };
-enum : uint8_t { C3_SOLID = 1, C3_OUTFLOW = 2 };
+// C3_U_DECOUPLED: a fluid cell none of whose nodes lies in the closure of the
+// solid; its displacement rows are harmonic-extension or identity rows, which
+// couple each displacement component only to itself.
+enum : uint8_t { C3_SOLID = 1, C3_OUTFLOW = 2, C3_U_DECOUPLED = 4 };
 
 struct HostMesh3 {
   int nx = 0, ny = 0, nz = 0, nnx = 0, nny = 0, nnz = 0, n_nodes = 0, n_cells = 0, nnzb = 0;
@@ -46,6 +49,7 @@ struct HostMesh3 {
   std::vector<int> rowptr, colidx;    // node block pattern (nodes sharing a cell)
   std::vector<int> blk_row;           // [nnzb] row node of each block
   std::vector<int> blk_src;           // [nnzb][8]: cell * 729 + li * 27 + lj, ascending cells, -1 padded
+  std::vector<int> cell_blk;          // [cell][27][27]: block of (local row node, local column node)
   double y0 = 0, y1 = 0, z0 = 0, z1 = 0;
 };
 
@@ -117,6 +121,11 @@ inline void build_mesh3(HostMesh3& m, const std::vector<double>& xv, const std::
         if (!in_fluid[n]) f |= N3_P_ID;
         m.node_flags[n] = f;
       }
+  for (int c = 0; c < m.n_cells; ++c) {
+    bool dec = !(m.cell_flags[c] & C3_SOLID);
+    for (int l = 0; l < 27 && dec; ++l) dec = !(m.node_flags[m.cell_nodes[(size_t)c * 27 + l]] & N3_IN_SOLID);
+    if (dec) m.cell_flags[c] |= C3_U_DECOUPLED;
+  }
   m.node_cells.assign((size_t)m.n_nodes * 8, -1);
   std::vector<int> cnt(m.n_nodes, 0);
   for (int c = 0; c < m.n_cells; ++c)
@@ -143,6 +152,7 @@ inline void build_mesh3(HostMesh3& m, const std::vector<double>& xv, const std::
   for (int n = 0; n < m.n_nodes; ++n)
     for (int b = m.rowptr[n]; b < m.rowptr[n + 1]; ++b) m.blk_row[b] = n;
   m.blk_src.assign((size_t)m.nnzb * 8, -1);
+  m.cell_blk.assign((size_t)m.n_cells * 729, -1);
   std::vector<int> bcnt(m.nnzb, 0);
   for (int c = 0; c < m.n_cells; ++c)
     for (int li = 0; li < 27; ++li)
@@ -151,6 +161,7 @@ inline void build_mesh3(HostMesh3& m, const std::vector<double>& xv, const std::
         const int b = (int)(std::lower_bound(m.colidx.begin() + m.rowptr[ni], m.colidx.begin() + m.rowptr[ni + 1], nj) -
                             m.colidx.begin());
         m.blk_src[(size_t)b * 8 + bcnt[b]++] = c * 729 + li * 27 + lj;
+        m.cell_blk[(size_t)c * 729 + li * 27 + lj] = b;
       }
 }
 
@@ -162,6 +173,7 @@ struct Mesh3View {
   const int* node_cells;
   double y0, y1, z0, z1;
   const int *blk_row, *colidx, *blk_src;
+  const int* cell_blk;
 };
 
 FSI3M_HD inline double inflow_ramp3(double t, double ramp_t) {

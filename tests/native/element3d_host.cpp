@@ -41,7 +41,7 @@ fsi3::HostMesh3 make_mesh(const double* xb, const int* nxs, int nxseg, const dou
 fsi3::Mesh3View view(const fsi3::HostMesh3& m) {
   return fsi3::Mesh3View{m.nnx, m.nny, m.nnz, m.n_nodes, m.n_cells, m.yn.data(), m.zn.data(),
                          m.cell_flags.data(), m.node_flags.data(), m.node_cells.data(), m.y0, m.y1, m.z0, m.z1,
-                         m.blk_row.data(), m.colidx.data(), m.blk_src.data()};
+                         m.blk_row.data(), m.colidx.data(), m.blk_src.data(), m.cell_blk.data()};
 }
 }  // namespace
 
@@ -179,5 +179,49 @@ extern "C" int fsi3_transfer_host(const double* xb, const int* nxs, int nxseg, c
   else if (mode == 3)
     for (int n = 0; n < Cm.n_nodes; ++n)
       for (int c = 0; c < 7; ++c) out[(size_t)n * 7 + c] = fsi3::interp_state3(v, in, n, c);
+  return 0;
+}
+
+#include "../../paper_1907_01252_gb300/csrc/fsi_vanka3.h"
+
+namespace {
+template <typename T>
+int vanka_cells(const fsi3::HostMesh3& m, const double* A, const double* r, double* zc) {
+  const fsi3::Mesh3View v = view(m);
+  std::vector<T> At(A, A + (size_t)m.nnzb * 49), inv(fsi3::VK3_SIZE), sh(fsi3::VK3_SH_T), ap(fsi3::VK3_AP_T),
+      rl(189), z(189);
+  std::vector<int> ish(fsi3::VK3_SH_I);
+  const fsi3::HostCta cta;
+  for (int c = 0; c < m.n_cells; ++c) {
+    if (!fsi3::vk3_setup_cell(cta, v, At.data(), c, sh.data(), ish.data(), inv.data())) return -(c + 1);
+    for (int l = 0; l < 27; ++l)
+      for (int f = 0; f < 7; ++f) rl[l * 7 + f] = (T)r[(size_t)m.cell_nodes[(size_t)c * 27 + l] * 7 + f];
+    fsi3::vk3_apply_cell(cta, (m.cell_flags[c] & fsi3::C3_U_DECOUPLED) != 0, inv.data(), rl.data(), ap.data(),
+                         z.data());
+    for (int e = 0; e < 189; ++e) zc[(size_t)c * 189 + e] = (double)z[e];
+  }
+  return 0;
+}
+}  // namespace
+
+// Vanka local solves of every cell of one slice: zc[cell][189] = (local matrix)^{-1}
+// (local residual) in local dof order, computed by the block elimination in T =
+// double (precision 0) or float (precision 1) from the Jacobian blocks A[nnzb][49]
+// (the mesh's own pattern) and the residual r[n_nodes][7]. x_out (optional):
+// the damped node average omega / cnt * (sum of the cells' corrections).
+// cell_flags_out (optional): the cell flags. Returns -(cell + 1) on a singular block.
+extern "C" int fsi3_vanka_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
+                               int nyseg, const double* zb, const int* nzs, int nzseg, const double* box,
+                               const double* A, const double* r, int precision, double omega, double* zc,
+                               double* x_out, unsigned char* cell_flags_out) {
+  const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
+  const int rc = precision ? vanka_cells<float>(m, A, r, zc) : vanka_cells<double>(m, A, r, zc);
+  if (rc) return rc;
+  if (cell_flags_out) std::copy(m.cell_flags.begin(), m.cell_flags.end(), cell_flags_out);
+  if (x_out) {
+    const fsi3::Mesh3View v = view(m);
+    for (int n = 0; n < m.n_nodes; ++n)
+      for (int c = 0; c < 7; ++c) x_out[(size_t)n * 7 + c] = fsi3::vk3_gather(v, zc, omega, n, c);
+  }
   return 0;
 }
