@@ -303,6 +303,61 @@ typedef struct fsi_mesh3d {
  * Jacobian's node pattern. Errors: FSI_EINVAL (bad mesh, null output). */
 int fsi3d_mesh_size(const fsi_mesh3d* mesh, int* n_nodes, int* n_dofs, int* nnzb);
 
+/* ---- 3D path: the same method on hexahedral Q2 elements ------------------
+ * The theta step of Sec. 2.3 in three dimensions: 27-node hexahedra, 7
+ * unknowns per node (v_x, v_y, v_z, u_x, u_y, u_z, p), 3 x 3 x 3 Gauss points.
+ * Fluid: no-slip on the four lateral walls; inflow 36 vbar s(t) (y - y0)(y1 - y)
+ * (z - z0)(z1 - z) / ((y1 - y0)^2 (z1 - z0)^2) with the ramp s(t) of the 2D
+ * path; free outflow. Displacement: zero on the outer boundary. Solved by Newton with FGMRES (classical
+ * Gram-Schmidt twice; the Hessenberg matrices live on the host) and a V-cycle
+ * over interface-fitted coarsenings. The V-cycle uses block Vanka local solves:
+ * velocity-pressure block and displacement Schur complement, in FP64 or
+ * (precision 2) FP32, and a dense inverse on the coarsest level (at most 4096
+ * dofs). Parameters as fsi_params, with these limits: precision 0 or 2;
+ * gmres_restart <= 63; the mesh must coarsen at least once; mg_smoother 1
+ * sweeps eight cell colours; graph_max_batch and pipeline_chunk are ignored.
+ * Device arrays are [S][n_dofs] (node-major, 7 per node); Jacobian blocks are
+ * [S][nnzb][7][7] row-major. Calls on one context are serialised by the caller.
+ * Every call synchronises its stream before it returns. */
+typedef struct fsi3_ctx fsi3_ctx;
+
+/* Build the level hierarchy and all device workspace. Errors: FSI_EINVAL (bad
+ * mesh or parameters), FSI_ENOMEM, FSI_ECUDA. */
+int fsi3_setup(const fsi_mesh3d* mesh, const fsi_params* params, fsi3_ctx** out);
+void fsi3_destroy(fsi3_ctx* ctx);
+int fsi3_n_nodes(const fsi3_ctx* ctx);
+int fsi3_n_dofs(const fsi3_ctx* ctx);
+int fsi3_n_levels(const fsi3_ctx* ctx);
+int fsi3_nnzb(const fsi3_ctx* ctx);
+/* Host copy of the block pattern: rowptr [n_nodes + 1], colidx [nnzb]. */
+int fsi3_bsr_pattern(const fsi3_ctx* ctx, int* rowptr, int* colidx);
+
+/* Residual of one theta step for S slices (as fsi_residual): U, U_old, R
+ * device [S][n_dofs], t_new host [S]. Errors: FSI_EINVAL. */
+int fsi3_residual(fsi3_ctx* ctx, int S, const double* U, const double* U_old,
+                  const double* t_new, double k, double theta, double* R, void* stream);
+
+/* Jacobian dR/dU in 7 x 7 blocks: vals device [S][nnzb][49]. Errors: FSI_EINVAL. */
+int fsi3_jacobian(fsi3_ctx* ctx, int S, const double* U, const double* U_old,
+                  double k, double theta, double* vals, void* stream);
+
+/* One theta step for S slices (as fsi_theta_step). Errors: FSI_ENEWTON,
+ * FSI_EGMRES, FSI_EJAC, FSI_ENAN, FSI_EINVAL. */
+int fsi3_theta_step(fsi3_ctx* ctx, int S, const double* U_old, const double* t_old,
+                    double k, double theta, double* U_new, fsi_stats* stats, void* stream);
+
+/* Fine and coarse propagators of Sec. 3 (as fsi_fine, fsi_coarse); S may exceed
+ * max_batch (batches of max_batch). */
+int fsi3_fine(fsi3_ctx* ctx, int S, const double* U0, const double* t0, double* U1,
+              fsi_stats* stats, void* stream);
+int fsi3_coarse(fsi3_ctx* ctx, int S, const double* U0, const double* t0, double* U1,
+                fsi_stats* stats, void* stream);
+
+/* Parareal iteration of Sec. 3 (as parareal_iterate, serial sweeps): U device
+ * [n_slices + 1][n_dofs]. Errors: as fsi3_theta_step, FSI_EDIVERGE. */
+int fsi3_parareal(fsi3_ctx* ctx, double* U, int max_iter, double tol,
+                  fsi_parareal_stats* stats, void* stream);
+
 /* ---- Batches of independent problems (beyond the paper, which solves one
  * problem at a time) ----------------------------------------------------
  * Many independent FSI problems of uneven meshes, materials and slice counts,

@@ -106,6 +106,19 @@ SIGNATURES = {
     "fsi_batch_parareal": (_I, [C.POINTER(fsi_instance), _I, _I, _VP]),
     "fsi_batch_autotune": (_I, [C.POINTER(fsi_instance), _I, C.POINTER(_I), _I, C.POINTER(_D), C.POINTER(_I),
                                 _VP]),
+    "fsi3_setup": (_I, [C.POINTER(fsi_mesh3d), C.POINTER(fsi_params), C.POINTER(_VP)]),
+    "fsi3_destroy": (None, [_VP]),
+    "fsi3_n_nodes": (_I, [_VP]),
+    "fsi3_n_dofs": (_I, [_VP]),
+    "fsi3_n_levels": (_I, [_VP]),
+    "fsi3_nnzb": (_I, [_VP]),
+    "fsi3_bsr_pattern": (_I, [_VP, C.POINTER(_I), C.POINTER(_I)]),
+    "fsi3_residual": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
+    "fsi3_jacobian": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
+    "fsi3_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
+    "fsi3_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
+    "fsi3_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
+    "fsi3_parareal": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
     "fsi_profile_enable": (_I, [C.c_ulonglong]),
     "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
     "fsi_launch_count": (C.c_longlong, [_I]),
@@ -383,6 +396,112 @@ class Context:
 
 def fsi_setup(workload, max_batch=1, **overrides):
     return Context(workload, max_batch, **overrides)
+
+
+def _mesh3d_struct(w: wl.Workload3D):
+    """(fsi_mesh3d, arrays it points into) for a 3D workload's interface-fitted mesh."""
+    keep, vals = [], []
+    for br, cn in zip(w.breaks, w.segments):
+        b = (C.c_double * len(br))(*br)
+        c = (C.c_int * len(cn))(*cn)
+        keep += [b, c]
+        vals += [len(cn), b, c]
+    box = (C.c_double * 6)(*np.ravel(wl.SOLID_BOX_3D))
+    keep.append(box)
+    return fsi_mesh3d(*vals, int(w.with_solid), box), keep
+
+
+class Context3D:
+    """An fsi3_ctx (the 3D path) built for a Workload3D. Arrays are device float64
+    tensors [S, n_dofs] (7 per node: v, u, p); Jacobian blocks [S, nnzb, 7, 7]."""
+
+    def __init__(self, workload: wl.Workload3D, max_batch: int = 1, **overrides):
+        lib = load_library()
+        w = workload
+        self._mesh, self._keep = _mesh3d_struct(w)
+        base = wl.Workload("3d", nx=1, ny=1, T=w.T, n_slices=w.n_slices, m_fine=w.m_fine, m_coarse=w.m_coarse,
+                           newton_tol=w.newton_tol, newton_maxit=w.newton_maxit, gmres_restart=w.gmres_restart,
+                           gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol, gmres_rtol_first=w.gmres_rtol_first,
+                           newton_eta=w.newton_eta, material=w.material)
+        p = _params(base, max_batch, dict(dict(mg_coarsest_max_dofs=2000, precision=2, graph_max_batch=0),
+                                          **overrides))
+        self.params = p
+        self._params = fsi_params(**p)
+        h = C.c_void_p()
+        _check(lib.fsi3_setup(C.byref(self._mesh), C.byref(self._params), C.byref(h)))
+        self.handle, self.lib, self.workload, self.max_batch = h, lib, w, max_batch
+        self.n_nodes = lib.fsi3_n_nodes(h)
+        self.n_dofs = lib.fsi3_n_dofs(h)
+        self.nnzb = lib.fsi3_nnzb(h)
+        self.n_levels = lib.fsi3_n_levels(h)
+
+    def close(self):
+        if self.handle:
+            self.lib.fsi3_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fsi3_residual(self, U, U_old, t_new, k, theta, R=None):
+        import torch
+        R = torch.empty_like(U) if R is None else R
+        t, tp = _dbl(t_new)
+        _check(self.lib.fsi3_residual(self.handle, U.shape[0], _ptr(U), _ptr(U_old), tp, k, theta, _ptr(R),
+                                      _stream()))
+        return R
+
+    def fsi3_jacobian(self, U, U_old, k, theta, vals=None):
+        import torch
+        S = U.shape[0]
+        vals = torch.empty((S, self.nnzb, 7, 7), dtype=torch.float64, device=U.device) if vals is None else vals
+        _check(self.lib.fsi3_jacobian(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
+        return vals
+
+    def fsi3_bsr_pattern(self):
+        rowptr = np.zeros(self.n_nodes + 1, dtype=np.int32)
+        colidx = np.zeros(self.nnzb, dtype=np.int32)
+        _check(self.lib.fsi3_bsr_pattern(self.handle, rowptr.ctypes.data_as(C.POINTER(C.c_int)),
+                                         colidx.ctypes.data_as(C.POINTER(C.c_int))))
+        return rowptr, colidx
+
+    _propagator_call = Context._propagator_call
+
+    def fsi3_theta_step(self, U_old, t_old, k, theta, U_new=None):
+        import torch
+        U_new = torch.empty_like(U_old) if U_new is None else U_new
+        t, tp = _dbl(t_old)
+        d = self._propagator_call(self.lib.fsi3_theta_step, U_old.shape[0], _ptr(U_old), tp, k, theta,
+                                  _ptr(U_new))
+        return U_new, d
+
+    def fsi3_fine(self, U0, t0, U1=None):
+        import torch
+        U1 = torch.empty_like(U0) if U1 is None else U1
+        t, tp = _dbl(t0)
+        return U1, self._propagator_call(self.lib.fsi3_fine, U0.shape[0], _ptr(U0), tp, _ptr(U1))
+
+    def fsi3_coarse(self, U0, t0, U1=None):
+        import torch
+        U1 = torch.empty_like(U0) if U1 is None else U1
+        t, tp = _dbl(t0)
+        return U1, self._propagator_call(self.lib.fsi3_coarse, U0.shape[0], _ptr(U0), tp, _ptr(U1))
+
+    def fsi3_parareal(self, U, max_iter, tol, history=False):
+        """U: device [n_slices + 1, n_dofs]; U[0] is the initial state. In place."""
+        st = fsi_parareal_stats()
+        hist = np.zeros((max(max_iter, 1), 3)) if history else None
+        if history:
+            st.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.history_len = max_iter
+        _check(self.lib.fsi3_parareal(self.handle, _ptr(U), max_iter, tol, C.byref(st), _stream()))
+        d = st.as_dict()
+        if history:
+            d["history"] = hist[:d["iterations"]].tolist()
+        return U, d
 
 
 def tip_functional(ctx: Context, U0, t0, n_steps):

@@ -120,6 +120,61 @@ def cells_per_segment_3d(nx, ny, nz):
     return (cells_per_segment(X3_BREAKS, nx), cells_per_segment(Y3_BREAKS, ny), cells_per_segment(Z3_BREAKS, nz))
 
 
+@dataclasses.dataclass(frozen=True)
+class Workload3D:
+    """The 3D channel with the plate: nx x ny x nz hexahedral Q2 cells split over the
+    segments of X3/Y3/Z3_BREAKS, interval T cut into n_slices slices of m_fine fine and
+    m_coarse coarse steps, solver settings as for Workload."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    T: float
+    n_slices: int
+    m_fine: int
+    m_coarse: int = 1
+    newton_tol: float = 1e-10
+    newton_maxit: int = 20
+    gmres_restart: int = 50
+    gmres_maxit: int = 2000
+    gmres_rtol: float = 1e-12
+    gmres_rtol_first: float = 1e-6
+    newton_eta: float = 1e-3
+    parareal_tol: float = 1e-8
+    material: Material = Material()
+    with_solid: bool = True
+
+    @property
+    def segments(self):
+        return cells_per_segment_3d(self.nx, self.ny, self.nz)
+
+    @property
+    def breaks(self):
+        return (X3_BREAKS, Y3_BREAKS, Z3_BREAKS)
+
+    @property
+    def n_nodes(self):
+        return (2 * self.nx + 1) * (2 * self.ny + 1) * (2 * self.nz + 1)
+
+    @property
+    def n_dofs(self):
+        return 7 * self.n_nodes
+
+    @property
+    def k_fine(self):
+        return self.T / self.n_slices / self.m_fine
+
+    @property
+    def k_coarse(self):
+        return self.T / self.n_slices / self.m_coarse
+
+
+# 3D channel, 8 x 4 x 4 Q2 hexahedra (9,639 dofs): a small case of the 3D path.
+SMALL3D_8x4x4 = Workload3D("fsi3d_q2_8x4x4_T1_8x4", nx=8, ny=4, nz=4, T=1.0, n_slices=8, m_fine=4)
+# 3D channel at scale: 32 x 8 x 8 Q2 hexahedra (131,495 dofs), T = 1, 32 slices x 16 fine steps.
+CHANNEL3D_32x8x8 = Workload3D("fsi3d_q2_32x8x8_T1_32x16", nx=32, ny=8, nz=8, T=1.0, n_slices=32, m_fine=16)
+
+
 def node_axis(breaks, counts):
     """Node coordinates of the Q2 mesh along one axis: 2 n + 1 uniform nodes per
     segment of n cells, shared at the break points."""
