@@ -112,28 +112,47 @@ __global__ void k3_gather_residual(Dev3 d, Phys3D P, const double* __restrict__ 
                                     P.vbar, P.ramp_t);
 }
 
-// Per cell: the element matrix Ke[s][cell][189][189]; lps_scale multiplies the
-// stabilisation weight (coarse multigrid levels).
-__global__ void __launch_bounds__(64) k3_cell_jacobian(Dev3 d, Phys3D P, const double* __restrict__ U,
-                                                      const double* __restrict__ Uo, size_t stride, double k,
-                                                      double theta, double lps_scale,
-                                                      const uint8_t* __restrict__ active, double* __restrict__ Ke) {
+// Per cell: the element matrix Ke[s][cell][189][189], one CTA per (cell, slice)
+// running the cooperative routine; lps_scale multiplies the stabilisation
+// weight (coarse multigrid levels). Dynamic shared memory CJ3_TOTAL doubles.
+constexpr int CJ3_THREADS = 256;
+
+__global__ void __launch_bounds__(CJ3_THREADS) k3_cell_jacobian(Dev3 d, Phys3D P, const double* __restrict__ U,
+                                                               const double* __restrict__ Uo, size_t stride, double k,
+                                                               double theta, double lps_scale,
+                                                               const uint8_t* __restrict__ active,
+                                                               double* __restrict__ Ke) {
   const int s = blockIdx.y;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cell = blockIdx.x;
   if (!active[s] || cell >= d.v.n_cells) return;
-  double Ue[189], Uoe[189];
+  extern __shared__ __align__(16) double shj[];
   const int* cn = d.cell_nodes + (size_t)cell * 27;
-  for (int l = 0; l < 27; ++l)
-    for (int f = 0; f < 7; ++f) {
-      Ue[l * 7 + f] = U[s * stride + (size_t)cn[l] * 7 + f];
-      Uoe[l * 7 + f] = Uo[s * stride + (size_t)cn[l] * 7 + f];
-    }
+  for (int e = threadIdx.x; e < 189; e += blockDim.x) {
+    const size_t g = s * stride + (size_t)cn[e / 7] * 7 + e % 7;
+    shj[fsi3::CJ3_UE + e] = U[g];
+    shj[fsi3::CJ3_UE + 189 + e] = Uo[g];
+  }
+  __syncthreads();
   const double* h = d.cell_h + (size_t)cell * 3;
+  double* alpha_slot = shj + fsi3::CJ3_FLAG + 7;   // the eighth flag slot is free
+  if (threadIdx.x == 0)
+    *alpha_slot = lps_scale * fsi3::stab_weight3(c_tab3, shj + fsi3::CJ3_UE + 189, h, P.alpha0, P.rho_f, P.nu_f);
+  __syncthreads();
+  const double alpha = *alpha_slot;
   const uint8_t cf = d.v.cell_flags[cell];
-  const double alpha = lps_scale * fsi3::stab_weight3(c_tab3, Uoe, h, P.alpha0, P.rho_f, P.nu_f);
   const fsi3::Phys3 ph{P.rho_f, P.nu_f, P.rho_s, P.mu_s, P.lambda_s};
-  fsi3::cell_jacobian3(ph, c_tab3, Ue, Uoe, h, cf & fsi3::C3_SOLID, cf & fsi3::C3_OUTFLOW, k, theta, alpha,
-                       Ke + ((size_t)s * d.v.n_cells + cell) * 189 * 189);
+  fsi3::cell_jacobian3_cta(fsi3::DevCta{(int)threadIdx.x, (int)blockDim.x}, ph, c_tab3, h, cf & fsi3::C3_SOLID,
+                           cf & fsi3::C3_OUTFLOW, k, theta, alpha, shj,
+                           Ke + ((size_t)s * d.v.n_cells + cell) * 189 * 189);
+}
+
+int launch_cell_jacobian(const Dev3& d, int n_cells, int S, const Phys3D& P, const double* U, const double* Uo,
+                         size_t stride, double k, double theta, double lps, const uint8_t* act, double* Ke,
+                         cudaStream_t st) {
+  const int smem = fsi3::CJ3_TOTAL * (int)sizeof(double);
+  CK3(cudaFuncSetAttribute(k3_cell_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k3_cell_jacobian<<<dim3(n_cells, S), CJ3_THREADS, smem, st>>>(d, P, U, Uo, stride, k, theta, lps, act, Ke);
+  return launched3();
 }
 
 // A[s][b][r][c] = the fixed-order gather of the element matrices (identity rows: unit diagonal).
@@ -613,8 +632,7 @@ int residual3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
 // FP64 blocks of level L for the state (U, Uo) into A64 (or the level's own FP64 buffer).
 int jacobian3(fsi3_ctx* c, fsi3_level& L, int S, const double* U, const double* Uo, double k, double theta,
               double lps, const uint8_t* act, double* A, cudaStream_t st) {
-  k3_cell_jacobian<<<dim3(nb3(L.h.n_cells, 64), S), 64, 0, st>>>(L.d, c->P, U, Uo, L.n, k, theta, lps, act, c->Ke);
-  TRY3(launched3());
+  TRY3(launch_cell_jacobian(L.d, L.h.n_cells, S, c->P, U, Uo, L.n, k, theta, lps, act, c->Ke, st));
   k3_assemble<double><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, c->Ke, act, A);
   return launched3();
 }
@@ -644,9 +662,7 @@ int mg_setup3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
           L.h.nnzb * 49, 1.0, c->A64, (size_t)L.h.nnzb * 49, 0.0, act, A, (size_t)L.h.nnzb * 49);
       TRY3(launched3());
     } else {
-      k3_cell_jacobian<<<dim3(nb3(L.h.n_cells, 64), S), 64, 0, st>>>(L.d, c->P, Ul, Uol, L.n, k, theta, lps, act,
-                                                                      c->Ke);
-      TRY3(launched3());
+      TRY3(launch_cell_jacobian(L.d, L.h.n_cells, S, c->P, Ul, Uol, L.n, k, theta, lps, act, c->Ke, st));
       k3_assemble<T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, c->Ke, act, A);
       TRY3(launched3());
     }

@@ -22,6 +22,8 @@
 
 #include <cmath>
 
+#include "fsi_cta.h"
+
 #ifdef __CUDACC__
 #define FSI3_HD __host__ __device__
 #else
@@ -407,6 +409,29 @@ FSI3_HD inline void cell_residual3(const Phys3& P, const Tables3& T, const doubl
   }
 }
 
+// States, gradients and old values at volume quadrature point q of a cell.
+FSI3_HD inline Qp3 qp_state3(const Tables3& T, const double* Ue, const double* Uo, const double* h, int q) {
+  Qp3 x{};
+  for (int l = 0; l < 27; ++l) {
+    const double ph = T.phi[q][l];
+    const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
+    for (int c = 0; c < 3; ++c) {
+      x.v[c] += ph * Ue[l * 7 + c];
+      x.u[c] += ph * Ue[l * 7 + 3 + c];
+      x.vo[c] += ph * Uo[l * 7 + c];
+      x.uo[c] += ph * Uo[l * 7 + 3 + c];
+      for (int jj = 0; jj < 3; ++jj) {
+        x.G.m[c][jj] += g[jj] * Ue[l * 7 + c];
+        x.Hu.m[c][jj] += g[jj] * Ue[l * 7 + 3 + c];
+        x.Go.m[c][jj] += g[jj] * Uo[l * 7 + c];
+        x.Huo.m[c][jj] += g[jj] * Uo[l * 7 + 3 + c];
+      }
+    }
+    x.p += ph * Ue[l * 7 + 6];
+  }
+  return x;
+}
+
 // Element matrix of one cell, Ke[(l * 7 + ci) * 189 + m * 7 + cj] = dRe[l, ci] / dUe[m, cj]
 // (before the row selection of the assembly), by the two-stage contraction
 // K += sum_q W B_l^T D_q B_m with the 28 x 28 tangent D_q of qp_flux3_lin.
@@ -416,24 +441,7 @@ FSI3_HD inline void cell_jacobian3(const Phys3& P, const Tables3& T, const doubl
   for (int i = 0; i < 189 * 189; ++i) Ke[i] = 0.0;
   const double vol = h[0] * h[1] * h[2];
   for (int q = 0; q < 27; ++q) {
-    Qp3 x{};
-    for (int l = 0; l < 27; ++l) {
-      const double ph = T.phi[q][l];
-      const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
-      for (int c = 0; c < 3; ++c) {
-        x.v[c] += ph * Ue[l * 7 + c];
-        x.u[c] += ph * Ue[l * 7 + 3 + c];
-        x.vo[c] += ph * Uo[l * 7 + c];
-        x.uo[c] += ph * Uo[l * 7 + 3 + c];
-        for (int jj = 0; jj < 3; ++jj) {
-          x.G.m[c][jj] += g[jj] * Ue[l * 7 + c];
-          x.Hu.m[c][jj] += g[jj] * Ue[l * 7 + 3 + c];
-          x.Go.m[c][jj] += g[jj] * Uo[l * 7 + c];
-          x.Huo.m[c][jj] += g[jj] * Uo[l * 7 + 3 + c];
-        }
-      }
-      x.p += ph * Ue[l * 7 + 6];
-    }
+    const Qp3 x = qp_state3(T, Ue, Uo, h, q);
     double D[28][28];   // [test slot ci * 4 + a][trial direction cj * 4 + b]
     for (int dir = 0; dir < 28; ++dir) {
       const int cj = dir / 4, b = dir % 4;
@@ -507,6 +515,155 @@ FSI3_HD inline void cell_jacobian3(const Phys3& P, const Tables3& T, const doubl
               for (int c = 0; c < 3; ++c) Ke[(l * 7 + c) * 189 + m * 7 + cj] += W * T.phi_f[f][l] * o[c] * gf[b][m];
         }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The element matrix computed by a cooperative thread group (fsi_cta.h): the
+// arithmetic of cell_jacobian3 in the same order, so the result is the same
+// bit for bit, with the work spread over the group and each entry of Ke
+// written once. The tangent columns of one trial field cj (27 points x 28
+// test slots x 4 directions) are computed together. For each test field ci,
+// a (ci, cj) block whose tangents vanish at every point is written as zeros
+// (unless the pressure stabilisation or the outflow face adds to it).
+// Otherwise E[q][a][m] = W_q sum_b D_q[ci a][cj b] B_b(m, q), and then
+// Ke[l ci][m cj] = sum_q sum_a B_a(l, q) E[q][a][m], plus the stabilisation
+// and outflow terms.
+// Shared scratch (doubles, CJ3_TOTAL); the caller stores Ue at CJ3_UE and Uo
+// at CJ3_UE + 189 and synchronises before the call.
+// ---------------------------------------------------------------------------
+constexpr int CJ3_XSZ = (int)(sizeof(Qp3) / sizeof(double));
+constexpr int CJ3_X = 0;                        // Qp3[27]
+constexpr int CJ3_B = CJ3_X + 27 * CJ3_XSZ;     // [27 q][4 a][27 l]
+constexpr int CJ3_W = CJ3_B + 27 * 4 * 27;      // [27] W_q
+constexpr int CJ3_D = CJ3_W + 27;               // [27 q][28 slots][4 b]: columns of the current trial field
+constexpr int CJ3_E = CJ3_D + 27 * 28 * 4;      // [27 q][4 a][27 m]
+constexpr int CJ3_FG = CJ3_E + 27 * 4 * 27;     // [9 face points][G, Hu]
+constexpr int CJ3_FO = CJ3_FG + 9 * 18;         // [9 face points][3 c][3 b] face tangents of the current field
+constexpr int CJ3_FLAG = CJ3_FO + 81;           // [7] nonzero flags of the (ci, cj) blocks
+constexpr int CJ3_UE = CJ3_FLAG + 8;            // Ue[189], Uo[189]
+constexpr int CJ3_TOTAL = CJ3_UE + 378;
+static_assert(sizeof(Qp3) % sizeof(double) == 0, "Qp3 holds doubles only");
+
+FSI3_HD inline bool cj3_nonzero(double x) {
+#ifdef __CUDA_ARCH__
+  return (__double_as_longlong(x) << 1) != 0;   // bit test: keeps the FP64 pipe free
+#else
+  return x != 0.0 || x != x;
+#endif
+}
+
+template <class Cta>
+FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tables3& T, const double* h, bool solid,
+                                       bool outflow, double k, double theta, double alpha, double* sh, double* Ke) {
+  const double* Ue = sh + CJ3_UE;
+  const double* Uo = Ue + 189;
+  Qp3* X = reinterpret_cast<Qp3*>(sh + CJ3_X);
+  double* B = sh + CJ3_B;
+  double* Wq = sh + CJ3_W;
+  double* Dc = sh + CJ3_D;
+  double* E = sh + CJ3_E;
+  double* FG = sh + CJ3_FG;
+  double* FO = sh + CJ3_FO;
+  double* flag = sh + CJ3_FLAG;
+  const double vol = h[0] * h[1] * h[2];
+  const bool face = outflow && !solid;
+  for (int q = cta.tid; q < 27; q += cta.nt) {
+    X[q] = qp_state3(T, Ue, Uo, h, q);
+    Wq[q] = T.wq[q] * vol;
+  }
+  for (int e = cta.tid; e < 27 * 4 * 27; e += cta.nt) {
+    const int q = e / 108, a = (e / 27) % 4, l = e % 27;
+    B[e] = a == 0 ? T.phi[q][l] : T.dphi[a - 1][q][l] / h[a - 1];
+  }
+  if (face)
+    for (int f = cta.tid; f < 9; f += cta.nt) {
+      M3 G{}, Hu{};
+      for (int l = 0; l < 27; ++l) {
+        double gf[3];
+        for (int a = 0; a < 3; ++a) gf[a] = T.dphi_f[a][f][l] / h[a];
+        for (int c = 0; c < 3; ++c)
+          for (int jj = 0; jj < 3; ++jj) {
+            G.m[c][jj] += gf[jj] * Ue[l * 7 + c];
+            Hu.m[c][jj] += gf[jj] * Ue[l * 7 + 3 + c];
+          }
+      }
+      for (int i = 0; i < 9; ++i) {
+        FG[f * 18 + i] = G.m[i / 3][i % 3];
+        FG[f * 18 + 9 + i] = Hu.m[i / 3][i % 3];
+      }
+    }
+  const double s3[3] = {vol / (h[0] * h[0]), vol / (h[1] * h[1]), vol / (h[2] * h[2])};
+  for (int cj = 0; cj < 7; ++cj) {
+    if (cta.tid < 7) flag[cta.tid] = 0.0;
+    for (int e = cta.tid; e < 27 * 4; e += cta.nt) {
+      const int q = e / 4, b = e % 4;
+      double dv[3] = {0, 0, 0}, du[3] = {0, 0, 0}, dp = 0.0;
+      M3 dG{}, dH{};
+      if (cj < 3) {
+        if (b == 0) dv[cj] = 1.0;
+        else dG.m[cj][b - 1] = 1.0;
+      } else if (cj < 6) {
+        if (b == 0) du[cj - 3] = 1.0;
+        else dH.m[cj - 3][b - 1] = 1.0;
+      } else if (b == 0) {
+        dp = 1.0;
+      }
+      double o[28];
+      qp_flux3_lin(P, X[q], solid, k, theta, dv, dG, du, dH, dp, o);
+      for (int r = 0; r < 28; ++r) Dc[(q * 28 + r) * 4 + b] = o[r];
+    }
+    if (face && cj < 6)
+      for (int e = cta.tid; e < 27; e += cta.nt) {
+        const int f = e / 3, b = e % 3;
+        M3 G, Hu, dG{}, dH{};
+        for (int i = 0; i < 9; ++i) {
+          G.m[i / 3][i % 3] = FG[f * 18 + i];
+          Hu.m[i / 3][i % 3] = FG[f * 18 + 9 + i];
+        }
+        if (cj < 3) dG.m[cj][b] = 1.0;
+        else dH.m[cj - 3][b] = 1.0;
+        double o[3];
+        face_flux3_lin(P, G, Hu, dG, dH, k, theta, o);
+        for (int c = 0; c < 3; ++c) FO[(f * 3 + c) * 3 + b] = o[c];
+      }
+    cta.sync();
+    for (int e = cta.tid; e < 27 * 28 * 4; e += cta.nt)
+      if (cj3_nonzero(Dc[e])) flag[((e / 4) % 28) / 4] = 1.0;
+    cta.sync();
+    for (int ci = 0; ci < 7; ++ci) {
+      const bool lps = !solid && ci == 6 && cj == 6, fc = face && ci < 3 && cj < 6;
+      if (flag[ci] == 0.0 && !lps && !fc) {
+        for (int e = cta.tid; e < 729; e += cta.nt)
+          Ke[((e / 27) * 7 + ci) * 189 + (e % 27) * 7 + cj] = 0.0;
+        continue;
+      }
+      for (int e = cta.tid; e < 27 * 4 * 27; e += cta.nt) {
+        const int q = e / 108, a = (e / 27) % 4, m = e % 27;
+        double ev = 0.0;
+        for (int b = 0; b < 4; ++b) ev += Dc[(q * 28 + ci * 4 + a) * 4 + b] * B[(q * 4 + b) * 27 + m];
+        E[e] = Wq[q] * ev;
+      }
+      cta.sync();
+      for (int e = cta.tid; e < 729; e += cta.nt) {
+        const int l = e / 27, m = e % 27;
+        double kv = 0.0;
+        for (int q = 0; q < 27; ++q) {
+          double acc = 0.0;
+          for (int a = 0; a < 4; ++a) acc += B[(q * 4 + a) * 27 + l] * E[(q * 4 + a) * 27 + m];
+          kv += acc;
+        }
+        if (lps) kv += k * alpha * (s3[0] * T.lps[0][l][m] + s3[1] * T.lps[1][l][m] + s3[2] * T.lps[2][l][m]);
+        if (fc)
+          for (int f = 0; f < 9; ++f) {
+            const double W = T.wf[f] * h[1] * h[2];
+            for (int b = 0; b < 3; ++b) kv += W * T.phi_f[f][l] * FO[(f * 3 + ci) * 3 + b] * (T.dphi_f[b][f][m] / h[b]);
+          }
+        Ke[(l * 7 + ci) * 189 + m * 7 + cj] = kv;
+      }
+      cta.sync();
+    }
+    cta.sync();
   }
 }
 

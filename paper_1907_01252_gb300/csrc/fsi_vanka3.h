@@ -13,9 +13,8 @@
 // 81 x 81 in FP64 fit one CTA). The corrections of the cells are averaged per
 // node and damped by omega, as in the 2D smoother.
 //
-// The per-cell routines are written once for a cooperative thread group: a
-// CUDA block (DevCta) or one host thread (HostCta) running the same phases in
-// the same order, so host checks execute the kernels' arithmetic.
+// The per-cell routines are written once for a cooperative thread group
+// (fsi_cta.h), so host checks execute the kernels' arithmetic.
 //
 // Stored inverse of a cell: VK3_SIZE elements (= 189^2), all column-major:
 //   [VK3_O_A] A11^{-1}            108 x 108
@@ -26,6 +25,7 @@
 
 #include <cmath>
 
+#include "fsi_cta.h"
 #include "fsi_mesh3d.h"
 
 namespace fsi3 {
@@ -68,17 +68,6 @@ FSI3M_HD inline T vk3_entry(const Mesh3View& m, const T* A, int cell, int a, int
   const int blk = m.cell_blk[(size_t)cell * 729 + (a / 7) * 27 + b / 7];
   return A[(size_t)blk * 49 + (a % 7) * 7 + b % 7];
 }
-
-struct HostCta {
-  int tid = 0, nt = 1;
-  FSI3M_HD void sync() const {}
-};
-#ifdef __CUDACC__
-struct DevCta {
-  int tid, nt;
-  __device__ void sync() const { __syncthreads(); }
-};
-#endif
 
 // Row of the largest |M[r][kk]|, r in [kk, n), the lowest such row on ties;
 // -1 if that maximum is not positive. Written to *piv by thread 0 (a warp

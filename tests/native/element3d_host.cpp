@@ -1,5 +1,8 @@
 // Host build of the 3D element physics of the CUDA library (the same header the
 // kernels compile), so tests can compare it with the FP64 oracle on the CPU.
+#include <algorithm>
+#include <vector>
+
 #include "../../paper_1907_01252_gb300/csrc/fsi_element3d.cuh"
 
 extern "C" int fsi3_cell_residual_host(const double* phys, const double* Ue, const double* Uo, const double* h,
@@ -25,6 +28,25 @@ extern "C" int fsi3_cell_jacobian_host(const double* phys, const double* Ue, con
   }
   const fsi3::Phys3 P{phys[0], phys[1], phys[2], phys[3], phys[4]};
   fsi3::cell_jacobian3(P, T, Ue, Uo, h, solid != 0, outflow != 0, k, theta, alpha, Ke);
+  return 0;
+}
+
+// The same element matrix by the cooperative routine the kernel runs (one host thread).
+extern "C" int fsi3_cell_jacobian_cta_host(const double* phys, const double* Ue, const double* Uo, const double* h,
+                                           int solid, int outflow, double k, double theta, double alpha,
+                                           double* Ke) {
+  static fsi3::Tables3 T;
+  static bool ready = false;
+  if (!ready) {
+    fsi3::build_tables3(T);
+    ready = true;
+  }
+  const fsi3::Phys3 P{phys[0], phys[1], phys[2], phys[3], phys[4]};
+  std::vector<double> sh(fsi3::CJ3_TOTAL, -1.0);   // stale values must not matter
+  std::copy(Ue, Ue + 189, sh.begin() + fsi3::CJ3_UE);
+  std::copy(Uo, Uo + 189, sh.begin() + fsi3::CJ3_UE + 189);
+  for (int i = 0; i < 189 * 189; ++i) Ke[i] = -7.0;   // every entry must be written
+  fsi3::cell_jacobian3_cta(fsi3::HostCta{}, P, T, h, solid != 0, outflow != 0, k, theta, alpha, sh.data(), Ke);
   return 0;
 }
 

@@ -448,3 +448,32 @@ def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, s
     scale = np.abs(ref).max(axis=0)
     err = np.abs(U - ref).max(axis=0) / scale
     assert np.all(err <= 1e-9), err
+
+
+@pytest.mark.parametrize("seed,k,theta", [(1, 0.02, 0.52), (2, 1 / 16, 1.0)])
+def test_cooperative_cell_jacobian_is_bitwise_the_serial_one(host_lib, seed, k, theta):
+    """The element matrix routine of the kernel (work spread over a thread group, run
+    here as one host thread) performs the serial routine's arithmetic in the same
+    order: identical bits on fluid, solid and outflow cells, every entry written."""
+    P = C.POINTER(C.c_double)
+    for name in ("fsi3_cell_jacobian_host", "fsi3_cell_jacobian_cta_host"):
+        getattr(host_lib, name).argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P]
+    mesh = on.make_mesh_nd([(0.0, 0.4, 0.45, 0.9), (0.0, 0.2, 0.41), (0.0, 0.055, 0.355, 0.41)],
+                           [[2, 1, 2], [1, 1], [1, 1, 1]], ((0.4, 0.45), (0.0, 0.2), (0.055, 0.355)))
+    mat = wl.Material()
+    U, Uo = state(mesh, seed), state(mesh, seed + 30)
+    phys = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s])
+    outflow = np.zeros(mesh.n_cells, dtype=bool)
+    outflow[mesh.outflow_cells] = True
+    h = np.array([0.2, 0.2, 0.055])
+    kinds = set()
+    for c in range(mesh.n_cells):
+        Ue = np.ascontiguousarray(U[mesh.cell_nodes[c]])
+        Uoe = np.ascontiguousarray(Uo[mesh.cell_nodes[c]])
+        args = (ptr(phys), ptr(Ue), ptr(Uoe), ptr(h), int(mesh.cell_solid[c]), int(outflow[c]), k, theta, 3e-4)
+        K1, K2 = np.zeros(189 * 189), np.zeros(189 * 189)
+        host_lib.fsi3_cell_jacobian_host(*args, ptr(K1))
+        host_lib.fsi3_cell_jacobian_cta_host(*args, ptr(K2))
+        assert np.array_equal(K1, K2), c
+        kinds.add((bool(mesh.cell_solid[c]), bool(outflow[c])))
+    assert kinds == {(False, False), (True, False), (False, True)}
