@@ -135,3 +135,26 @@ def test_3d_parareal_with_n_iterations_is_the_fine_solution():
         for name, sl in FIELDS.items():
             den = max(np.abs(ref[:, sl]).max(), 1e-300)
             assert np.abs(got[:, sl] - ref[:, sl]).max() <= 1e-12 * den, (i, name)
+
+
+def test_3d_parareal_iterate_matches_oracle():
+    """One Parareal iteration (predictor sweep with C, batched fine solves, corrected
+    sweep F + (C_new - C_old)) equals the oracle's iterate at every slice boundary."""
+    from oracle import parareal as opr
+    w = wl.Workload3D("tiny3d_pr", nx=5, ny=2, nz=3, T=0.06, n_slices=3, m_fine=1)
+    mesh = oracle_mesh(w)
+    model = on.FSIModelND(mesh, w.material, newton_tol=1e-12)
+    dt = w.T / w.n_slices
+    coarse = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_coarse, theta=1.0)  # noqa: E731
+    fine = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine)  # noqa: E731
+    U0 = np.zeros((mesh.n_nodes, 7))
+    ref = opr.parareal(U0, w.n_slices, coarse, fine, 1)[1]
+    ctx = ctx_for(w, w.n_slices)
+    U = torch.zeros((w.n_slices + 1, ctx.n_dofs), dtype=torch.float64, device=DEV)
+    U, st = ctx.fsi3_parareal(U, 1, 0.0)
+    assert st["iterations"] == 1
+    for i in range(1, w.n_slices + 1):
+        got = U[i].cpu().numpy().reshape(-1, 7)
+        for name, sl in FIELDS.items():
+            den = max(np.abs(ref[i][:, sl]).max(), 1e-300)
+            assert np.abs(got[:, sl] - ref[i][:, sl]).max() <= 1e-9 * den, (i, name)
