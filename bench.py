@@ -24,6 +24,10 @@ Parareal iteration each, run concurrently by the library's worker threads with
 the worker count chosen by the library's autotuner (its timed candidate runs
 are the warm-up). value = fine time-steps of all problems per second.
 
+--unit parareal3d measures the 3D path (hexahedral Q2, 7 unknowns per node) on the
+32 x 8 x 8 channel with the plate (131,495 dofs, T = 1, 32 slices x 16 fine steps): one
+fsi3_parareal iteration per step, FP32 multigrid inside FP64 FGMRES and Newton.
+
 N > 1 runs N independent replicas (one per GPU, one rank each): the path
 does not shard, so there is no collective on the data path.
 """
@@ -57,7 +61,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step", "batch"])
+    ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step", "batch",
+                                                           "parareal3d"])
     ap.add_argument("--instances", type=int, default=4,
                     help="--unit batch: the first K problems of the seeded 48-problem uneven batch")
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
@@ -224,6 +229,46 @@ def bench_batch(args, torch, fsi, wl, dev):
     print(json.dumps(line))
 
 
+def bench_3d(args, torch, fsi, wl, dev):
+    """One line for the 3D path (see the module docstring): one Parareal iteration of the
+    32 x 8 x 8 channel workload per step, all 32 slices' fine solves batched."""
+    w = wl.CHANNEL3D_32x8x8
+    N = w.n_slices
+    ctx = fsi.Context3D(w, max_batch=N)
+    U = torch.zeros((N + 1, ctx.n_dofs), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        U[1:].zero_()
+        return ctx.fsi3_parareal(U, 1, 0.0)[1]
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    value = N * w.m_fine * args.steps / (ms / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (FP32 multigrid)", "data": "synthetic",
+            "config": {"workload": w.name, "unit": "parareal3d", "n_dofs": ctx.n_dofs, "n_slices": N,
+                       "m_fine": w.m_fine, "levels": ctx.n_levels, "nnzb": ctx.nnzb,
+                       "step": "fsi3_parareal with 1 iteration from rest",
+                       "fine_newton": st["fine"]["newton_iters"], "fine_gmres": st["fine"]["gmres_iters"],
+                       "coarse_newton": st["coarse"]["newton_iters"], "coarse_gmres": st["coarse"]["gmres_iters"],
+                       "l2": "inputs larger than L2 (Jacobian blocks 426 MB per slice)"},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -243,6 +288,8 @@ def main():
     build.build_library()
     if args.unit == "batch":
         return bench_batch(args, torch, fsi, wl, dev)
+    if args.unit == "parareal3d":
+        return bench_3d(args, torch, fsi, wl, dev)
     w = wl.LARGE_128x32
     N = w.n_slices
     fine_unit = args.unit in ("fine_step", "coarse_step")
