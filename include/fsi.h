@@ -125,6 +125,9 @@ typedef struct fsi_params {
                               the fine solves run in batches of pipeline_chunk slices
                               as soon as their inputs exist). Results are identical */
   int max_batch;           /* most slices advanced in one call */
+  int mg_coarse_sweeps;    /* 3D path only: 0 solves the coarsest level with its dense
+                              inverse; > 0 applies that many smoother sweeps there
+                              instead (no inverse to build for each coarse step) */
 } fsi_params;
 
 /* Iteration statistics of one call (filled when the pointer is non-NULL). */
@@ -313,7 +316,7 @@ int fsi3d_mesh_size(const fsi_mesh3d* mesh, int* n_nodes, int* n_dofs, int* nnzb
  * over interface-fitted coarsenings. The V-cycle uses block Vanka local solves:
  * velocity-pressure block and displacement Schur complement, in FP64 or
  * (precision 2) FP32, and a dense inverse on the coarsest level (at most 4096
- * dofs). Parameters as fsi_params, with these limits: precision 0 or 2;
+ * dofs) or, with mg_coarse_sweeps > 0, that many smoother sweeps there. Parameters as fsi_params, with these limits: precision 0 or 2;
  * gmres_restart <= 63; the mesh must coarsen at least once; mg_smoother 1
  * sweeps eight cell colours; graph_max_batch and pipeline_chunk are ignored.
  * Device arrays are [S][n_dofs] (node-major, 7 per node); Jacobian blocks are

@@ -458,6 +458,7 @@ struct fsi3_level {
   std::vector<void*> owned;
   size_t n = 0;
   bool coarsest = false;
+  bool dense = false;                // coarsest level solved with its dense inverse
   std::vector<int> colour_cells[8];  // cells per colour (multiplicative smoother)
   const int* colour_dev[8] = {};
   // workspace (T = the multigrid precision; double when FP64)
@@ -570,7 +571,7 @@ int setup_level3(fsi3_level& L, int S, bool mg32, bool need_state) {
   TRY3(A(&L.r, (size_t)S * L.n * ts));
   TRY3(A(&L.b, (size_t)S * L.n * ts));
   TRY3(A(&L.x, (size_t)S * L.n * ts));
-  if (L.coarsest) {
+  if (L.dense) {
     const size_t nn = L.n * L.n;
     TRY3(dal3(L.owned, &L.D, (size_t)S * nn));
     TRY3(dal3(L.owned, &L.Dinv64, (size_t)S * nn));
@@ -666,7 +667,7 @@ int mg_setup3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
       k3_assemble<T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, c->Ke, act, A);
       TRY3(launched3());
     }
-    if (L.coarsest) {
+    if (L.dense) {
       const size_t nn = L.n * L.n;
       CK3(cudaMemsetAsync(L.D, 0, (size_t)S * nn * sizeof(double), st));
       k3_dense_from_bsr<T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, A, act, L.D);
@@ -728,6 +729,12 @@ template <typename T>
 int vcycle3(fsi3_ctx* c, size_t l, int S, const T* b, const uint8_t* act, cudaStream_t st) {
   fsi3_level& L = c->lev[l];
   T* x = reinterpret_cast<T*>(L.x);
+  if (L.coarsest && !L.dense) {   // smoother sweeps in place of the coarsest solve
+    k3_fill<T><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>((int)L.n, T(0), act, x, L.n);
+    TRY3(launched3());
+    for (int i = 0; i < c->prm.mg_coarse_sweeps; ++i) TRY3(smooth3<T>(c, L, S, b, i == 0, act, st));
+    return FSI_OK;
+  }
   if (L.coarsest) {
     k3_dense_apply<T><<<dim3(nb3(L.n * 32, 256), S), 256, 0, st>>>((int)L.n, reinterpret_cast<const T*>(L.Dinv), b,
                                                                     L.n, act, x);
@@ -1087,6 +1094,7 @@ int fsi3_setup(const fsi_mesh3d* mesh, const fsi_params* p, fsi3_ctx** out) {
     return fail3(FSI_EINVAL, "invalid solver parameters (3D: gmres_restart <= 63)");
   if (p->precision == 1) return fail3(FSI_EINVAL, "the 3D path supports precision 0 and 2");
   if (p->mg_smoother != 0 && p->mg_smoother != 1) return fail3(FSI_EINVAL, "mg_smoother must be 0 or 1");
+  if (p->mg_coarse_sweeps < 0 || p->mg_coarse_sweeps > 1000) return fail3(FSI_EINVAL, "mg_coarse_sweeps outside 0..1000");
   fsi3_ctx* c = new fsi3_ctx;
   auto cleanup = [&](int rc) {
     fsi3_destroy(c);
@@ -1120,9 +1128,10 @@ int fsi3_setup(const fsi_mesh3d* mesh, const fsi_params* p, fsi3_ctx** out) {
     c->lev.push_back(std::move(C));
   }
   if (c->lev.size() < 2) return cleanup(fail3(FSI_EINVAL, "the mesh needs at least one coarser level"));
-  if ((size_t)c->lev.back().h.n_nodes * 7 > 4096)
-    return cleanup(fail3(FSI_EINVAL, "coarsest level above 4096 dofs"));
   c->lev.back().coarsest = true;
+  c->lev.back().dense = p->mg_coarse_sweeps == 0;
+  if (c->lev.back().dense && (size_t)c->lev.back().h.n_nodes * 7 > 4096)
+    return cleanup(fail3(FSI_EINVAL, "coarsest level above 4096 dofs"));
   int rc = setup_tables3();
   if (rc) return cleanup(rc);
   for (size_t l = 0; l < c->lev.size(); ++l) {

@@ -38,7 +38,7 @@ class fsi_params(C.Structure):
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
                 ("graph_max_batch", C.c_int), ("precision", C.c_int), ("pipeline_chunk", C.c_int),
-                ("max_batch", C.c_int)]
+                ("max_batch", C.c_int), ("mg_coarse_sweeps", C.c_int)]
 
 
 class fsi_stats(C.Structure):
@@ -218,7 +218,8 @@ def _params(w: wl.Workload, max_batch: int, overrides):
              gmres_restart=w.gmres_restart, gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol,
              gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
              mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.5, mg_reuse=2,
-             mg_rebuild_every=4, graph_max_batch=4, precision=0, pipeline_chunk=0, max_batch=max_batch)
+             mg_rebuild_every=4, graph_max_batch=4, precision=0, pipeline_chunk=0, max_batch=max_batch,
+             mg_coarse_sweeps=0)
     p.update(overrides)
     return p
 
@@ -423,7 +424,10 @@ class Context3D:
                            newton_tol=w.newton_tol, newton_maxit=w.newton_maxit, gmres_restart=w.gmres_restart,
                            gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol, gmres_rtol_first=w.gmres_rtol_first,
                            newton_eta=w.newton_eta, material=w.material)
-        p = _params(base, max_batch, dict(dict(mg_coarsest_max_dofs=2000, precision=2, graph_max_batch=0),
+        # 3D defaults: FP32 multigrid, the coloured multiplicative Vanka sweep, and smoother sweeps on the
+        # coarsest level instead of its dense inverse
+        p = _params(base, max_batch, dict(dict(mg_coarsest_max_dofs=2000, precision=2, graph_max_batch=0,
+                                               mg_smoother=1, mg_omega=1.0, mg_smooth=1, mg_coarse_sweeps=8),
                                           **overrides))
         self.params = p
         self._params = fsi_params(**p)

@@ -25,6 +25,7 @@ struct Params {
   int coarsest_max_dofs, smooth;
   double omega, coarse_lps;
   int smoother;   // 0 additive (node averages), 1 multiplicative over the 8 cell colours
+  int coarse_sweeps;   // 0: dense LU on the coarsest level; > 0: that many smoother sweeps there
 };
 
 fsi3::Mesh3View make_view(const fsi3::HostMesh3& m) {
@@ -218,7 +219,7 @@ struct Solver {
       jacobian(L.h, mat, L.U.data(), L.Uo.data(), k, theta, lps, A);
       if (l == 0) A64 = A;
       L.A.assign(A.begin(), A.end());
-      if (L.coarsest) {
+      if (L.coarsest && prm.coarse_sweeps == 0) {
         std::vector<double> At(L.A.begin(), L.A.end());   // the factors of the preconditioner's operator
         if (!dense_lu(L.h, At, L.LU, L.piv)) return -1;
       } else {
@@ -278,6 +279,11 @@ struct Solver {
   // L.x = V-cycle applied to b (b may alias L.b).
   void vcycle(size_t l, const TM* b) {
     Level<TM>& L = lev[l];
+    if (L.coarsest && prm.coarse_sweeps > 0) {
+      std::fill(L.x.begin(), L.x.end(), TM(0));
+      for (int i = 0; i < prm.coarse_sweeps; ++i) smooth(L, b, i == 0);
+      return;
+    }
     if (L.coarsest) {
       std::vector<double> t(b, b + L.n);
       lu_solve(L.LU, L.piv, t);
@@ -429,7 +435,7 @@ int theta_step(const double* const* br, const int* const* seg, const int* nseg, 
 // One theta step t_new - k -> t_new of the 3D problem, solved as above. mat =
 // {rho_f, nu_f, rho_s, mu_s, lambda_s, vbar, ramp_t, alpha0}; prm = {newton_tol,
 // newton_maxit, gmres_restart, gmres_maxit, gmres_rtol, gmres_rtol_first,
-// newton_eta, mg_coarsest_max_dofs, mg_smooth, mg_omega, mg_coarse_lps, mg_smoother};
+// newton_eta, mg_coarsest_max_dofs, mg_smooth, mg_omega, mg_coarse_lps, mg_smoother, mg_coarse_sweeps};
 // precision 0: FP64 multigrid, 1: FP32 multigrid (FGMRES in FP64 either way).
 // stats = {Newton iterations, FGMRES iterations, levels, coarsest dofs}.
 // Returns 0, or -1/-2 singular coarsest/Vanka block, -3 FGMRES limit,
@@ -439,7 +445,8 @@ extern "C" int fsi3_theta_step_host(const double* xb, const int* nxs, int nxseg,
                                     const double* mat, const double* prm_in, int precision, const double* Uold,
                                     double t_new, double k, double theta, double* Unew, int* stats) {
   const Params prm{prm_in[0], (int)prm_in[1], (int)prm_in[2], (int)prm_in[3], prm_in[4], prm_in[5],
-                   prm_in[6], (int)prm_in[7], (int)prm_in[8], prm_in[9], prm_in[10], (int)prm_in[11]};
+                   prm_in[6], (int)prm_in[7], (int)prm_in[8], prm_in[9], prm_in[10], (int)prm_in[11],
+                   (int)prm_in[12]};
   const double* br[3] = {xb, yb, zb};
   const int* seg[3] = {nxs, nys, nzs};
   const int nseg[3] = {nxseg, nyseg, nzseg};

@@ -422,12 +422,13 @@ def oracle_step_3d():
     return mesh, mat, Uo, model.step(Uo, 0.5, 0.02, 0.52)
 
 
-@pytest.mark.parametrize("precision,smoother", [(0, 0), (1, 1)])
-def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, smoother):
+@pytest.mark.parametrize("precision,smoother,coarse_sweeps", [(0, 0, 0), (1, 1, 0), (1, 1, 8)])
+def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, smoother, coarse_sweeps):
     """One theta step solved the library's way (inexact Newton, FGMRES(50) + V-cycle with
     the block Vanka smoother over 2695 -> 1715 dofs, dense coarsest) equals the oracle's
     Newton step to 1e-9 per field; FP32 multigrid inside FP64 FGMRES reaches the same
-    root. smoother 1 is the coloured multiplicative sweep."""
+    root. smoother 1 is the coloured multiplicative sweep; coarse_sweeps > 0 replaces the
+    coarsest solve by that many sweeps."""
     mesh, mat, Uo, ref = oracle_step_3d
     P = C.POINTER(C.c_double)
     host_lib.fsi3_theta_step_host.argtypes = [P, C.c_void_p, C.c_int] * 3 + [P, P, P, C.c_int, P, C.c_double,
@@ -435,8 +436,9 @@ def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, s
     args, keep = mesh_args()
     m = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s, mat.vbar, mat.ramp_t, mat.alpha0])
     #              newton_tol maxit restart gmres_maxit rtol rtol_first eta coarsest smooth omega lps smoother
+    #              coarse_sweeps
     prm = np.array([1e-10, 20, 50, 2000, 1e-12, 1e-6, 1e-3, 2000, 2 - smoother, 0.6 + 0.4 * smoother, 0.5,
-                    smoother], dtype=float)
+                    smoother, coarse_sweeps], dtype=float)
     U = np.zeros_like(Uo)
     stats = np.zeros(4, dtype=np.int32)
     rc = host_lib.fsi3_theta_step_host(*args, ptr(m), ptr(prm), precision, ptr(Uo), 0.52, 0.02, 0.52, ptr(U),
@@ -444,7 +446,9 @@ def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, s
     assert rc == 0
     n_newton, n_krylov, levels, coarsest = stats
     assert levels == 2 and coarsest == 1715 and 3 <= n_newton <= 8
-    assert n_krylov <= 120 * n_newton
+    # with sweeps in place of the coarsest solve the two-level toy hierarchy converges ~2.5x slower
+    # (on three levels the two are alike); the bound only catches a broken preconditioner
+    assert n_krylov <= (120 if coarse_sweeps == 0 else 300) * n_newton, n_krylov
     scale = np.abs(ref).max(axis=0)
     err = np.abs(U - ref).max(axis=0) / scale
     assert np.all(err <= 1e-9), err

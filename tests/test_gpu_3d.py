@@ -103,10 +103,10 @@ def oracle_step():
     return mesh, Uo, model.step(Uo, 0.5, 0.02, 0.52)
 
 
-@pytest.mark.parametrize("precision,smoother", [(0, 0), (2, 0), (2, 1)])
-def test_3d_theta_step_matches_oracle(oracle_step, precision, smoother):
+@pytest.mark.parametrize("precision,smoother,coarse_sweeps", [(0, 0, 0), (2, 0, 0), (2, 1, 0), (2, 1, 8)])
+def test_3d_theta_step_matches_oracle(oracle_step, precision, smoother, coarse_sweeps):
     mesh, Uo, ref = oracle_step
-    ctx = ctx_for(TINY, 2, precision=precision, mg_smoother=smoother,
+    ctx = ctx_for(TINY, 2, precision=precision, mg_smoother=smoother, mg_coarse_sweeps=coarse_sweeps,
                   mg_omega=1.0 if smoother else 0.6, mg_smooth=1 if smoother else 2)
     U0 = dev(np.stack([Uo, Uo]))
     U1, st = ctx.fsi3_theta_step(U0, [0.5, 0.5], 0.02, 0.52)
