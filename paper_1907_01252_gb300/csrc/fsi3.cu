@@ -188,6 +188,27 @@ __global__ void k3_spmv(Dev3 d, const T* __restrict__ A, const T* __restrict__ x
   y[s * ystride + e] = RESID ? bvec[s * ystride + e] - acc : acc;
 }
 
+// r = b - A x on the listed rows only (the nodes of one colour's cells; other rows untouched).
+template <typename T>
+__global__ void k3_resid_rows(Dev3 d, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ bvec,
+                              size_t stride, const int* __restrict__ nodes, int nnodes,
+                              const uint8_t* __restrict__ active, T* __restrict__ y) {
+  const int s = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || e >= nnodes * 7) return;
+  const int node = nodes[e / 7], r = e % 7;
+  const T* As = A + (size_t)s * d.nnzb * 49;
+  const T* xs = x + s * stride;
+  T acc = 0;
+  for (int b = d.rowptr[node]; b < d.rowptr[node + 1]; ++b) {
+    const T* blk = As + (size_t)b * 49 + r * 7;
+    const T* xj = xs + (size_t)d.v.colidx[b] * 7;
+    for (int c = 0; c < 7; ++c) acc += blk[c] * xj[c];
+  }
+  const size_t o = s * stride + (size_t)node * 7 + r;
+  y[o] = bvec[o] - acc;
+}
+
 // y = a x + b y (types may differ: precision conversions of the preconditioner)
 template <typename TI, typename TO>
 __global__ void k3_axpby(int n, double a, const TI* __restrict__ x, size_t xs, double b,
@@ -460,7 +481,9 @@ struct fsi3_level {
   bool coarsest = false;
   bool dense = false;                // coarsest level solved with its dense inverse
   std::vector<int> colour_cells[8];  // cells per colour (multiplicative smoother)
+  std::vector<int> colour_nodes[8];  // the nodes of those cells, ascending
   const int* colour_dev[8] = {};
+  const int* colour_nodes_dev[8] = {};
   // workspace (T = the multigrid precision; double when FP64)
   void *A = nullptr, *inv = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *cz = nullptr, *Dinv = nullptr;
   double *U = nullptr, *Uo = nullptr, *D = nullptr, *Dinv64 = nullptr;
@@ -559,7 +582,15 @@ int setup_level3(fsi3_level& L, int S, bool mg32, bool need_state) {
     const int cx = c % h.nx, cy = (c / h.nx) % h.ny, cz = c / (h.nx * h.ny);
     L.colour_cells[(cx & 1) + 2 * (cy & 1) + 4 * (cz & 1)].push_back(c);
   }
-  for (int k = 0; k < 8; ++k) TRY3(up3(L.owned, &L.colour_dev[k], L.colour_cells[k]));
+  for (int k = 0; k < 8; ++k) {
+    std::vector<char> seen(h.n_nodes, 0);
+    for (int c : L.colour_cells[k])
+      for (int l = 0; l < 27; ++l) seen[h.cell_nodes[(size_t)c * 27 + l]] = 1;
+    for (int nd = 0; nd < h.n_nodes; ++nd)
+      if (seen[nd]) L.colour_nodes[k].push_back(nd);
+    TRY3(up3(L.owned, &L.colour_dev[k], L.colour_cells[k]));
+    TRY3(up3(L.owned, &L.colour_nodes_dev[k], L.colour_nodes[k]));
+  }
   const size_t ts = mg32 ? sizeof(float) : sizeof(double);
   auto A = [&](void** p, size_t bytes) -> int {
     unsigned char* q;
@@ -706,7 +737,9 @@ int smooth3(fsi3_ctx* c, fsi3_level& L, int S, const T* b, bool first, const uin
     for (int k = 0; k < 8; ++k) {
       const int nc = (int)L.colour_cells[k].size();
       if (nc == 0) continue;
-      k3_spmv<T, true><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.d, A, x, L.n, b, L.n, act, r);
+      const int nn = (int)L.colour_nodes[k].size();
+      k3_resid_rows<T><<<dim3(nb3((size_t)nn * 7, 256), S), 256, 0, st>>>(L.d, A, x, b, L.n, L.colour_nodes_dev[k],
+                                                                          nn, act, r);
       k3_vanka_apply<T><<<dim3(nc, S), 128, 0, st>>>(L.d, inv, r, L.n, act, L.colour_dev[k], nc, cz);
       k3_vanka_scatter<T><<<dim3(nb3((size_t)nc * 189, 256), S), 256, 0, st>>>(L.d, L.colour_dev[k], nc, cz, om, L.n,
                                                                                  act, x);
