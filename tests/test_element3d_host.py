@@ -481,3 +481,19 @@ def test_cooperative_cell_jacobian_is_bitwise_the_serial_one(host_lib, seed, k, 
         assert np.array_equal(K1, K2), c
         kinds.add((bool(mesh.cell_solid[c]), bool(outflow[c])))
     assert kinds == {(False, False), (True, False), (False, True)}
+
+
+def test_3d_cell_colours_share_no_node():
+    """The coloured sweep adds each colour's corrections without atomics: cells of one
+    colour (the parities of the three cell indices) must share no node, and the eight
+    colours must cover every cell once."""
+    counts = ((4, 1, 3), (2, 3), (2, 2, 1))
+    mesh = on.make_mesh_nd(BREAKS3, counts, BOX3)
+    nx, ny, nz = (sum(c) for c in counts)
+    cells = np.arange(mesh.n_cells)
+    cx, cy, cz = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    colour = (cx & 1) + 2 * (cy & 1) + 4 * (cz & 1)
+    assert np.all(np.bincount(colour, minlength=8) > 0)
+    for k in range(8):
+        nodes = mesh.cell_nodes[colour == k].ravel()
+        assert len(np.unique(nodes)) == len(nodes), k
