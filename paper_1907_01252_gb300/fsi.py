@@ -425,11 +425,11 @@ class Context3D:
                            gmres_maxit=w.gmres_maxit, gmres_rtol=w.gmres_rtol, gmres_rtol_first=w.gmres_rtol_first,
                            newton_eta=w.newton_eta, material=w.material)
         # 3D defaults: FP32 multigrid, the coloured multiplicative Vanka sweep, smoother sweeps on the
-        # coarsest level instead of its dense inverse, and a quarter of the stabilisation weight per
-        # coarser level (chosen by FGMRES counts of the host solver)
+        # coarsest level instead of its dense inverse, a quarter of the stabilisation weight per coarser
+        # level, and the hierarchy rebuilt at every Newton iterate (chosen by FGMRES counts of the host solver)
         p = _params(base, max_batch, dict(dict(mg_coarsest_max_dofs=2000, precision=2, graph_max_batch=0,
                                                mg_smoother=1, mg_omega=1.0, mg_smooth=1, mg_coarse_sweeps=8,
-                                               mg_coarse_lps=0.25),
+                                               mg_coarse_lps=0.25, mg_reuse=0),
                                           **overrides))
         self.params = p
         self._params = fsi_params(**p)

@@ -26,6 +26,7 @@ struct Params {
   double omega, coarse_lps;
   int smoother;   // 0 additive (node averages), 1 multiplicative over the 8 cell colours
   int coarse_sweeps;   // 0: dense LU on the coarsest level; > 0: that many smoother sweeps there
+  int reuse;           // 2: keep the hierarchy of the first Newton iterate; 0: rebuild it every iteration
 };
 
 fsi3::Mesh3View make_view(const fsi3::HostMesh3& m) {
@@ -405,8 +406,8 @@ int theta_step(const double* const* br, const int* const* seg, const int* nseg, 
       rtol = it == 0 ? std::max(prm.gmres_rtol, prm.gmres_rtol_first) : prm.gmres_rtol;
       if (it > 0) target = std::min(1e-2 * nr, prm.newton_eta * prm.newton_tol * std::max(r0, 1.0));
     }
-    if (it == 0) {
-      const int rc = S.setup(U.data(), Uold, k, theta);   // the hierarchy of the first iterate is kept
+    if (it == 0 || prm.reuse < 2) {
+      const int rc = S.setup(U.data(), Uold, k, theta);   // with reuse 2 the first iterate's hierarchy is kept
       if (rc) return rc;
     } else {
       std::vector<double> A;   // exact Jacobian for the Krylov operator
@@ -435,7 +436,8 @@ int theta_step(const double* const* br, const int* const* seg, const int* nseg, 
 // One theta step t_new - k -> t_new of the 3D problem, solved as above. mat =
 // {rho_f, nu_f, rho_s, mu_s, lambda_s, vbar, ramp_t, alpha0}; prm = {newton_tol,
 // newton_maxit, gmres_restart, gmres_maxit, gmres_rtol, gmres_rtol_first,
-// newton_eta, mg_coarsest_max_dofs, mg_smooth, mg_omega, mg_coarse_lps, mg_smoother, mg_coarse_sweeps};
+// newton_eta, mg_coarsest_max_dofs, mg_smooth, mg_omega, mg_coarse_lps, mg_smoother, mg_coarse_sweeps,
+// mg_reuse} (14 entries).
 // precision 0: FP64 multigrid, 1: FP32 multigrid (FGMRES in FP64 either way).
 // stats = {Newton iterations, FGMRES iterations, levels, coarsest dofs}.
 // Returns 0, or -1/-2 singular coarsest/Vanka block, -3 FGMRES limit,
@@ -446,7 +448,7 @@ extern "C" int fsi3_theta_step_host(const double* xb, const int* nxs, int nxseg,
                                     double t_new, double k, double theta, double* Unew, int* stats) {
   const Params prm{prm_in[0], (int)prm_in[1], (int)prm_in[2], (int)prm_in[3], prm_in[4], prm_in[5],
                    prm_in[6], (int)prm_in[7], (int)prm_in[8], prm_in[9], prm_in[10], (int)prm_in[11],
-                   (int)prm_in[12]};
+                   (int)prm_in[12], (int)prm_in[13]};
   const double* br[3] = {xb, yb, zb};
   const int* seg[3] = {nxs, nys, nzs};
   const int nseg[3] = {nxseg, nyseg, nzseg};

@@ -436,9 +436,9 @@ def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, s
     args, keep = mesh_args()
     m = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s, mat.vbar, mat.ramp_t, mat.alpha0])
     #              newton_tol maxit restart gmres_maxit rtol rtol_first eta coarsest smooth omega lps smoother
-    #              coarse_sweeps
+    #              coarse_sweeps reuse
     prm = np.array([1e-10, 20, 50, 2000, 1e-12, 1e-6, 1e-3, 2000, 2 - smoother, 0.6 + 0.4 * smoother, 0.5,
-                    smoother, coarse_sweeps], dtype=float)
+                    smoother, coarse_sweeps, 2], dtype=float)
     U = np.zeros_like(Uo)
     stats = np.zeros(4, dtype=np.int32)
     rc = host_lib.fsi3_theta_step_host(*args, ptr(m), ptr(prm), precision, ptr(Uo), 0.52, 0.02, 0.52, ptr(U),
