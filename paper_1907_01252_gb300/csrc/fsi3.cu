@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -534,19 +535,23 @@ void free_all(std::vector<void*>& own) {
   own.clear();
 }
 
+// The reference tables are the same for every context: one upload per device,
+// serialised across host threads.
+constexpr int kMaxDevices3 = 64;
+std::mutex g_tab3_mutex;
+bool g_tab3_done[kMaxDevices3] = {};
+
 int setup_tables3() {
-  static bool done = false;   // the tables are the same for every context; one upload per process and device
-  static int dev_done = -1;
   int dev = 0;
   CK3(cudaGetDevice(&dev));
-  if (done && dev == dev_done) return FSI_OK;
-  fsi3::Tables3* T = new fsi3::Tables3;
-  fsi3::build_tables3(*T);
-  const cudaError_t e = cudaMemcpyToSymbol(c_tab3, T, sizeof(fsi3::Tables3));
-  delete T;
+  if (dev < 0 || dev >= kMaxDevices3) return fail3(FSI_EINVAL, "device index beyond the supported range");
+  std::lock_guard<std::mutex> lock(g_tab3_mutex);
+  if (g_tab3_done[dev]) return FSI_OK;
+  std::vector<fsi3::Tables3> T(1);
+  fsi3::build_tables3(T[0]);
+  const cudaError_t e = cudaMemcpyToSymbol(c_tab3, T.data(), sizeof(fsi3::Tables3));
   if (e != cudaSuccess) return fail3(FSI_ECUDA, std::string("tables: ") + cudaGetErrorString(e));
-  done = true;
-  dev_done = dev;
+  g_tab3_done[dev] = true;
   return FSI_OK;
 }
 
