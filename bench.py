@@ -242,11 +242,20 @@ def bench_3d(args, torch, fsi, wl, dev):
         U[1:].zero_()
         return ctx.fsi3_parareal(U, 1, 0.0)[1]
 
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fsi.profile3(True)   # per-kernel CUDA-event times of the last warm-up step
         step()
+    torch.cuda.synchronize()
+    kernel_ms = {k: v for k, v in fsi.profile3_read().items() if v[1]}
+    fsi.profile3(False)
+    total = sum(v[0] for v in kernel_ms.values()) or 1.0
+    shares = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
+              for k, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1][0])}
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     torch.cuda.synchronize()
+    l0 = fsi.launch_count3()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -255,6 +264,7 @@ def bench_3d(args, torch, fsi, wl, dev):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    launches = fsi.launch_count3() - l0
     value = N * w.m_fine * args.steps / (ms / 1000.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -264,8 +274,9 @@ def bench_3d(args, torch, fsi, wl, dev):
                        "step": "fsi3_parareal with 1 iteration from rest",
                        "fine_newton": st["fine"]["newton_iters"], "fine_gmres": st["fine"]["gmres_iters"],
                        "coarse_newton": st["coarse"]["newton_iters"], "coarse_gmres": st["coarse"]["gmres_iters"],
-                       "l2": "inputs larger than L2 (Jacobian blocks 426 MB per slice)"},
-            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None}
+                       "l2": "inputs larger than L2 (Jacobian blocks 426 MB per slice)",
+                       "kernels_last_warmup": shares},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": launches}
     print(json.dumps(line))
 
 

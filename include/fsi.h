@@ -361,6 +361,18 @@ int fsi3_coarse(fsi3_ctx* ctx, int S, const double* U0, const double* t0, double
 int fsi3_parareal(fsi3_ctx* ctx, double* U, int max_iter, double tol,
                   fsi_parareal_stats* stats, void* stream);
 
+/* Launch accounting of the 3D kernels (process-wide, all threads): every launch
+ * is counted; fsi3_profile_enable(1) clears the recorded times and brackets each
+ * later launch with two CUDA events on its stream (0 stops recording).
+ * fsi3_profile_read waits for the recorded events of kernel id and returns their
+ * summed device time and count. fsi3_launch_count(-1) sums over all kernels.
+ * Errors: FSI_EINVAL (bad id or null output), FSI_ECUDA. */
+int fsi3_kernel_count(void);
+const char* fsi3_kernel_name(int kernel_id);
+long long fsi3_launch_count(int kernel_id);
+int fsi3_profile_enable(int on);
+int fsi3_profile_read(int kernel_id, double* total_ms, long long* timed_launches);
+
 /* ---- Batches of independent problems (beyond the paper, which solves one
  * problem at a time) ----------------------------------------------------
  * Many independent FSI problems of uneven meshes, materials and slice counts,

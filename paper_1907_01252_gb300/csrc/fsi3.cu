@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,6 +51,102 @@ int launched3() {
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FSI_OK : fail3(FSI_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
+
+// Launch accounting of the 3D kernels: every launch is counted; with profiling
+// on, each launch is bracketed by two CUDA events on its stream, read later
+// (no synchronisation on the launch path).
+enum Ki3 {
+  KI3_CELL_JACOBIAN,
+  KI3_CELL_RESIDUAL,
+  KI3_GATHER_RESIDUAL,
+  KI3_ASSEMBLE,
+  KI3_INTERP_STATE,
+  KI3_AXPBY,
+  KI3_DENSE_FROM_BSR,
+  KI3_IDENTITY_INACTIVE,
+  KI3_CONVERT,
+  KI3_VANKA_SETUP,
+  KI3_RESID_ROWS,
+  KI3_VANKA_APPLY,
+  KI3_VANKA_SCATTER,
+  KI3_SPMV,
+  KI3_VANKA_GATHER,
+  KI3_FILL,
+  KI3_DENSE_APPLY,
+  KI3_RESTRICT,
+  KI3_PROLONG_ADD,
+  KI3_DOTS_PARTIAL,
+  KI3_DOTS_FINISH,
+  KI3_SCALE,
+  KI3_SUB_BASIS,
+  KI3_ADD_BASIS,
+  KI3_APPLY_DIRICHLET,
+  KI3_PARAREAL_CORRECT,
+  KI3_COUNT
+};
+const char* const kKernelNames3[KI3_COUNT] = {
+    "k3_cell_jacobian",
+    "k3_cell_residual",
+    "k3_gather_residual",
+    "k3_assemble",
+    "k3_interp_state",
+    "k3_axpby",
+    "k3_dense_from_bsr",
+    "k3_identity_inactive",
+    "k3_convert",
+    "k3_vanka_setup",
+    "k3_resid_rows",
+    "k3_vanka_apply",
+    "k3_vanka_scatter",
+    "k3_spmv",
+    "k3_vanka_gather",
+    "k3_fill",
+    "k3_dense_apply",
+    "k3_restrict",
+    "k3_prolong_add",
+    "k3_dots_partial",
+    "k3_dots_finish",
+    "k3_scale",
+    "k3_sub_basis",
+    "k3_add_basis",
+    "k3_apply_dirichlet",
+    "k3_parareal_correct",
+};
+
+struct Prof3 {
+  std::mutex mu;
+  std::atomic<bool> on{false};
+  std::atomic<long long> launches[KI3_COUNT] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[KI3_COUNT];
+};
+Prof3 g_prof3;
+
+inline void prof3_pre(int id, cudaStream_t st, cudaEvent_t* a) {
+  g_prof3.launches[id].fetch_add(1, std::memory_order_relaxed);
+  *a = nullptr;
+  if (!g_prof3.on.load(std::memory_order_relaxed)) return;
+  if (cudaEventCreate(a) != cudaSuccess || cudaEventRecord(*a, st) != cudaSuccess) *a = nullptr;
+}
+
+inline void prof3_post(int id, cudaEvent_t a, cudaStream_t st) {
+  if (!a) return;
+  cudaEvent_t b = nullptr;
+  if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(b, st) != cudaSuccess) {
+    cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(g_prof3.mu);
+  g_prof3.ev[id].push_back({a, b});
+}
+
+#define P3(id, kern, grid, block, smem, st, ...)   \
+  do {                                              \
+    cudaEvent_t ev_;                                \
+    prof3_pre(id, st, &ev_);                        \
+    kern<<<grid, block, smem, st>>>(__VA_ARGS__);   \
+    prof3_post(id, ev_, st);                        \
+  } while (0)
 
 __constant__ fsi3::Tables3 c_tab3;
 
@@ -152,7 +249,7 @@ int launch_cell_jacobian(const Dev3& d, int n_cells, int S, const Phys3D& P, con
                          cudaStream_t st) {
   const int smem = fsi3::CJ3_TOTAL * (int)sizeof(double);
   CK3(cudaFuncSetAttribute(k3_cell_jacobian, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k3_cell_jacobian<<<dim3(n_cells, S), CJ3_THREADS, smem, st>>>(d, P, U, Uo, stride, k, theta, lps, act, Ke);
+  P3(KI3_CELL_JACOBIAN, (k3_cell_jacobian), (dim3(n_cells, S)), CJ3_THREADS, smem, st, d, P, U, Uo, stride, k, theta, lps, act, Ke);
   return launched3();
 }
 
@@ -660,9 +757,9 @@ int validate_mesh3(const fsi_mesh3d* m) {
 int residual3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, double theta, const uint8_t* act,
               double* R, cudaStream_t st) {
   const fsi3_level& L = c->lev[0];
-  k3_cell_residual<<<dim3(nb3(L.h.n_cells, 128), S), 128, 0, st>>>(L.d, c->P, U, Uo, L.n, k, theta, act, c->Re);
+  P3(KI3_CELL_RESIDUAL, (k3_cell_residual), (dim3(nb3(L.h.n_cells, 128), S)), 128, 0, st, L.d, c->P, U, Uo, L.n, k, theta, act, c->Re);
   TRY3(launched3());
-  k3_gather_residual<<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.d, c->P, c->Re, U, L.n, c->t_dev, act, R);
+  P3(KI3_GATHER_RESIDUAL, (k3_gather_residual), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.d, c->P, c->Re, U, L.n, c->t_dev, act, R);
   return launched3();
 }
 
@@ -670,7 +767,7 @@ int residual3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
 int jacobian3(fsi3_ctx* c, fsi3_level& L, int S, const double* U, const double* Uo, double k, double theta,
               double lps, const uint8_t* act, double* A, cudaStream_t st) {
   TRY3(launch_cell_jacobian(L.d, L.h.n_cells, S, c->P, U, Uo, L.n, k, theta, lps, act, c->Ke, st));
-  k3_assemble<double><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, c->Ke, act, A);
+  P3(KI3_ASSEMBLE, (k3_assemble<double>), (dim3(nb3((size_t)L.h.nnzb * 49, 256), S)), 256, 0, st, L.d, c->Ke, act, A);
   return launched3();
 }
 
@@ -685,8 +782,8 @@ int mg_setup3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
       const fsi3_level& F = c->lev[l - 1];
       const double* Uf = l == 1 ? U : F.U;
       const double* Uof = l == 1 ? Uo : F.Uo;
-      k3_interp_state<<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.tv, Uf, F.n, L.n, L.h.n_nodes, act, L.U);
-      k3_interp_state<<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.tv, Uof, F.n, L.n, L.h.n_nodes, act, L.Uo);
+      P3(KI3_INTERP_STATE, (k3_interp_state), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.tv, Uf, F.n, L.n, L.h.n_nodes, act, L.U);
+      P3(KI3_INTERP_STATE, (k3_interp_state), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.tv, Uof, F.n, L.n, L.h.n_nodes, act, L.Uo);
       TRY3(launched3());
       Ul = L.U;
       Uol = L.Uo;
@@ -695,30 +792,30 @@ int mg_setup3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, d
     T* A = reinterpret_cast<T*>(L.A);
     if (l == 0) {   // the Krylov operator, and its copy in T for the preconditioner
       TRY3(jacobian3(c, L, S, Ul, Uol, k, theta, 1.0, act, c->A64, st));
-      k3_axpby<double, T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(
+      P3(KI3_AXPBY, (k3_axpby<double, T>), (dim3(nb3((size_t)L.h.nnzb * 49, 256), S)), 256, 0, st, 
           L.h.nnzb * 49, 1.0, c->A64, (size_t)L.h.nnzb * 49, 0.0, act, A, (size_t)L.h.nnzb * 49);
       TRY3(launched3());
     } else {
       TRY3(launch_cell_jacobian(L.d, L.h.n_cells, S, c->P, Ul, Uol, L.n, k, theta, lps, act, c->Ke, st));
-      k3_assemble<T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, c->Ke, act, A);
+      P3(KI3_ASSEMBLE, (k3_assemble<T>), (dim3(nb3((size_t)L.h.nnzb * 49, 256), S)), 256, 0, st, L.d, c->Ke, act, A);
       TRY3(launched3());
     }
     if (L.dense) {
       const size_t nn = L.n * L.n;
       CK3(cudaMemsetAsync(L.D, 0, (size_t)S * nn * sizeof(double), st));
-      k3_dense_from_bsr<T><<<dim3(nb3((size_t)L.h.nnzb * 49, 256), S), 256, 0, st>>>(L.d, A, act, L.D);
-      k3_identity_inactive<<<dim3(nb3(L.n, 256), S), 256, 0, st>>>((int)L.n, act, L.D);
+      P3(KI3_DENSE_FROM_BSR, (k3_dense_from_bsr<T>), (dim3(nb3((size_t)L.h.nnzb * 49, 256), S)), 256, 0, st, L.d, A, act, L.D);
+      P3(KI3_IDENTITY_INACTIVE, (k3_identity_inactive), (dim3(nb3(L.n, 256), S)), 256, 0, st, (int)L.n, act, L.D);
       TRY3(launched3());
       const int rc = fsi_dense_invert(S, (int)L.n, L.D, L.Dinv64, 0, st);
       if (rc != FSI_OK) return rc;
       if (c->mg32) {
-        k3_convert<T><<<nb3((size_t)S * nn, 256), 256, 0, st>>>((size_t)S * nn, L.Dinv64, reinterpret_cast<T*>(L.Dinv));
+        P3(KI3_CONVERT, (k3_convert<T>), (nb3((size_t)S * nn, 256)), 256, 0, st, (size_t)S * nn, L.Dinv64, reinterpret_cast<T*>(L.Dinv));
         TRY3(launched3());
       }
     } else {
       const int smem = fsi3::vk3_setup_smem_bytes<T>();
       CK3(cudaFuncSetAttribute(k3_vanka_setup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      k3_vanka_setup<T><<<dim3(L.h.n_cells, S), 256, smem, st>>>(L.d, A, act, reinterpret_cast<T*>(L.inv),
+      P3(KI3_VANKA_SETUP, (k3_vanka_setup<T>), (dim3(L.h.n_cells, S)), 256, smem, st, L.d, A, act, reinterpret_cast<T*>(L.inv),
                                                                    c->status);
       TRY3(launched3());
     }
@@ -743,10 +840,10 @@ int smooth3(fsi3_ctx* c, fsi3_level& L, int S, const T* b, bool first, const uin
       const int nc = (int)L.colour_cells[k].size();
       if (nc == 0) continue;
       const int nn = (int)L.colour_nodes[k].size();
-      k3_resid_rows<T><<<dim3(nb3((size_t)nn * 7, 256), S), 256, 0, st>>>(L.d, A, x, b, L.n, L.colour_nodes_dev[k],
+      P3(KI3_RESID_ROWS, (k3_resid_rows<T>), (dim3(nb3((size_t)nn * 7, 256), S)), 256, 0, st, L.d, A, x, b, L.n, L.colour_nodes_dev[k],
                                                                           nn, act, r);
-      k3_vanka_apply<T><<<dim3(nc, S), 128, 0, st>>>(L.d, inv, r, L.n, act, L.colour_dev[k], nc, cz);
-      k3_vanka_scatter<T><<<dim3(nb3((size_t)nc * 189, 256), S), 256, 0, st>>>(L.d, L.colour_dev[k], nc, cz, om, L.n,
+      P3(KI3_VANKA_APPLY, (k3_vanka_apply<T>), (dim3(nc, S)), 128, 0, st, L.d, inv, r, L.n, act, L.colour_dev[k], nc, cz);
+      P3(KI3_VANKA_SCATTER, (k3_vanka_scatter<T>), (dim3(nb3((size_t)nc * 189, 256), S)), 256, 0, st, L.d, L.colour_dev[k], nc, cz, om, L.n,
                                                                                  act, x);
       TRY3(launched3());
     }
@@ -754,11 +851,11 @@ int smooth3(fsi3_ctx* c, fsi3_level& L, int S, const T* b, bool first, const uin
   }
   const T* rr = b;
   if (!first) {
-    k3_spmv<T, true><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.d, A, x, L.n, b, L.n, act, r);
+    P3(KI3_SPMV, (k3_spmv<T, true>), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.d, A, x, L.n, b, L.n, act, r);
     rr = r;
   }
-  k3_vanka_apply<T><<<dim3(L.h.n_cells, S), 128, 0, st>>>(L.d, inv, rr, L.n, act, nullptr, L.h.n_cells, cz);
-  k3_vanka_gather<T><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.d, cz, om, L.n, act, x);
+  P3(KI3_VANKA_APPLY, (k3_vanka_apply<T>), (dim3(L.h.n_cells, S)), 128, 0, st, L.d, inv, rr, L.n, act, nullptr, L.h.n_cells, cz);
+  P3(KI3_VANKA_GATHER, (k3_vanka_gather<T>), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.d, cz, om, L.n, act, x);
   return launched3();
 }
 
@@ -768,28 +865,28 @@ int vcycle3(fsi3_ctx* c, size_t l, int S, const T* b, const uint8_t* act, cudaSt
   fsi3_level& L = c->lev[l];
   T* x = reinterpret_cast<T*>(L.x);
   if (L.coarsest && !L.dense) {   // smoother sweeps in place of the coarsest solve
-    k3_fill<T><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>((int)L.n, T(0), act, x, L.n);
+    P3(KI3_FILL, (k3_fill<T>), (dim3(nb3(L.n, 256), S)), 256, 0, st, (int)L.n, T(0), act, x, L.n);
     TRY3(launched3());
     for (int i = 0; i < c->prm.mg_coarse_sweeps; ++i) TRY3(smooth3<T>(c, L, S, b, i == 0, act, st));
     return FSI_OK;
   }
   if (L.coarsest) {
-    k3_dense_apply<T><<<dim3(nb3(L.n * 32, 256), S), 256, 0, st>>>((int)L.n, reinterpret_cast<const T*>(L.Dinv), b,
+    P3(KI3_DENSE_APPLY, (k3_dense_apply<T>), (dim3(nb3(L.n * 32, 256), S)), 256, 0, st, (int)L.n, reinterpret_cast<const T*>(L.Dinv), b,
                                                                     L.n, act, x);
     return launched3();
   }
-  k3_fill<T><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>((int)L.n, T(0), act, x, L.n);
+  P3(KI3_FILL, (k3_fill<T>), (dim3(nb3(L.n, 256), S)), 256, 0, st, (int)L.n, T(0), act, x, L.n);
   TRY3(launched3());
   for (int i = 0; i < c->prm.mg_smooth; ++i) TRY3(smooth3<T>(c, L, S, b, i == 0, act, st));
   fsi3_level& C = c->lev[l + 1];
   T* r = reinterpret_cast<T*>(L.r);
-  k3_spmv<T, true><<<dim3(nb3(L.n, 256), S), 256, 0, st>>>(L.d, reinterpret_cast<const T*>(L.A), x, L.n, b, L.n,
+  P3(KI3_SPMV, (k3_spmv<T, true>), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.d, reinterpret_cast<const T*>(L.A), x, L.n, b, L.n,
                                                             act, r);
-  k3_restrict<T><<<dim3(nb3(C.n, 128), S), 128, 0, st>>>(C.tv, L.d.v.node_flags, C.d.v.node_flags, r, L.n, C.n,
+  P3(KI3_RESTRICT, (k3_restrict<T>), (dim3(nb3(C.n, 128), S)), 128, 0, st, C.tv, L.d.v.node_flags, C.d.v.node_flags, r, L.n, C.n,
                                                           C.h.n_nodes, act, reinterpret_cast<T*>(C.b));
   TRY3(launched3());
   TRY3(vcycle3<T>(c, l + 1, S, reinterpret_cast<const T*>(C.b), act, st));
-  k3_prolong_add<T><<<dim3(nb3(L.n, 128), S), 128, 0, st>>>(C.tv, L.d.v.node_flags, reinterpret_cast<const T*>(C.x),
+  P3(KI3_PROLONG_ADD, (k3_prolong_add<T>), (dim3(nb3(L.n, 128), S)), 128, 0, st, C.tv, L.d.v.node_flags, reinterpret_cast<const T*>(C.x),
                                                              L.n, C.n, L.h.n_nodes, act, x);
   TRY3(launched3());
   for (int i = 0; i < c->prm.mg_smooth; ++i) TRY3(smooth3<T>(c, L, S, b, false, act, st));
@@ -801,8 +898,8 @@ int dots3(fsi3_ctx* c, int S, int nv, const double* V, size_t vstride, size_t vs
           const uint8_t* act, std::vector<double>& h, cudaStream_t st) {
   const int n = (int)c->n;
   const unsigned nblk = nb3(n, R3_CHUNK);
-  k3_dots_partial<<<dim3(nblk, S), R3_THREADS, 0, st>>>(n, nv, V, vstride, vslice, w, c->n, act, c->partial);
-  k3_dots_finish<<<S, 64, 0, st>>>((int)nblk, nv, c->partial, act, c->dots);
+  P3(KI3_DOTS_PARTIAL, (k3_dots_partial), (dim3(nblk, S)), R3_THREADS, 0, st, n, nv, V, vstride, vslice, w, c->n, act, c->partial);
+  P3(KI3_DOTS_FINISH, (k3_dots_finish), (S), 64, 0, st, (int)nblk, nv, c->partial, act, c->dots);
   TRY3(launched3());
   h.assign((size_t)S * 64, 0.0);
   CK3(cudaMemcpyAsync(h.data(), c->dots, (size_t)S * 64 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -822,7 +919,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
   const size_t vsl = (size_t)(m + 1) * n, zsl = (size_t)m * n;
   const unsigned g = nb3(n, 256);
   CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-  k3_fill<double><<<dim3(g, S), 256, 0, st>>>((int)n, 0.0, c->active, x, n);
+  P3(KI3_FILL, (k3_fill<double>), (dim3(g, S)), 256, 0, st, (int)n, 0.0, c->active, x, n);
   TRY3(launched3());
   std::vector<double> hb;
   TRY3(dots3(c, S, 1, b, 0, n, b, c->active, hb, st));
@@ -846,7 +943,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
   while (any(act)) {
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     // r = b - A x into V[0]; beta
-    k3_spmv<double, true><<<dim3(g, S), 256, 0, st>>>(L.d, c->A64, x, n, b, n, c->active, c->w);
+    P3(KI3_SPMV, (k3_spmv<double, true>), (dim3(g, S)), 256, 0, st, L.d, c->A64, x, n, b, n, c->active, c->w);
     TRY3(launched3());
     TRY3(dots3(c, S, 1, c->w, 0, n, c->w, c->active, h1, st));
     std::vector<uint8_t> cyc = act;   // slices iterating in this cycle
@@ -875,29 +972,29 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
     if (!any(cyc)) break;
     CK3(cudaMemcpyAsync(c->active, cyc.data(), S, cudaMemcpyHostToDevice, st));
     CK3(cudaMemcpyAsync(c->scal, scal.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
-    k3_scale<<<dim3(g, S), 256, 0, st>>>((int)n, c->w, n, c->scal, c->active, c->V, vsl);
+    P3(KI3_SCALE, (k3_scale), (dim3(g, S)), 256, 0, st, (int)n, c->w, n, c->scal, c->active, c->V, vsl);
     TRY3(launched3());
     std::vector<uint8_t> run = cyc;   // slices still adding basis vectors in this cycle
     for (int j = 0; j < m && any(run); ++j) {
       CK3(cudaMemcpyAsync(c->active, run.data(), S, cudaMemcpyHostToDevice, st));
       // z_j = M^{-1} v_j (in T), w = A z_j
       T* xin = reinterpret_cast<T*>(L.b);
-      k3_axpby<double, T><<<dim3(g, S), 256, 0, st>>>((int)n, 1.0, c->V + (size_t)j * n, vsl, 0.0, c->active, xin, n);
+      P3(KI3_AXPBY, (k3_axpby<double, T>), (dim3(g, S)), 256, 0, st, (int)n, 1.0, c->V + (size_t)j * n, vsl, 0.0, c->active, xin, n);
       TRY3(launched3());
       TRY3(vcycle3<T>(c, 0, S, xin, c->active, st));
-      k3_axpby<T, double><<<dim3(g, S), 256, 0, st>>>((int)n, 1.0, reinterpret_cast<const T*>(L.x), n, 0.0, c->active,
+      P3(KI3_AXPBY, (k3_axpby<T, double>), (dim3(g, S)), 256, 0, st, (int)n, 1.0, reinterpret_cast<const T*>(L.x), n, 0.0, c->active,
                                                       c->Z + (size_t)j * n, zsl);
-      k3_spmv<double, false><<<dim3(g, S), 256, 0, st>>>(L.d, c->A64, c->Z + (size_t)j * n, zsl, nullptr, n,
+      P3(KI3_SPMV, (k3_spmv<double, false>), (dim3(g, S)), 256, 0, st, L.d, c->A64, c->Z + (size_t)j * n, zsl, nullptr, n,
                                                         c->active, c->w);
       TRY3(launched3());
       // classical Gram-Schmidt, twice
       TRY3(dots3(c, S, j + 1, c->V, n, vsl, c->w, c->active, h1, st));
       CK3(cudaMemcpyAsync(c->dots, h1.data(), (size_t)S * 64 * sizeof(double), cudaMemcpyHostToDevice, st));
-      k3_sub_basis<<<dim3(g, S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
+      P3(KI3_SUB_BASIS, (k3_sub_basis), (dim3(g, S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
       TRY3(launched3());
       TRY3(dots3(c, S, j + 1, c->V, n, vsl, c->w, c->active, h2, st));
       CK3(cudaMemcpyAsync(c->dots, h2.data(), (size_t)S * 64 * sizeof(double), cudaMemcpyHostToDevice, st));
-      k3_sub_basis<<<dim3(g, S), 256, 0, st>>>((int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
+      P3(KI3_SUB_BASIS, (k3_sub_basis), (dim3(g, S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
       TRY3(launched3());
       std::vector<double> hn;
       TRY3(dots3(c, S, 1, c->w, 0, n, c->w, c->active, hn, st));
@@ -933,7 +1030,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
         }
       }
       CK3(cudaMemcpyAsync(c->scal, scal.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
-      k3_scale<<<dim3(g, S), 256, 0, st>>>((int)n, c->w, n, c->scal, c->active, c->V + (size_t)(j + 1) * n, vsl);
+      P3(KI3_SCALE, (k3_scale), (dim3(g, S)), 256, 0, st, (int)n, c->w, n, c->scal, c->active, c->V + (size_t)(j + 1) * n, vsl);
       TRY3(launched3());
     }
     // x += Z y per slice (back substitution on the host)
@@ -952,7 +1049,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
     CK3(cudaMemcpyAsync(c->active, cyc.data(), S, cudaMemcpyHostToDevice, st));
     CK3(cudaMemcpyAsync(c->ycoef, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CK3(cudaMemcpyAsync(c->cnt, cnt.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-    k3_add_basis<<<dim3(g, S), 256, 0, st>>>((int)n, c->Z, n, zsl, c->ycoef, c->cnt, c->active, x, n);
+    P3(KI3_ADD_BASIS, (k3_add_basis), (dim3(g, S)), 256, 0, st, (int)n, c->Z, n, zsl, c->ycoef, c->cnt, c->active, x, n);
     TRY3(launched3());
   }
   if (stats)
@@ -980,7 +1077,7 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
   CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
   CK3(cudaMemcpyAsync(c->status, st_h.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
   const fsi3_level& L = c->lev[0];
-  k3_apply_dirichlet<<<dim3(nb3(L.h.n_nodes, 128), S), 128, 0, st>>>(L.d, c->P, c->Uit, n, c->t_dev, c->active);
+  P3(KI3_APPLY_DIRICHLET, (k3_apply_dirichlet), (dim3(nb3(L.h.n_nodes, 128), S)), 128, 0, st, L.d, c->P, c->Uit, n, c->t_dev, c->active);
   TRY3(launched3());
   std::vector<double> r0(S, 0.0), nr(S), hr;
   std::vector<int> nit(S, 0), why(S, 0);
@@ -1031,7 +1128,7 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
     } else {
       TRY3(mg_setup3<double>(c, S, c->Uit, c->Uold, k, theta, c->active, st));
     }
-    k3_axpby<double, double><<<dim3(nb3(n, 256), S), 256, 0, st>>>((int)n, -1.0, c->R, n, 0.0, c->active, c->bk, n);
+    P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->bk, n);
     TRY3(launched3());
     int rc = c->mg32 ? fgmres3<float>(c, S, c->bk, c->xk, act, rtol, target, stats, st)
                      : fgmres3<double>(c, S, c->bk, c->xk, act, rtol, target, stats, st);
@@ -1045,7 +1142,7 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
     if (rc != FSI_OK && rc != FSI_EGMRES && rc != FSI_ENAN) return rc;
     if (rc == FSI_EGMRES || rc == FSI_ENAN) status = rc;
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-    k3_axpby<double, double><<<dim3(nb3(n, 256), S), 256, 0, st>>>((int)n, 1.0, c->xk, n, 1.0, c->active, c->Uit, n);
+    P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, 1.0, c->xk, n, 1.0, c->active, c->Uit, n);
     TRY3(launched3());
   }
   CK3(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1090,7 +1187,7 @@ int propagate3(fsi3_ctx* c, int S, const double* U0, const double* t0, double* U
 int correct3(fsi3_ctx* c, int i, const double* Cn, double* U, double inc[3], cudaStream_t st) {
   const size_t n = c->n;
   const int nrb = c->red_blocks;
-  k3_parareal_correct<<<nrb, R3_THREADS, 0, st>>>((int)n, c->Fv + (size_t)i * n, Cn, c->Cold + (size_t)i * n,
+  P3(KI3_PARAREAL_CORRECT, (k3_parareal_correct), (nrb), R3_THREADS, 0, st, (int)n, c->Fv + (size_t)i * n, Cn, c->Cold + (size_t)i * n,
                                                   U + (size_t)(i + 1) * n, c->ppart);
   TRY3(launched3());
   std::vector<double> part((size_t)nrb * 6);
@@ -1113,6 +1210,47 @@ int correct3(fsi3_ctx* c, int i, const double* Cn, double* U, double inc[3], cud
 // C ABI (3D)
 // ---------------------------------------------------------------------------
 extern "C" {
+
+int fsi3_kernel_count(void) { return KI3_COUNT; }
+
+const char* fsi3_kernel_name(int id) { return (id >= 0 && id < KI3_COUNT) ? kKernelNames3[id] : nullptr; }
+
+long long fsi3_launch_count(int id) {
+  if (id >= KI3_COUNT) return -1;
+  if (id >= 0) return g_prof3.launches[id].load();
+  long long t = 0;
+  for (int k = 0; k < KI3_COUNT; ++k) t += g_prof3.launches[k].load();
+  return t;
+}
+
+int fsi3_profile_enable(int on) {
+  std::lock_guard<std::mutex> lock(g_prof3.mu);
+  for (auto& v : g_prof3.ev) {
+    for (auto& pr : v) {
+      cudaEventSynchronize(pr.second);
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    v.clear();
+  }
+  g_prof3.on.store(on != 0);
+  return FSI_OK;
+}
+
+int fsi3_profile_read(int id, double* total_ms, long long* timed_launches) {
+  if (id < 0 || id >= KI3_COUNT || !total_ms || !timed_launches) return fail3(FSI_EINVAL, "bad profile query");
+  std::lock_guard<std::mutex> lock(g_prof3.mu);
+  double t = 0.0;
+  for (auto& pr : g_prof3.ev[id]) {
+    float ms = 0.0f;
+    CK3(cudaEventSynchronize(pr.second));
+    CK3(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    t += ms;
+  }
+  *total_ms = t;
+  *timed_launches = (long long)g_prof3.ev[id].size();
+  return FSI_OK;
+}
 
 void fsi3_destroy(fsi3_ctx* c) {
   if (!c) return;

@@ -119,6 +119,11 @@ SIGNATURES = {
     "fsi3_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi3_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi3_parareal": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+    "fsi3_kernel_count": (_I, []),
+    "fsi3_kernel_name": (C.c_char_p, [_I]),
+    "fsi3_launch_count": (C.c_longlong, [_I]),
+    "fsi3_profile_enable": (_I, [_I]),
+    "fsi3_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong)]),
     "fsi_profile_enable": (_I, [C.c_ulonglong]),
     "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
     "fsi_launch_count": (C.c_longlong, [_I]),
@@ -393,6 +398,31 @@ class Context:
         if history:
             d["history"] = hist[:d["iterations"]].tolist()
         return U, d
+
+
+def kernel_names3():
+    lib = load_library()
+    return [lib.fsi3_kernel_name(i).decode() for i in range(lib.fsi3_kernel_count())]
+
+
+def profile3(on=True):
+    """Start (clearing earlier records) or stop CUDA-event timing of the 3D kernels."""
+    _check(load_library().fsi3_profile_enable(1 if on else 0))
+
+
+def profile3_read():
+    """{kernel name: (summed device ms, timed launches)} of the 3D kernels recorded so far."""
+    lib = load_library()
+    out = {}
+    for i, name in enumerate(kernel_names3()):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(lib.fsi3_profile_read(i, C.byref(ms), C.byref(n)))
+        out[name] = (ms.value, n.value)
+    return out
+
+
+def launch_count3():
+    return load_library().fsi3_launch_count(-1)
 
 
 def fsi_setup(workload, max_batch=1, **overrides):

@@ -55,3 +55,19 @@ def test_fsi3_setup_rejects_a_bad_mesh(fsi):
     h = C.c_void_p()
     rc = fsi.load_library().fsi3_setup(C.byref(mesh), C.byref(prm), C.byref(h))
     assert rc == fsi.FSI_EINVAL and "segment" in fsi.load_library().fsi_last_error().decode()
+
+
+def test_fsi3_launch_accounting_on_the_host(fsi):
+    """The 3D kernel table and its accounting work without a device: every 3D kernel has a
+    name, nothing ran in this process, and enabling and reading records is harmless."""
+    names = fsi.kernel_names3()
+    assert len(names) == len(set(names)) and all(n.startswith("k3_") for n in names)
+    assert {"k3_cell_jacobian", "k3_vanka_apply", "k3_vanka_setup", "k3_spmv"} <= set(names)
+    assert fsi.launch_count3() == 0
+    fsi.profile3(True)
+    assert all(v == (0.0, 0) for v in fsi.profile3_read().values())
+    fsi.profile3(False)
+    lib = fsi.load_library()
+    assert lib.fsi3_kernel_name(len(names)) is None and lib.fsi3_launch_count(len(names)) == -1
+    ms, n = C.c_double(), C.c_longlong()
+    assert lib.fsi3_profile_read(-1, C.byref(ms), C.byref(n)) == fsi.FSI_EINVAL
