@@ -116,8 +116,8 @@ extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, c
 }
 
 // The assembled Jacobian of one slice in 7 x 7 blocks (row-major), computed the
-// way the kernels will: element matrices per cell, then every block entry by
-// the fixed-order gather. rowptr_out [n_nodes + 1], colidx_out [nnzb],
+// way the kernels do: element matrices per cell by the kernel's cooperative
+// routine, then every block entry by the fixed-order gather. rowptr_out [n_nodes + 1], colidx_out [nnzb],
 // vals_out [nnzb][49]; the sizes come from fsi3_mesh_host.
 extern "C" int fsi3_jacobian_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
                                   int nyseg, const double* zb, const int* nzs, int nzseg, const double* box,
@@ -131,7 +131,7 @@ extern "C" int fsi3_jacobian_host(const double* xb, const int* nxs, int nxseg, c
   }
   const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
   const fsi3::Phys3 P{mat[0], mat[1], mat[2], mat[3], mat[4]};
-  std::vector<double> Ke((size_t)m.n_cells * 189 * 189), Ue(189), Uoe(189);
+  std::vector<double> Ke((size_t)m.n_cells * 189 * 189), Ue(189), Uoe(189), sh(fsi3::CJ3_TOTAL);
   for (int c = 0; c < m.n_cells; ++c) {
     for (int l = 0; l < 27; ++l)
       for (int f = 0; f < 7; ++f) {
@@ -141,7 +141,11 @@ extern "C" int fsi3_jacobian_host(const double* xb, const int* nxs, int nxseg, c
     const double* h = &m.cell_h[(size_t)c * 3];
     const bool solid = m.cell_flags[c] & fsi3::C3_SOLID, outflow = m.cell_flags[c] & fsi3::C3_OUTFLOW;
     const double alpha = fsi3::stab_weight3(T, Uoe.data(), h, mat[7], mat[0], mat[1]);
-    fsi3::cell_jacobian3(P, T, Ue.data(), Uoe.data(), h, solid, outflow, k, theta, alpha, &Ke[(size_t)c * 189 * 189]);
+    // the kernel's routine (cooperative, sum-factorised), run by one host thread
+    std::copy(Ue.begin(), Ue.end(), sh.begin() + fsi3::CJ3_UE);
+    std::copy(Uoe.begin(), Uoe.end(), sh.begin() + fsi3::CJ3_UE + 189);
+    fsi3::cell_jacobian3_cta(fsi3::HostCta{}, P, T, h, solid, outflow, k, theta, alpha, sh.data(),
+                             &Ke[(size_t)c * 189 * 189]);
   }
   const fsi3::Mesh3View v = view(m);
   std::copy(m.rowptr.begin(), m.rowptr.end(), rowptr_out);

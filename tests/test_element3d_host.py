@@ -455,10 +455,12 @@ def test_3d_theta_step_matches_the_oracle(host_lib, oracle_step_3d, precision, s
 
 
 @pytest.mark.parametrize("seed,k,theta", [(1, 0.02, 0.52), (2, 1 / 16, 1.0)])
-def test_cooperative_cell_jacobian_is_bitwise_the_serial_one(host_lib, seed, k, theta):
-    """The element matrix routine of the kernel (work spread over a thread group, run
-    here as one host thread) performs the serial routine's arithmetic in the same
-    order: identical bits on fluid, solid and outflow cells, every entry written."""
+def test_cooperative_cell_jacobian_matches_the_serial_one(host_lib, seed, k, theta):
+    """The element matrix routine of the kernel (work spread over a thread group, the
+    contraction over the Gauss points sum-factorised; run here as one host thread)
+    equals the serial routine up to rounding on fluid, solid and outflow cells: every
+    (test, trial) block within 1e-13 of its largest entry, zero blocks exactly zero,
+    every entry written."""
     P = C.POINTER(C.c_double)
     for name in ("fsi3_cell_jacobian_host", "fsi3_cell_jacobian_cta_host"):
         getattr(host_lib, name).argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P]
@@ -478,7 +480,15 @@ def test_cooperative_cell_jacobian_is_bitwise_the_serial_one(host_lib, seed, k, 
         K1, K2 = np.zeros(189 * 189), np.zeros(189 * 189)
         host_lib.fsi3_cell_jacobian_host(*args, ptr(K1))
         host_lib.fsi3_cell_jacobian_cta_host(*args, ptr(K2))
-        assert np.array_equal(K1, K2), c
+        A1, A2 = K1.reshape(27, 7, 27, 7), K2.reshape(27, 7, 27, 7)
+        for ci in range(7):
+            for cj in range(7):
+                b1, b2 = A1[:, ci, :, cj], A2[:, ci, :, cj]
+                sc = np.abs(b1).max()
+                if sc == 0.0:
+                    assert np.all(b2 == 0.0), (c, ci, cj)
+                else:
+                    assert np.abs(b2 - b1).max() <= 1e-13 * sc, (c, ci, cj, np.abs(b2 - b1).max() / sc)
         kinds.add((bool(mesh.cell_solid[c]), bool(outflow[c])))
     assert kinds == {(False, False), (True, False), (False, True)}
 
