@@ -170,73 +170,107 @@ FSI3_HD inline void face_flux3(const Phys3& P, const M3& G, const M3& Hu, const 
 // Directional derivative of qp_flux3 in the direction (dv, dG, du, dH, dp) of
 // the t_n unknowns, out[28]. In 3D the adjugate is quadratic in grad u:
 // d adj(F)[dH] = (tr(A dH) A - A dH A) / J (from adj F = J F^{-1}).
-FSI3_HD inline void qp_flux3_lin(const Phys3& P, const Qp3& q, bool solid, double k, double theta, const double* dv,
-                                 const M3& dG, const double* du, const M3& dH, double dp, double* out) {
+// The parts of the linearised flux at one point that do not depend on the
+// direction (state, old state and material only): computed once per point and
+// shared by its 28 directions.
+struct Qp3Lin {
+  M3 F, A, C, Co, Gh, Bh, Gt, Q, Sig;
+  double J, Jh, w[3], Bw[3], M[3], Av[3];
+};
+
+FSI3_HD inline void qp_lin_prepare3(const Phys3& P, const Qp3& q, bool solid, Qp3Lin& L) {
+  const M3 I = eye3();
+  L.F = add(I, q.Hu);
+  if (!solid) {
+    const M3 Fo = add(I, q.Huo);
+    L.J = det(L.F);
+    const double Jo = det(Fo);
+    L.A = adj(L.F);
+    L.C = tp(L.A);
+    L.Co = tp(adj(Fo));
+    L.Gh = scale(0.5, add(q.G, q.Go));
+    const M3 Fh = add(I, scale(0.5, add(q.Hu, q.Huo)));
+    L.Bh = scale(1.0 / det(Fh), adj(Fh));
+    L.Jh = 0.5 * (L.J + Jo);
+    for (int c = 0; c < 3; ++c) L.w[c] = q.u[c] - q.uo[c];
+    mv(L.Bh, L.w, L.Bw);
+    mv(L.Gh, L.Bw, L.M);
+    mv(L.A, q.v, L.Av);
+    L.Gt = tp(q.G);
+    L.Q = add(mul(mul(q.G, L.A), L.C), mul(mul(L.C, L.Gt), L.C));
+  } else {
+    const double mu = P.mu_s, lam = P.lambda_s;
+    const M3 E = scale(0.5, add(mul(tp(L.F), L.F), scale(-1.0, I)));
+    L.Sig = add(scale(2.0 * mu, E), scale(lam * trace(E), I));
+  }
+}
+
+// The linearised flux at one point in one direction, from the prepared parts.
+FSI3_HD inline void qp_flux3_lin_prepared(const Phys3& P, const Qp3& q, const Qp3Lin& L, bool solid, double k,
+                                          double theta, const double* dv, const M3& dG, const double* du,
+                                          const M3& dH, double dp, double* out) {
   for (int i = 0; i < 28; ++i) out[i] = 0.0;
   const double kt = k * theta, kto = k * (1.0 - theta);
-  const M3 I = eye3();
-  const M3 F = add(I, q.Hu);
   if (!solid) {
     const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
-    const M3 Fo = add(I, q.Huo);
-    const double J = det(F), Jo = det(Fo);
-    const M3 A = adj(F), C = tp(A), Co = tp(adj(Fo));
+    const M3& A = L.A;
+    const M3& C = L.C;
+    const double J = L.J;
     const double dJ = trace(mul(A, dH));
     const M3 dA = scale(1.0 / J, add(scale(dJ, A), scale(-1.0, mul(mul(A, dH), A))));
     const M3 dC = tp(dA);
     // mass term: Jh ((v - vo) - Gh Bh w), Bh = Fh^{-1}, dBh = -Bh (dH / 2) Bh
-    const M3 Gh = scale(0.5, add(q.G, q.Go));
-    const M3 Fh = add(I, scale(0.5, add(q.Hu, q.Huo)));
-    const M3 Bh = scale(1.0 / det(Fh), adj(Fh));
-    const double Jh = 0.5 * (J + Jo), dJh = 0.5 * dJ;
-    const M3 dBh = scale(-0.5, mul(mul(Bh, dH), Bh));
-    double w[3], Bw[3], M[3], t1[3], t2[3], t3[3], t4[3], dM[3];
-    for (int c = 0; c < 3; ++c) w[c] = q.u[c] - q.uo[c];
-    mv(Bh, w, Bw);
-    mv(Gh, Bw, M);
-    mv(dG, Bw, t1);                 // dGh Bh w = (dG / 2) Bh w
-    mv(dBh, w, t2);
-    mv(Gh, t2, t3);                 // Gh dBh w
-    mv(Bh, du, t2);
-    mv(Gh, t2, t4);                 // Gh Bh dw
+    const double dJh = 0.5 * dJ;
+    const M3 dBh = scale(-0.5, mul(mul(L.Bh, dH), L.Bh));
+    double t1[3], t2[3], t3[3], t4[3], dM[3];
+    mv(dG, L.Bw, t1);               // dGh Bh w = (dG / 2) Bh w
+    mv(dBh, L.w, t2);
+    mv(L.Gh, t2, t3);               // Gh dBh w
+    mv(L.Bh, du, t2);
+    mv(L.Gh, t2, t4);               // Gh Bh dw
     for (int c = 0; c < 3; ++c) dM[c] = 0.5 * t1[c] + t3[c] + t4[c];
     // convection G A v
-    double Av[3], dGAv[3], dAv[3], GdAv[3], Adv[3], GAdv[3];
-    mv(A, q.v, Av);
-    mv(dG, Av, dGAv);
+    double dGAv[3], dAv[3], GdAv[3], Adv[3], GAdv[3];
+    mv(dG, L.Av, dGAv);
     mv(dA, q.v, dAv);
     mv(q.G, dAv, GdAv);
     mv(A, dv, Adv);
     mv(q.G, Adv, GAdv);
     for (int c = 0; c < 3; ++c)
-      out[c * 4] = rf * (dJh * ((q.v[c] - q.vo[c]) - M[c]) + Jh * (dv[c] - dM[c])) +
+      out[c * 4] = rf * (dJh * ((q.v[c] - q.vo[c]) - L.M[c]) + L.Jh * (dv[c] - dM[c])) +
                    kt * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
     // stress (rho nu / J) Q - p C with Q = G A C + C G^T C; the old term depends on p only
-    const M3 Gt = tp(q.G), dGt = tp(dG);
-    const M3 Q = add(mul(mul(q.G, A), C), mul(mul(C, Gt), C));
+    const M3 dGt = tp(dG);
+    const M3& Gt = L.Gt;
     M3 dQ = add(add(mul(mul(dG, A), C), mul(mul(q.G, dA), C)), mul(mul(q.G, A), dC));
     dQ = add(dQ, add(add(mul(mul(dC, Gt), C), mul(mul(C, dGt), C)), mul(mul(C, Gt), dC)));
     for (int c = 0; c < 3; ++c)
       for (int j = 0; j < 3; ++j)
-        out[c * 4 + 1 + j] = kt * ((rn / J) * dQ.m[c][j] - (rn * dJ / (J * J)) * Q.m[c][j] - dp * C.m[c][j] -
+        out[c * 4 + 1 + j] = kt * ((rn / J) * dQ.m[c][j] - (rn * dJ / (J * J)) * L.Q.m[c][j] - dp * C.m[c][j] -
                                    q.p * dC.m[c][j]) -
-                             kto * dp * Co.m[c][j];
+                             kto * dp * L.Co.m[c][j];
     for (int c = 0; c < 3; ++c)
       for (int j = 0; j < 3; ++j) out[(3 + c) * 4 + 1 + j] = kt * dH.m[c][j];
     out[6 * 4] = k * (trace(mul(dG, A)) + trace(mul(q.G, dA)));
   } else {
     const double mu = P.mu_s, lam = P.lambda_s;
-    const M3 E = scale(0.5, add(mul(tp(F), F), scale(-1.0, I)));
-    const M3 Sig = add(scale(2.0 * mu, E), scale(lam * trace(E), I));
+    const M3& F = L.F;
     const M3 dE = scale(0.5, add(mul(tp(dH), F), mul(tp(F), dH)));
-    const M3 dSig = add(scale(2.0 * mu, dE), scale(lam * trace(dE), I));
-    const M3 S = scale(kt, add(mul(dH, Sig), mul(F, dSig)));
+    const M3 dSig = add(scale(2.0 * mu, dE), scale(lam * trace(dE), eye3()));
+    const M3 S = scale(kt, add(mul(dH, L.Sig), mul(F, dSig)));
     for (int c = 0; c < 3; ++c) {
       out[c * 4] = P.rho_s * dv[c];
       out[(3 + c) * 4] = du[c] - kt * dv[c];
       for (int j = 0; j < 3; ++j) out[c * 4 + 1 + j] = S.m[c][j];
     }
   }
+}
+
+FSI3_HD inline void qp_flux3_lin(const Phys3& P, const Qp3& q, bool solid, double k, double theta, const double* dv,
+                                 const M3& dG, const double* du, const M3& dH, double dp, double* out) {
+  Qp3Lin L;
+  qp_lin_prepare3(P, q, solid, L);
+  qp_flux3_lin_prepared(P, q, L, solid, k, theta, dv, dG, du, dH, dp, out);
 }
 
 // Directional derivative of face_flux3 in the t_n gradients (dG, dH), out[3].
@@ -554,8 +588,11 @@ constexpr int CJ3_UE = CJ3_FLAG + 8;            // Ue[189], Uo[189]
 constexpr int CJ3_T1 = CJ3_UE + 378;            // [4 a][27 m][9 (q1, q2)][3 l3]
 constexpr int CJ3_T2 = CJ3_T1 + 2916;           // [4 a][27 m][3 q1][9 (l2, l3)]
 constexpr int CJ3_F = CJ3_T2 + 2916;            // [3 d][2: value, derivative / h_d][3 i][3 s]
-constexpr int CJ3_TOTAL = CJ3_F + 54;
+constexpr int CJ3_LSZ = (int)(sizeof(Qp3Lin) / sizeof(double));
+constexpr int CJ3_XL = CJ3_F + 54;              // Qp3Lin[27]: the direction-independent tangent parts
+constexpr int CJ3_TOTAL = CJ3_XL + 27 * CJ3_LSZ;
 static_assert(sizeof(Qp3) % sizeof(double) == 0, "Qp3 holds doubles only");
+static_assert(sizeof(Qp3Lin) % sizeof(double) == 0, "Qp3Lin holds doubles only");
 
 FSI3_HD inline bool cj3_nonzero(double x) {
 #ifdef __CUDA_ARCH__
@@ -580,8 +617,10 @@ FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tab
   double* flag = sh + CJ3_FLAG;
   const double vol = h[0] * h[1] * h[2];
   const bool face = outflow && !solid;
+  Qp3Lin* XL = reinterpret_cast<Qp3Lin*>(sh + CJ3_XL);
   for (int q = cta.tid; q < 27; q += cta.nt) {
     X[q] = qp_state3(T, Ue, Uo, h, q);
+    qp_lin_prepare3(P, X[q], solid, XL[q]);
     Wq[q] = T.wq[q] * vol;
   }
   for (int e = cta.tid; e < 27 * 4 * 27; e += cta.nt) {
@@ -631,7 +670,7 @@ FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tab
         dp = 1.0;
       }
       double o[28];
-      qp_flux3_lin(P, X[q], solid, k, theta, dv, dG, du, dH, dp, o);
+      qp_flux3_lin_prepared(P, X[q], XL[q], solid, k, theta, dv, dG, du, dH, dp, o);
       for (int r = 0; r < 28; ++r) Dc[(q * 28 + r) * 4 + b] = o[r];
     }
     if (face && cj < 6)
