@@ -174,7 +174,7 @@ FSI3_HD inline void face_flux3(const Phys3& P, const M3& G, const M3& Hu, const 
 // direction (state, old state and material only): computed once per point and
 // shared by its 28 directions.
 struct Qp3Lin {
-  M3 F, A, C, Co, Gh, Bh, Gt, Q, Sig;
+  M3 F, A, C, Co, Gh, Bh, Gt, Q, Sig, AC;
   double J, Jh, w[3], Bw[3], M[3], Av[3];
 };
 
@@ -198,6 +198,7 @@ FSI3_HD inline void qp_lin_prepare3(const Phys3& P, const Qp3& q, bool solid, Qp
     mv(L.A, q.v, L.Av);
     L.Gt = tp(q.G);
     L.Q = add(mul(mul(q.G, L.A), L.C), mul(mul(L.C, L.Gt), L.C));
+    L.AC = mul(L.A, L.C);
   } else {
     const double mu = P.mu_s, lam = P.lambda_s;
     const M3 E = scale(0.5, add(mul(tp(L.F), L.F), scale(-1.0, I)));
@@ -264,6 +265,107 @@ FSI3_HD inline void qp_flux3_lin_prepared(const Phys3& P, const Qp3& q, const Qp
       for (int j = 0; j < 3; ++j) out[c * 4 + 1 + j] = S.m[c][j];
     }
   }
+}
+
+// The linearised flux in one unit direction: trial field cj (v, u components,
+// then p), slot b (0: the value, 1 + d: the derivative in direction d). Only
+// the nine displacement-gradient directions need dense 3 x 3 products; the
+// others reduce to rank-one updates or vanish. Equal to
+// qp_flux3_lin_prepared in the same direction up to rounding.
+FSI3_HD inline void qp_flux3_lin_unit(const Phys3& P, const Qp3& q, const Qp3Lin& L, bool solid, double k,
+                                      double theta, int cj, int b, double* out) {
+  for (int i = 0; i < 28; ++i) out[i] = 0.0;
+  const double kt = k * theta, kto = k * (1.0 - theta);
+  if (solid) {
+    if (cj < 3) {
+      if (b == 0) {
+        out[cj * 4] = P.rho_s;
+        out[(3 + cj) * 4] = -kt;
+      }
+    } else if (cj < 6) {
+      const int c = cj - 3;
+      if (b == 0) {
+        out[(3 + c) * 4] = 1.0;
+      } else {
+        const int j = b - 1;   // dH = e_c e_j^T
+        const double mu = P.mu_s, lam = P.lambda_s;
+        const M3& F = L.F;
+        M3 dSig;
+        const double trE = F.m[c][j];
+        for (int r = 0; r < 3; ++r)
+          for (int t = 0; t < 3; ++t) {
+            const double dE = 0.5 * ((r == j ? F.m[c][t] : 0.0) + (t == j ? F.m[c][r] : 0.0));
+            dSig.m[r][t] = 2.0 * mu * dE + (r == t ? lam * trE : 0.0);
+          }
+        const M3 FdS = mul(F, dSig);
+        for (int r = 0; r < 3; ++r)
+          for (int t = 0; t < 3; ++t) out[r * 4 + 1 + t] = kt * ((r == c ? L.Sig.m[j][t] : 0.0) + FdS.m[r][t]);
+      }
+    }
+    return;
+  }
+  const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
+  const M3& A = L.A;
+  const M3& C = L.C;
+  const double J = L.J;
+  if (cj < 3) {
+    const int c = cj;
+    if (b == 0) {   // dv = e_c: mass and convection G A e_c
+      for (int r = 0; r < 3; ++r) {
+        double gac = 0.0;
+        for (int t = 0; t < 3; ++t) gac += q.G.m[r][t] * A.m[t][c];
+        out[r * 4] = rf * (L.Jh * (r == c ? 1.0 : 0.0)) + kt * rf * gac;
+      }
+      return;
+    }
+    const int j = b - 1;   // dG = e_c e_j^T
+    out[c * 4] = rf * (L.Jh * (-0.5 * L.Bw[j])) + kt * rf * L.Av[j];
+    for (int r = 0; r < 3; ++r)
+      for (int t = 0; t < 3; ++t) {
+        const double dQ = (r == c ? L.AC.m[j][t] : 0.0) + C.m[r][j] * C.m[c][t];
+        out[r * 4 + 1 + t] = kt * ((rn / J) * dQ);
+      }
+    out[6 * 4] = k * A.m[j][c];
+    return;
+  }
+  if (cj < 6) {
+    const int c = cj - 3;
+    if (b == 0) {   // du = e_c: the mesh-velocity part of the mass term, Gh Bh e_c
+      double t2[3] = {L.Bh.m[0][c], L.Bh.m[1][c], L.Bh.m[2][c]}, t4[3];
+      mv(L.Gh, t2, t4);
+      for (int r = 0; r < 3; ++r) out[r * 4] = rf * (L.Jh * (0.0 - t4[r]));
+      return;
+    }
+    const int j = b - 1;   // dH = e_c e_j^T
+    const double dJ = A.m[j][c];
+    M3 dA, dBh;
+    for (int r = 0; r < 3; ++r)
+      for (int t = 0; t < 3; ++t) {
+        dA.m[r][t] = (1.0 / J) * (dJ * A.m[r][t] - A.m[r][c] * A.m[j][t]);
+        dBh.m[r][t] = -0.5 * (L.Bh.m[r][c] * L.Bh.m[j][t]);
+      }
+    const M3 dC = tp(dA);
+    double t2[3], dM[3], dAv[3], GdAv[3];
+    mv(dBh, L.w, t2);
+    mv(L.Gh, t2, dM);
+    mv(dA, q.v, dAv);
+    mv(q.G, dAv, GdAv);
+    const double dJh = 0.5 * dJ;
+    for (int r = 0; r < 3; ++r)
+      out[r * 4] = rf * (dJh * ((q.v[r] - q.vo[r]) - L.M[r]) + L.Jh * (0.0 - dM[r])) + kt * rf * GdAv[r];
+    const M3& Gt = L.Gt;
+    const M3 dQ = add(add(mul(mul(q.G, dA), C), mul(mul(q.G, A), dC)),
+                      add(mul(mul(dC, Gt), C), mul(mul(C, Gt), dC)));
+    for (int r = 0; r < 3; ++r)
+      for (int t = 0; t < 3; ++t)
+        out[r * 4 + 1 + t] = kt * ((rn / J) * dQ.m[r][t] - (rn * dJ / (J * J)) * L.Q.m[r][t] - q.p * dC.m[r][t]);
+    out[(3 + c) * 4 + 1 + j] = kt;
+    out[6 * 4] = k * trace(mul(q.G, dA));
+    return;
+  }
+  if (b == 0)   // dp = 1
+    for (int r = 0; r < 3; ++r)
+      for (int t = 0; t < 3; ++t) out[r * 4 + 1 + t] = kt * (-C.m[r][t]) - kto * L.Co.m[r][t];
 }
 
 FSI3_HD inline void qp_flux3_lin(const Phys3& P, const Qp3& q, bool solid, double k, double theta, const double* dv,
@@ -658,19 +760,8 @@ FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tab
     if (cta.tid < 7) flag[cta.tid] = 0.0;
     for (int e = cta.tid; e < 27 * 4; e += cta.nt) {
       const int q = e / 4, b = e % 4;
-      double dv[3] = {0, 0, 0}, du[3] = {0, 0, 0}, dp = 0.0;
-      M3 dG{}, dH{};
-      if (cj < 3) {
-        if (b == 0) dv[cj] = 1.0;
-        else dG.m[cj][b - 1] = 1.0;
-      } else if (cj < 6) {
-        if (b == 0) du[cj - 3] = 1.0;
-        else dH.m[cj - 3][b - 1] = 1.0;
-      } else if (b == 0) {
-        dp = 1.0;
-      }
       double o[28];
-      qp_flux3_lin_prepared(P, X[q], XL[q], solid, k, theta, dv, dG, du, dH, dp, o);
+      qp_flux3_lin_unit(P, X[q], XL[q], solid, k, theta, cj, b, o);
       for (int r = 0; r < 28; ++r) Dc[(q * 28 + r) * 4 + b] = o[r];
     }
     if (face && cj < 6)

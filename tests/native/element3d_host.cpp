@@ -251,3 +251,38 @@ extern "C" int fsi3_vanka_host(const double* xb, const int* nxs, int nxseg, cons
   }
   return 0;
 }
+
+// The tangent at every Gauss point in all 28 unit directions, by the general
+// routine and by the unit-direction routine: Dg, Du [27][28 directions][28 outputs].
+extern "C" int fsi3_tangents_host(const double* phys, const double* Ue, const double* Uo, const double* h, int solid,
+                                  double k, double theta, double* Dg, double* Du) {
+  static fsi3::Tables3 T;
+  static bool ready = false;
+  if (!ready) {
+    fsi3::build_tables3(T);
+    ready = true;
+  }
+  const fsi3::Phys3 P{phys[0], phys[1], phys[2], phys[3], phys[4]};
+  for (int q = 0; q < 27; ++q) {
+    const fsi3::Qp3 x = fsi3::qp_state3(T, Ue, Uo, h, q);
+    fsi3::Qp3Lin L;
+    fsi3::qp_lin_prepare3(P, x, solid != 0, L);
+    for (int dir = 0; dir < 28; ++dir) {
+      const int cj = dir / 4, b = dir % 4;
+      double dv[3] = {0, 0, 0}, du[3] = {0, 0, 0}, dp = 0.0;
+      fsi3::M3 dG{}, dH{};
+      if (cj < 3) {
+        if (b == 0) dv[cj] = 1.0;
+        else dG.m[cj][b - 1] = 1.0;
+      } else if (cj < 6) {
+        if (b == 0) du[cj - 3] = 1.0;
+        else dH.m[cj - 3][b - 1] = 1.0;
+      } else if (b == 0) {
+        dp = 1.0;
+      }
+      fsi3::qp_flux3_lin_prepared(P, x, L, solid != 0, k, theta, dv, dG, du, dH, dp, Dg + (q * 28 + dir) * 28);
+      fsi3::qp_flux3_lin_unit(P, x, L, solid != 0, k, theta, cj, b, Du + (q * 28 + dir) * 28);
+    }
+  }
+  return 0;
+}

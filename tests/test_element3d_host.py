@@ -507,3 +507,27 @@ def test_3d_cell_colours_share_no_node():
     for k in range(8):
         nodes = mesh.cell_nodes[colour == k].ravel()
         assert len(np.unique(nodes)) == len(nodes), k
+
+
+@pytest.mark.parametrize("solid", [0, 1])
+def test_unit_direction_tangent_matches_the_general_one(host_lib, solid):
+    """The tangent specialised to unit directions (rank-one forms for the velocity,
+    velocity-gradient, displacement and pressure directions) equals the general
+    linearisation at every Gauss point and direction, on random states, to 1e-13 of
+    the largest entry of that point's tangent."""
+    P = C.POINTER(C.c_double)
+    host_lib.fsi3_tangents_host.argtypes = [P, P, P, P, C.c_int, C.c_double, C.c_double, P, P]
+    mat = wl.Material()
+    phys = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s])
+    rng = np.random.default_rng(40 + solid)
+    for trial in range(3):
+        Ue = np.empty((27, 7))
+        Ue[:, :3], Ue[:, 3:6], Ue[:, 6] = rng.normal(size=(27, 3)), 0.05 * rng.normal(size=(27, 3)), rng.normal(size=27)
+        Uo = Ue + 0.01 * rng.normal(size=Ue.shape)
+        h = rng.uniform(0.05, 0.2, 3)
+        Dg, Du = np.zeros(27 * 28 * 28), np.zeros(27 * 28 * 28)
+        host_lib.fsi3_tangents_host(ptr(phys), ptr(np.ascontiguousarray(Ue)), ptr(np.ascontiguousarray(Uo)), ptr(h),
+                                    solid, 0.02, 0.52, ptr(Dg), ptr(Du))
+        Dg, Du = Dg.reshape(27, 28, 28), Du.reshape(27, 28, 28)
+        scale = np.abs(Dg).max(axis=(1, 2))
+        assert np.all(np.abs(Du - Dg).max(axis=(1, 2)) <= 1e-13 * scale), np.max(np.abs(Du - Dg).max(axis=(1, 2)) / scale)
