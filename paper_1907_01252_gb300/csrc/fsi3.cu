@@ -596,7 +596,8 @@ struct fsi3_ctx {
   std::vector<void*> owned;
   double *Uit = nullptr, *Uold = nullptr, *R = nullptr, *A64 = nullptr, *Ke = nullptr, *Re = nullptr;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *xk = nullptr, *bk = nullptr;
-  double *partial = nullptr, *dots = nullptr, *scal = nullptr, *ycoef = nullptr, *t_dev = nullptr;
+  double *partial = nullptr, *dots = nullptr, *dots_b = nullptr, *dots_n = nullptr, *scal = nullptr, *ycoef = nullptr,
+         *t_dev = nullptr;
   int *cnt = nullptr, *status = nullptr;
   uint8_t *active = nullptr;
   double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
@@ -893,6 +894,17 @@ int vcycle3(fsi3_ctx* c, size_t l, int S, const T* b, const uint8_t* act, cudaSt
   return FSI_OK;
 }
 
+// Batched dots on the device: out[s * 64 + i] = <V[s][i], w[s]>, i < nv (fixed reduction order).
+int dots3_dev(fsi3_ctx* c, int S, int nv, const double* V, size_t vstride, size_t vslice, const double* w,
+              const uint8_t* act, double* out, cudaStream_t st) {
+  const int n = (int)c->n;
+  const unsigned nblk = nb3(n, R3_CHUNK);
+  P3(KI3_DOTS_PARTIAL, (k3_dots_partial), (dim3(nblk, S)), R3_THREADS, 0, st, n, nv, V, vstride, vslice, w, c->n, act,
+     c->partial);
+  P3(KI3_DOTS_FINISH, (k3_dots_finish), (S), 64, 0, st, (int)nblk, nv, c->partial, act, out);
+  return launched3();
+}
+
 // Batched dots: out[s][i] = <V[s][i], w[s]>, i < nv, to the host array h[S][64].
 int dots3(fsi3_ctx* c, int S, int nv, const double* V, size_t vstride, size_t vslice, const double* w,
           const uint8_t* act, std::vector<double>& h, cudaStream_t st) {
@@ -987,17 +999,23 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
       P3(KI3_SPMV, (k3_spmv<double, false>), (dim3(g, S)), 256, 0, st, L.d, c->A64, c->Z + (size_t)j * n, zsl, nullptr, n,
                                                         c->active, c->w);
       TRY3(launched3());
-      // classical Gram-Schmidt, twice
-      TRY3(dots3(c, S, j + 1, c->V, n, vsl, c->w, c->active, h1, st));
-      CK3(cudaMemcpyAsync(c->dots, h1.data(), (size_t)S * 64 * sizeof(double), cudaMemcpyHostToDevice, st));
+      // classical Gram-Schmidt, twice: the coefficients stay on the device for the subtractions, and the
+      // host reads both passes and the new norm after one synchronisation
+      TRY3(dots3_dev(c, S, j + 1, c->V, n, vsl, c->w, c->active, c->dots, st));
       P3(KI3_SUB_BASIS, (k3_sub_basis), (dim3(g, S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
       TRY3(launched3());
-      TRY3(dots3(c, S, j + 1, c->V, n, vsl, c->w, c->active, h2, st));
-      CK3(cudaMemcpyAsync(c->dots, h2.data(), (size_t)S * 64 * sizeof(double), cudaMemcpyHostToDevice, st));
-      P3(KI3_SUB_BASIS, (k3_sub_basis), (dim3(g, S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->dots, c->active, c->w, n);
+      TRY3(dots3_dev(c, S, j + 1, c->V, n, vsl, c->w, c->active, c->dots_b, st));
+      P3(KI3_SUB_BASIS, (k3_sub_basis), (dim3(g, S)), 256, 0, st, (int)n, j + 1, c->V, n, vsl, c->dots_b, c->active, c->w,
+         n);
       TRY3(launched3());
-      std::vector<double> hn;
-      TRY3(dots3(c, S, 1, c->w, 0, n, c->w, c->active, hn, st));
+      TRY3(dots3_dev(c, S, 1, c->w, 0, n, c->w, c->active, c->dots_n, st));
+      std::vector<double> hn((size_t)S * 64);
+      h1.assign((size_t)S * 64, 0.0);
+      h2.assign((size_t)S * 64, 0.0);
+      CK3(cudaMemcpyAsync(h1.data(), c->dots, (size_t)S * 64 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK3(cudaMemcpyAsync(h2.data(), c->dots_b, (size_t)S * 64 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK3(cudaMemcpyAsync(hn.data(), c->dots_n, (size_t)S * 64 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK3(cudaStreamSynchronize(st));
       for (int s = 0; s < S; ++s) {
         if (!run[s]) continue;
         double hcol[65];
@@ -1326,6 +1344,7 @@ int fsi3_setup(const fsi_mesh3d* mesh, const fsi_params* p, fsi3_ctx** out) {
       (rc = A(&c->Z, S * m * n)) || (rc = A(&c->A64, S * (size_t)L0.h.nnzb * 49)) ||
       (rc = A(&c->Ke, S * cells_max * 189 * 189)) || (rc = A(&c->Re, S * (size_t)L0.h.n_cells * 189)) ||
       (rc = A(&c->partial, S * (size_t)nb3(n, R3_CHUNK) * 64)) || (rc = A(&c->dots, S * 64)) ||
+      (rc = A(&c->dots_b, S * 64)) || (rc = A(&c->dots_n, S * 64)) ||
       (rc = A(&c->scal, S)) || (rc = A(&c->ycoef, S * 64)) || (rc = A(&c->t_dev, S)) || (rc = A(&c->cnt, S)) ||
       (rc = A(&c->status, S)) || (rc = A(&c->active, S)))
     return cleanup(rc);
