@@ -32,6 +32,7 @@ def try_setup(fsi, w, **overrides):
     (dict(mg_smoother=2), "mg_smoother"),
     (dict(max_batch=0), "invalid"),
     (dict(newton_tol=0.0), "invalid"),
+    (dict(mg_coarse_sweeps=-1), "mg_coarse_sweeps"),
 ])
 def test_fsi3_setup_rejects_bad_parameters(fsi, overrides, msg):
     rc, err, h = try_setup(fsi, wl.SMALL3D_8x4x4, **overrides)
