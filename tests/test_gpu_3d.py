@@ -158,3 +158,19 @@ def test_3d_parareal_iterate_matches_oracle():
         for name, sl in FIELDS.items():
             den = max(np.abs(ref[i][:, sl]).max(), 1e-300)
             assert np.abs(got[:, sl] - ref[i][:, sl]).max() <= 1e-9 * den, (i, name)
+
+
+def test_3d_failures_are_reported_per_slice():
+    """A non-finite state in one slice ends that slice with FSI_ENAN (per-slice status) while
+    the other slice completes; a batch larger than max_batch is rejected with FSI_EINVAL."""
+    from paper_1907_01252_gb300 import fsi
+    ctx = ctx_for(TINY, 2)
+    U = torch.zeros((2, ctx.n_dofs), dtype=torch.float64, device=DEV)
+    U[1, 7 * (5 + 11 * (2 + 5 * 3)) + 6] = float("nan")   # the pressure of an interior node (i, j, k) = (5, 2, 3)
+    with pytest.raises(fsi.FsiError) as e:
+        ctx.fsi3_theta_step(U, [0.0, 0.0], 0.01, 0.51)
+    assert e.value.code == fsi.FSI_ENAN
+    assert e.value.slice_status == [0, fsi.FSI_ENAN]
+    with pytest.raises(fsi.FsiError) as e:
+        ctx.fsi3_theta_step(torch.zeros((3, ctx.n_dofs), dtype=torch.float64, device=DEV), [0.0] * 3, 0.01, 0.51)
+    assert e.value.code == fsi.FSI_EINVAL
