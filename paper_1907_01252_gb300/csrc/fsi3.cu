@@ -177,27 +177,34 @@ __global__ void k3_apply_dirichlet(Dev3 d, Phys3D P, double* __restrict__ U, siz
     if (fsi3::identity_row3(nf, c)) x[c] = fsi3::dirichlet3(d.v, node, c, t[s], P.vbar, P.ramp_t);
 }
 
-// Per cell: stabilisation weight from the old state, then the cell residual Re[s][cell][189].
-__global__ void __launch_bounds__(128) k3_cell_residual(Dev3 d, Phys3D P, const double* __restrict__ U,
-                                                       const double* __restrict__ Uo, size_t stride, double k,
-                                                       double theta, const uint8_t* __restrict__ active,
-                                                       double* __restrict__ Re) {
+// Per cell: stabilisation weight from the old state, then the cell residual
+// Re[s][cell][189]; one CTA per (cell, slice) running the cooperative routine.
+constexpr int CR3_THREADS = 192;
+
+__global__ void __launch_bounds__(CR3_THREADS, 1) k3_cell_residual(Dev3 d, Phys3D P, const double* __restrict__ U,
+                                                               const double* __restrict__ Uo, size_t stride, double k,
+                                                               double theta, const uint8_t* __restrict__ active,
+                                                               double* __restrict__ Re) {
   const int s = blockIdx.y;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cell = blockIdx.x;
   if (!active[s] || cell >= d.v.n_cells) return;
-  double Ue[189], Uoe[189];
+  __shared__ double shr[fsi3::CR3_TOTAL];
+  __shared__ double alpha_s;
   const int* cn = d.cell_nodes + (size_t)cell * 27;
-  for (int l = 0; l < 27; ++l)
-    for (int f = 0; f < 7; ++f) {
-      Ue[l * 7 + f] = U[s * stride + (size_t)cn[l] * 7 + f];
-      Uoe[l * 7 + f] = Uo[s * stride + (size_t)cn[l] * 7 + f];
-    }
+  for (int e = threadIdx.x; e < 189; e += blockDim.x) {
+    const size_t g = s * stride + (size_t)cn[e / 7] * 7 + e % 7;
+    shr[fsi3::CR3_UE + e] = U[g];
+    shr[fsi3::CR3_UE + 189 + e] = Uo[g];
+  }
+  __syncthreads();
   const double* h = d.cell_h + (size_t)cell * 3;
+  if (threadIdx.x == 0) alpha_s = fsi3::stab_weight3(c_tab3, shr + fsi3::CR3_UE + 189, h, P.alpha0, P.rho_f, P.nu_f);
+  __syncthreads();
   const uint8_t cf = d.v.cell_flags[cell];
-  const double alpha = fsi3::stab_weight3(c_tab3, Uoe, h, P.alpha0, P.rho_f, P.nu_f);
   const fsi3::Phys3 ph{P.rho_f, P.nu_f, P.rho_s, P.mu_s, P.lambda_s};
-  fsi3::cell_residual3(ph, c_tab3, Ue, Uoe, h, cf & fsi3::C3_SOLID, cf & fsi3::C3_OUTFLOW, k, theta, alpha,
-                       Re + ((size_t)s * d.v.n_cells + cell) * 189);
+  fsi3::cell_residual3_cta(fsi3::DevCta{(int)threadIdx.x, (int)blockDim.x}, ph, c_tab3, h, cf & fsi3::C3_SOLID,
+                           cf & fsi3::C3_OUTFLOW, k, theta, alpha_s, shr,
+                           Re + ((size_t)s * d.v.n_cells + cell) * 189);
 }
 
 __global__ void k3_gather_residual(Dev3 d, Phys3D P, const double* __restrict__ Re, const double* __restrict__ U,
@@ -758,7 +765,8 @@ int validate_mesh3(const fsi_mesh3d* m) {
 int residual3(fsi3_ctx* c, int S, const double* U, const double* Uo, double k, double theta, const uint8_t* act,
               double* R, cudaStream_t st) {
   const fsi3_level& L = c->lev[0];
-  P3(KI3_CELL_RESIDUAL, (k3_cell_residual), (dim3(nb3(L.h.n_cells, 128), S)), 128, 0, st, L.d, c->P, U, Uo, L.n, k, theta, act, c->Re);
+  P3(KI3_CELL_RESIDUAL, (k3_cell_residual), (dim3(L.h.n_cells, S)), CR3_THREADS, 0, st, L.d, c->P, U, Uo, L.n, k, theta,
+     act, c->Re);
   TRY3(launched3());
   P3(KI3_GATHER_RESIDUAL, (k3_gather_residual), (dim3(nb3(L.n, 256), S)), 256, 0, st, L.d, c->P, c->Re, U, L.n, c->t_dev, act, R);
   return launched3();

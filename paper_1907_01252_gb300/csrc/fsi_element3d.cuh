@@ -661,6 +661,73 @@ FSI3_HD inline void cell_jacobian3(const Phys3& P, const Tables3& T, const doubl
 }
 
 // ---------------------------------------------------------------------------
+// The cell residual computed by a cooperative thread group (fsi_cta.h): the
+// arithmetic of cell_residual3 in the same order (bit for bit), with the 27
+// point fluxes and the 9 outflow-face fluxes computed in parallel and each of
+// the 189 entries summed over the points by one thread. Shared scratch
+// CR3_TOTAL doubles; the caller stores Ue at CR3_UE and Uo at CR3_UE + 189 and
+// synchronises before the call.
+// ---------------------------------------------------------------------------
+constexpr int CR3_X = 0;                            // Qp3[27]
+constexpr int CR3_F = CR3_X + 27 * (int)(sizeof(Qp3) / sizeof(double));   // [27][28] point fluxes
+constexpr int CR3_FO = CR3_F + 27 * 28;             // [9][3] face fluxes
+constexpr int CR3_UE = CR3_FO + 27;                 // Ue[189], Uo[189]
+constexpr int CR3_TOTAL = CR3_UE + 378;
+
+template <class Cta>
+FSI3_HD inline void cell_residual3_cta(const Cta& cta, const Phys3& P, const Tables3& T, const double* h, bool solid,
+                                       bool outflow, double k, double theta, double alpha, double* sh, double* Re) {
+  const double* Ue = sh + CR3_UE;
+  const double* Uo = Ue + 189;
+  Qp3* X = reinterpret_cast<Qp3*>(sh + CR3_X);
+  double* F = sh + CR3_F;
+  double* FO = sh + CR3_FO;
+  const double vol = h[0] * h[1] * h[2];
+  const bool face = outflow && !solid;
+  for (int q = cta.tid; q < 27; q += cta.nt) {
+    X[q] = qp_state3(T, Ue, Uo, h, q);
+    qp_flux3(P, X[q], solid, k, theta, F + q * 28);
+  }
+  if (face)
+    for (int f = cta.tid; f < 9; f += cta.nt) {
+      M3 G{}, Hu{}, Go{}, Huo{};
+      for (int l = 0; l < 27; ++l) {
+        const double g[3] = {T.dphi_f[0][f][l] / h[0], T.dphi_f[1][f][l] / h[1], T.dphi_f[2][f][l] / h[2]};
+        for (int c = 0; c < 3; ++c)
+          for (int j = 0; j < 3; ++j) {
+            G.m[c][j] += g[j] * Ue[l * 7 + c];
+            Hu.m[c][j] += g[j] * Ue[l * 7 + 3 + c];
+            Go.m[c][j] += g[j] * Uo[l * 7 + c];
+            Huo.m[c][j] += g[j] * Uo[l * 7 + 3 + c];
+          }
+      }
+      face_flux3(P, G, Hu, Go, Huo, k, theta, FO + f * 3);
+    }
+  cta.sync();
+  const double s3[3] = {vol / (h[0] * h[0]), vol / (h[1] * h[1]), vol / (h[2] * h[2])};
+  for (int e = cta.tid; e < 189; e += cta.nt) {
+    const int l = e / 7, c = e % 7;
+    double r = 0.0;
+    for (int q = 0; q < 27; ++q) {
+      const double* f = F + q * 28;
+      const double W = T.wq[q] * vol;
+      const double ph = T.phi[q][l];
+      const double g[3] = {T.dphi[0][q][l] / h[0], T.dphi[1][q][l] / h[1], T.dphi[2][q][l] / h[2]};
+      r += W * (ph * f[c * 4] + g[0] * f[c * 4 + 1] + g[1] * f[c * 4 + 2] + g[2] * f[c * 4 + 3]);
+    }
+    if (!solid && c == 6) {
+      double acc = 0.0;
+      for (int m = 0; m < 27; ++m)
+        acc += (s3[0] * T.lps[0][l][m] + s3[1] * T.lps[1][l][m] + s3[2] * T.lps[2][l][m]) * Ue[m * 7 + 6];
+      r += k * alpha * acc;
+    }
+    if (face && c < 3)
+      for (int f = 0; f < 9; ++f) r += T.wf[f] * h[1] * h[2] * T.phi_f[f][l] * FO[f * 3 + c];
+    Re[e] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The element matrix computed by a cooperative thread group (fsi_cta.h), with
 // the work spread over the group and each entry of Ke written once. The
 // tangent columns of one trial field cj (27 points x 28 test slots x 4

@@ -31,6 +31,25 @@ extern "C" int fsi3_cell_jacobian_host(const double* phys, const double* Ue, con
   return 0;
 }
 
+// The same cell residual by the cooperative routine the kernel runs (one host thread).
+extern "C" int fsi3_cell_residual_cta_host(const double* phys, const double* Ue, const double* Uo, const double* h,
+                                           int solid, int outflow, double k, double theta, double alpha,
+                                           double* Re) {
+  static fsi3::Tables3 T;
+  static bool ready = false;
+  if (!ready) {
+    fsi3::build_tables3(T);
+    ready = true;
+  }
+  const fsi3::Phys3 P{phys[0], phys[1], phys[2], phys[3], phys[4]};
+  std::vector<double> sh(fsi3::CR3_TOTAL, -1.0);
+  std::copy(Ue, Ue + 189, sh.begin() + fsi3::CR3_UE);
+  std::copy(Uo, Uo + 189, sh.begin() + fsi3::CR3_UE + 189);
+  for (int i = 0; i < 189; ++i) Re[i] = -7.0;
+  fsi3::cell_residual3_cta(fsi3::HostCta{}, P, T, h, solid != 0, outflow != 0, k, theta, alpha, sh.data(), Re);
+  return 0;
+}
+
 // The same element matrix by the cooperative routine the kernel runs (one host thread).
 extern "C" int fsi3_cell_jacobian_cta_host(const double* phys, const double* Ue, const double* Uo, const double* h,
                                            int solid, int outflow, double k, double theta, double alpha,

@@ -557,3 +557,28 @@ def test_3d_coarse_theta_step_matches_the_oracle(host_lib):
     assert rc == 0 and stats[0] >= 2
     err = np.abs(U - ref).max(axis=0) / np.abs(ref).max(axis=0)
     assert np.all(err <= 1e-9), err
+
+
+@pytest.mark.parametrize("seed,k,theta", [(3, 0.02, 0.52), (4, 1 / 16, 1.0)])
+def test_cooperative_cell_residual_is_bitwise_the_serial_one(host_lib, seed, k, theta):
+    """The cell residual routine of the kernel (point and face fluxes in parallel, one
+    thread per entry; run here as one host thread) performs the serial routine's
+    arithmetic in the same order: identical bits on fluid, solid and outflow cells."""
+    P = C.POINTER(C.c_double)
+    for name in ("fsi3_cell_residual_host", "fsi3_cell_residual_cta_host"):
+        getattr(host_lib, name).argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, P]
+    mesh = on.make_mesh_nd(BREAKS3, COUNTS3, BOX3)
+    mat = wl.Material()
+    U, Uo = state(mesh, seed), state(mesh, seed + 30)
+    phys = np.array([mat.rho_f, mat.nu_f, mat.rho_s, mat.mu_s, mat.lambda_s])
+    outflow = np.zeros(mesh.n_cells, dtype=bool)
+    outflow[mesh.outflow_cells] = True
+    h = np.array([0.2, 0.2, 0.055])
+    for c in range(mesh.n_cells):
+        Ue = np.ascontiguousarray(U[mesh.cell_nodes[c]])
+        Uoe = np.ascontiguousarray(Uo[mesh.cell_nodes[c]])
+        args = (ptr(phys), ptr(Ue), ptr(Uoe), ptr(h), int(mesh.cell_solid[c]), int(outflow[c]), k, theta, 3e-4)
+        R1, R2 = np.zeros(189), np.zeros(189)
+        host_lib.fsi3_cell_residual_host(*args, ptr(R1))
+        host_lib.fsi3_cell_residual_cta_host(*args, ptr(R2))
+        assert np.array_equal(R1, R2), c
