@@ -101,8 +101,8 @@ extern "C" int fsi3_mesh_host(const double* xb, const int* nxs, int nxseg, const
 }
 
 // The assembled step residual R[n_nodes][7] of one slice, computed the way the
-// kernels will: per cell (stabilisation weight, cell residual), then per row
-// (fixed-order gather or identity row). mat = {rho_f, nu_f, rho_s, mu_s,
+// kernels do: per cell (stabilisation weight, the cooperative cell residual),
+// then per row (fixed-order gather or identity row). mat = {rho_f, nu_f, rho_s, mu_s,
 // lambda_s, vbar, ramp_t, alpha0}.
 extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, const double* yb, const int* nys,
                                   int nyseg, const double* zb, const int* nzs, int nzseg, const double* box,
@@ -116,7 +116,7 @@ extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, c
   }
   const fsi3::HostMesh3 m = make_mesh(xb, nxs, nxseg, yb, nys, nyseg, zb, nzs, nzseg, box);
   const fsi3::Phys3 P{mat[0], mat[1], mat[2], mat[3], mat[4]};
-  std::vector<double> Re((size_t)m.n_cells * 27 * 7), Ue(189), Uoe(189);
+  std::vector<double> Re((size_t)m.n_cells * 27 * 7), Ue(189), Uoe(189), sh(fsi3::CR3_TOTAL);
   for (int c = 0; c < m.n_cells; ++c) {
     for (int l = 0; l < 27; ++l)
       for (int f = 0; f < 7; ++f) {
@@ -126,7 +126,11 @@ extern "C" int fsi3_residual_host(const double* xb, const int* nxs, int nxseg, c
     const double* h = &m.cell_h[(size_t)c * 3];
     const bool solid = m.cell_flags[c] & fsi3::C3_SOLID, outflow = m.cell_flags[c] & fsi3::C3_OUTFLOW;
     const double alpha = fsi3::stab_weight3(T, Uoe.data(), h, mat[7], mat[0], mat[1]);
-    fsi3::cell_residual3(P, T, Ue.data(), Uoe.data(), h, solid, outflow, k, theta, alpha, &Re[(size_t)c * 189]);
+    // the kernel's routine (cooperative), run by one host thread
+    std::copy(Ue.begin(), Ue.end(), sh.begin() + fsi3::CR3_UE);
+    std::copy(Uoe.begin(), Uoe.end(), sh.begin() + fsi3::CR3_UE + 189);
+    fsi3::cell_residual3_cta(fsi3::HostCta{}, P, T, h, solid, outflow, k, theta, alpha, sh.data(),
+                             &Re[(size_t)c * 189]);
   }
   const fsi3::Mesh3View v = view(m);
   for (int n = 0; n < m.n_nodes; ++n)
