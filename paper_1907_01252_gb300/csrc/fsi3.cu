@@ -1,7 +1,8 @@
 // 3D path of the library: hexahedral Q2 elements with 7 unknowns per node
 // (v, u, p). The theta step of Sec. 2.3 is solved by Newton's method, with
 // FGMRES preconditioned by a geometric multigrid V-cycle (block Vanka smoother,
-// Q2 transfers, dense coarsest solve), for S slices per launch (grid.y =
+// additive or over eight cell colours; Q2 transfers; a dense inverse or
+// smoother sweeps on the coarsest level), for S slices per launch (grid.y =
 // slice). On top sit the propagators F and C of Sec. 3 and the Parareal
 // iteration. Every per-entry step is a __host__ __device__ function of the 3D
 // headers, which are also run on the host against the oracle. This file holds
