@@ -2,20 +2,32 @@
 workload (83,525 dofs per state, T = 2, 64 slices x 32 fine shifted
 Crank-Nicolson steps, FP64 throughout).
 
-One step = one pass of the whole hot path: parareal_iterate with one
-iteration, i.e. the sequential coarse predictor sweep (64 implicit-Euler
-steps), the fine propagator of all 64 slices batched (32 steps of every
-slice at once: residual, Jacobian, multigrid-FGMRES Newton), the corrected
-coarse sweep and the Parareal correction. value = fine time-steps advanced
-per second (64 x 32 per step).
+The line follows one continuing Parareal run (Sec. 3). The predictor sweep
+(64 implicit-Euler steps) comes first, untimed; then one step = one Parareal
+iteration (parareal_continue): the fine propagator of every slice not yet exact,
+batched (32 steps of all those slices at once: residual, Jacobian,
+multigrid-FGMRES Newton), then the corrected coarse sweep with the correction.
+The first --warmup iterations are untimed, the next --steps are timed.
+value = fine time-steps advanced per second over the timed iterations. Each
+timed step also copies the iterate in from pinned host memory and back out,
+and the same loop gives the end-to-end figure.
+
+Against the metric's accuracy: the serial fine solution of the whole interval
+is computed first on the same GPU (timed: the serial single-slice figure), and
+every iterate's slice-boundary error against it (v, u, p, Frobenius norm, Sec.
+4.1) is reported with the iteration at which it reaches 1e-8, if it does, and
+the run time to that point. A converged run of the 16 x 4 workload (8 slices x
+16 fine steps), iterated to 1e-8, gives the time to that accuracy and the
+speed-up over the serial fine solve on a workload small enough to converge in
+the bench. The precision variants run the predictor and one iteration.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Profiling aids (not the benchmark line): --unit fine_step times one batched
-fine theta step of --slices slices of the same workload (the dominant part of
-a Parareal pass), --unit coarse_step one single-slice coarse (theta = 1) step
-as in the sequential sweep, and --kernel-table prints the per-kernel
-CUDA-event times of the last warm-up step to stderr.
+fine theta step of --slices slices of the same workload, --unit coarse_step
+one single-slice coarse (theta = 1) step as in the sequential sweep, and
+--kernel-table prints the per-kernel CUDA-event times of the last warm-up step
+to stderr.
 
 --unit batch measures the batch runner instead: the first --instances
 problems of the seeded uneven batch (meshes 64x16 .. 192x48, random solid
@@ -47,7 +59,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Parareal FSI time-steps/s, batched slices vs serial, at 1e-8 rel error"
 UNIT = "fine time-steps/s"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 x max SM clock
 # DRAM read + write bytes of one finest-level SpMV launch of 8 slices, from the ncu capture summarised in
 # profiles/fsi_spmv_128x32_ncu_full.md (451.4 MB); set to None when k_bsr_spmv changes.
 SPMV_TRAFFIC_8_SLICES = 451.4e6
@@ -56,11 +67,10 @@ SPMV_TRAFFIC_8_SLICES = 451.4e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step", "batch",
                                                            "parareal3d"])
     ap.add_argument("--instances", type=int, default=4,
@@ -68,7 +78,9 @@ def parse():
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
     ap.add_argument("--kernel-table", action="store_true")
     ap.add_argument("--no-precision-variant", action="store_true",
-                    help="skip the extra pass with the FP32 linear solver")
+                    help="skip the precision-variant runs (FP32 solver or FP32 multigrid)")
+    ap.add_argument("--no-small-converged", action="store_true",
+                    help="skip the converged Parareal run of the 16 x 4 workload")
     return ap.parse_args()
 
 
@@ -186,7 +198,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "oracle_sample": vals[0]["sample"]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -280,6 +293,372 @@ def bench_3d(args, torch, fsi, wl, dev):
     print(json.dumps(line))
 
 
+FIELDS = (("v", slice(0, 2)), ("u", slice(2, 4)), ("p", slice(4, 5)))
+
+
+def rel_errors(Ua, Ur, N):
+    """Largest relative error over the slice boundaries 1..N, per field (v, u, p),
+    each boundary's field measured in the Frobenius norm (Sec. 4.1)."""
+    A = Ua.view(N + 1, -1, 5)[1:]
+    B = Ur.view(N + 1, -1, 5)[1:]
+    out = {}
+    for name, sl in FIELDS:
+        num = (A[:, :, sl] - B[:, :, sl]).flatten(1).norm(dim=1)
+        den = B[:, :, sl].flatten(1).norm(dim=1).clamp_min(1e-300)
+        out[name] = float((num / den).max())
+    return out
+
+
+def load_peaks():
+    """HBM copy bandwidth (GB/s) measured on this machine's GPUs, or the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def fp64_peak(torch, fsi, stream):
+    """FP64 FMA throughput of this GPU in TFLOP/s, measured with the library's probe
+    kernel (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM)."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    blocks = 152 * 8
+    fsi.fp64_probe(blocks, 2000, sink)   # warm-up
+    best = 0.0
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        flops = fsi.fp64_probe(blocks, 20000, sink)
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, flops / (a.elapsed_time(b) / 1000.0) / 1e12)
+    return best
+
+
+def serial_fine(ctx, w, U, stream, torch):
+    """The serial fine solution: slice after slice, one slice per fsi_fine call, on the
+    GPU. U[0] holds the initial state; fills U[1..N]. Returns the seconds it took."""
+    N = w.n_slices
+    dt = w.T / N
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for i in range(N):
+        ctx.fsi_fine(U[i:i + 1], [i * dt], U[i + 1:i + 2])
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1000.0
+
+
+def timed(stream, torch, fn):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return out, a.elapsed_time(b) / 1000.0
+
+
+def converged_run(torch, fsi, w, dev, stream, tol=1e-8):
+    """Parareal to the metric's accuracy on a small workload: one iteration at a time
+    until the slice-boundary error against the serial fine solution is <= tol
+    (at the latest at k = N, where the iterate is the serial solution). Times the
+    whole run (predictor included) and the serial fine solve on the same GPU."""
+    N = w.n_slices
+    ctx = fsi.Context(w, max_batch=N)
+    Us = torch.zeros((N + 1, ctx.n_dofs), dtype=torch.float64, device=dev)
+    serial_fine(ctx, w, Us.clone(), stream, torch)   # warm-up (graph capture, tables)
+    t_ser = serial_fine(ctx, w, Us, stream, torch)
+    U = torch.zeros_like(Us)
+    _, t = timed(stream, torch, lambda: ctx.parareal_iterate(U, 0, 0.0))
+    errs = []
+    while True:
+        (_, st), ti = timed(stream, torch, lambda: ctx.parareal_continue(U, 1, 0.0))
+        t += ti
+        e = rel_errors(U, Us, N)
+        errs.append(max(e.values()))
+        if max(e.values()) <= tol or st["iterations"] >= N:
+            break
+    ctx.close()
+    return {"workload": w.name, "n_slices": N, "m_fine": w.m_fine, "iterations_to_1e-8": len(errs),
+            "max_rel_err_per_iteration": errs, "parareal_seconds": t, "serial_gpu_seconds": t_ser,
+            "parareal_fine_steps_per_s": N * w.m_fine / t, "serial_gpu_fine_steps_per_s": N * w.m_fine / t_ser,
+            "speedup_vs_serial": t_ser / t}
+
+
+def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
+    """The bench line: one continuing Parareal run of the 128 x 32 workload, one
+    iteration per step (see the module docstring)."""
+    w = wl.LARGE_128x32
+    N = w.n_slices
+    dt = w.T / N
+    stream = torch.cuda.current_stream(dev)
+    hbm_gbs, hbm_src = load_peaks()
+    ctx = fsi.Context(w, max_batch=N)
+    n = ctx.n_dofs
+
+    # the serial fine solution of the whole interval on the same GPU (the metric's reference)
+    Us = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
+    t_serial = serial_fine(ctx, w, Us, stream, torch)
+
+    # the run: predictor sweep, then W warm-up iterations (the last one finds the dominant kernel)
+    U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
+    _, t_pred = timed(stream, torch, lambda: ctx.parareal_iterate(U, 0, 0.0))
+    iters = []
+    saved = []
+    names = fsi.kernel_names()
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fsi.profile_enable(names)
+        S = max(0, N - len(iters))
+        (_, st), ti = timed(stream, torch, lambda: ctx.parareal_continue(U, 1, 0.0))
+        iters.append({"iteration": st["iterations"], "fine_slices": S, "seconds": ti, "timed": False,
+                      "fine_gmres": st["fine"]["gmres_iters"], "coarse_gmres": st["coarse"]["gmres_iters"]})
+        saved.append(U.clone())
+    shares = {nm: fsi.profile_read(nm)[0] for nm in names}
+    if not any(shares.values()):
+        shares["k_bsr_spmv"] = 1.0
+    dominant = max(shares, key=shares.get)
+    total_ms = sum(shares.values())
+    if args.kernel_table and rank == 0:
+        print("kernel event times of the last warm-up iteration (ms, share, launches):", file=sys.stderr)
+        for nm in sorted(shares, key=shares.get, reverse=True):
+            if shares[nm] > 0:
+                print("  %-20s %10.2f %6.2f%% %8d" % (nm, shares[nm], 100 * shares[nm] / total_ms,
+                                                   fsi.profile_read(nm)[1]), file=sys.stderr)
+    fsi.profile_enable([dominant])
+
+    # timed region: K iterations; every step copies the iterate in from pinned host
+    # memory and back out, so the same loop gives the device and the end-to-end time
+    hU = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+    hU.copy_(U)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = fsi.launch_count()
+    ev = []
+    steps_done = []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        U.copy_(hU, non_blocking=True)
+        e[1].record(stream)
+        _, st = ctx.parareal_continue(U, 1, 0.0)
+        e[2].record(stream)
+        hU.copy_(U, non_blocking=True)
+        e[3].record(stream)
+        saved.append(U.clone())
+        ev.append(e)
+        steps_done.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = fsi.launch_count() - l0
+    clk = clocks.stop()
+    dev_s = [e[1].elapsed_time(e[2]) / 1000.0 for e in ev]
+    e2e_s = [e[0].elapsed_time(e[3]) / 1000.0 for e in ev]
+    fine_units = 0
+    prev = iters[-1]["iteration"] if iters else 0
+    for st, ts in zip(steps_done, dev_s):
+        S = N - (st["iterations"] - 1) if st["iterations"] > prev else 0   # no iteration runs past N
+        prev = st["iterations"]
+        fine_units += S * w.m_fine
+        iters.append({"iteration": st["iterations"], "fine_slices": S, "seconds": ts, "timed": True,
+                      "fine_gmres": st["fine"]["gmres_iters"], "coarse_gmres": st["coarse"]["gmres_iters"]})
+    dom_ms, dom_n, dom_flops = fsi.profile_read(dominant)
+    dom_bytes = fsi.profile_read_bytes(dominant)
+    fsi.profile_enable([])
+    fp64_tflops = fp64_peak(torch, fsi, stream)   # right after the timed region, at its clocks
+    ms = 1000.0 * sum(dev_s)
+    ms, value = aggregate(ms, fine_units, dist, dev)
+    e2e_ms, e2e_value = aggregate(1000.0 * sum(e2e_s), fine_units, dist, dev)
+
+    # error of every iterate against the serial fine solution
+    t_cum = t_pred
+    reached = None
+    for rec, Ui in zip(iters, saved):
+        rec["max_rel_err_vs_serial"] = rel_errors(Ui, Us, N)
+        t_cum += rec["seconds"]
+        rec["run_seconds"] = t_cum
+        if reached is None and max(rec["max_rel_err_vs_serial"].values()) <= 1e-8:
+            reached = rec
+    best = min(iters, key=lambda r: max(r["max_rel_err_vs_serial"].values())) if iters else None
+    at_tol = {"tolerance": 1e-8, "reached": reached is not None,
+              "iterations_run": len(iters),
+              "iteration_reached": reached["iteration"] if reached else None,
+              "run_seconds_to_reach": reached["run_seconds"] if reached else None,
+              "fine_steps_per_s_at_1e-8": (N * w.m_fine / reached["run_seconds"]) if reached else None,
+              "smallest_error": best["max_rel_err_vs_serial"] if best else None,
+              "smallest_error_iteration": best["iteration"] if best else None,
+              "exact_at_iteration": N,
+              "note": "an iterate is exact (the serial fine solution) at k = N (Sec. 4.1); boundaries "
+                      "1..k are exact after iteration k"}
+    last_saved = saved[-1] if saved else U
+    del saved[1:]
+
+    # the dominant kernel's roofline over the timed region, and one isolated launch of it
+    roof = {"kernel": dominant, "share_of_kernel_time_last_warmup": shares[dominant] / total_ms if total_ms else None}
+    if dom_ms > 0 and dom_bytes > 0:
+        gbs = dom_bytes / (dom_ms / 1000.0) / 1e9
+        tfl = dom_flops / (dom_ms / 1000.0) / 1e12
+        alu_frac = tfl / fp64_tflops
+        hbm_frac = gbs / hbm_gbs
+        roof.update({"bound": "alu" if alu_frac >= hbm_frac else "hbm",
+                     "achieved": tfl if alu_frac >= hbm_frac else gbs,
+                     "peak": fp64_tflops if alu_frac >= hbm_frac else hbm_gbs,
+                     "unit": "TFLOP/s" if alu_frac >= hbm_frac else "GB/s",
+                     "frac": max(alu_frac, hbm_frac),
+                     "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": hbm_frac, "peak_source": hbm_src},
+                     "fp64": {"achieved_tflops": tfl, "peak_tflops": fp64_tflops, "frac": alu_frac,
+                              "peak_source": "measured in this run: the library's FP64 FMA probe kernel"},
+                     "timed_launches": dom_n, "algorithmic_bytes": dom_bytes, "algorithmic_flops": dom_flops,
+                     "traffic": None,
+                     "traffic_note": "the timed launches mix levels and batch sizes; the per-launch DRAM traffic "
+                                     "of the finest-level batched launch is in isolated_finest_launch"})
+    elif dom_ms > 0 and dom_flops > 0:
+        tfl = dom_flops / (dom_ms / 1000.0) / 1e12
+        roof.update({"bound": "alu", "achieved": tfl, "peak": fp64_tflops, "unit": "TFLOP/s",
+                     "frac": tfl / fp64_tflops, "traffic": None, "timed_launches": dom_n})
+    iso = None
+    if dominant == "k_bsr_spmv":
+        t_old = [i * dt for i in range(N)]
+        vals = ctx.fsi_jacobian(last_saved[1:], last_saved[:N], w.k_fine, 0.5 + w.material.theta0 * w.k_fine)
+        x = last_saved[1:].contiguous()
+        y = torch.empty_like(x)
+        ctx.fsi_bsr_spmv(vals, x, y)
+        reps = 20
+        _, ts = timed(stream, torch, lambda: [ctx.fsi_bsr_spmv(vals, x, y) for _ in range(reps)])
+        nnzb = ctx.nnzb
+        abytes = N * 8 * (25 * nnzb + 2 * n) + 4 * (nnzb + 2 * n // 5 + 1)
+        sec = ts / reps
+        iso = {"slices": N, "ms": 1000 * sec, "algorithmic_bytes": abytes, "achieved_gbs": abytes / sec / 1e9,
+               "hbm_frac": abytes / sec / 1e9 / hbm_gbs,
+               "fp64_frac": 50.0 * nnzb * N / sec / 1e12 / fp64_tflops,
+               "traffic": SPMV_TRAFFIC_8_SLICES * N / 8 if SPMV_TRAFFIC_8_SLICES else None,
+               "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 8-slice finest-level "
+                                 "launch, scaled by 8 (traffic grows with the slices)",
+               "l2": "inputs larger than L2 (3.4 GB of blocks); back-to-back launches"}
+        del vals, x, y, t_old
+    roof["isolated_finest_launch"] = iso
+
+    # precision variants (config 3): the predictor and one iteration from the same start,
+    # against the FP64 iterate after iteration 1 and the exact first boundary
+    variants = []
+    if not args.no_precision_variant and args.warmup >= 1:
+        U1_64 = saved[0]
+        tip = wl.tip_node(w)
+        desc = {1: "FP32 linear solver (FGMRES, multigrid, Vanka, operator) inside the FP64 Newton loop (Newton "
+                   "tolerance 1e-11); FP64 residual, J = det F, Parareal correction",
+                2: "FP64 FGMRES preconditioned by an FP32 multigrid V-cycle (FP32 Vanka, transfers, level "
+                   "operators); FP64 residual, J = det F, Parareal correction"}
+        for prec in (1, 2):
+            ctxv = fsi.Context(w, max_batch=N, precision=prec, **({"newton_tol": 1e-11} if prec == 1 else {}))
+            Uv = torch.zeros_like(U)
+            (_, sv), tv = timed(stream, torch, lambda: ctxv.parareal_iterate(Uv, 1, 0.0))
+            err = rel_errors(Uv, U1_64, N)
+            a = Uv.view(N + 1, -1, 5)[1:, tip, 2:4]
+            b = U1_64.view(N + 1, -1, 5)[1:, tip, 2:4]
+            err["tip_displacement"] = float(((a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-300)).max())
+            b1 = rel_errors(Uv[:2].contiguous(), Us[:2].contiguous(), 1)
+            variants.append({"precision": prec, "what": desc[prec], "step": "predictor + iteration 1",
+                             "seconds": tv, "fine_steps_per_s": N * w.m_fine / tv,
+                             "fp64_seconds_same_work": t_pred + iters[0]["seconds"],
+                             "max_rel_err_vs_fp64_iterate": err, "boundary1_rel_err_vs_fp64_serial": b1,
+                             "newton_fine": sv["fine"], "newton_coarse": sv["coarse"]})
+            ctxv.close()
+            del Uv
+
+    small = None
+    if not args.no_small_converged:
+        small = converged_run(torch, fsi, wl.SMALL_16x4, dev, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+
+    # the paper's speedup model, Eq. (eq:speedup), S = 1 / (r + (K / N)(1 + r)), with r the measured
+    # cost of one coarse slice step (the predictor sweep / N) over one serial fine slice
+    r = (t_pred / N) / (t_serial / N)
+    model = {"r": r, "K": args.steps, "N": N, "S": 1.0 / (r + (args.steps / N) * (1.0 + r)),
+             "note": "model speed-up with one processor per slice and K iterations"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "unit": "parareal", "n_dofs": n, "n_slices": N,
+                           "m_fine": w.m_fine, "m_coarse": w.m_coarse, "mg_levels": ctx.n_levels,
+                           "step": "one Parareal iteration of one continuing run (parareal_continue): batched "
+                                   "fine solves of every slice not yet exact, then the corrected coarse sweep; "
+                                   "value = fine time-steps advanced per second over the timed iterations",
+                           "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
+                           "solver": {"newton_tol": w.newton_tol, "newton_eta": w.newton_eta,
+                                      "gmres_rtol_first": w.gmres_rtol_first, "gmres_rtol": w.gmres_rtol,
+                                      "gmres_restart": w.gmres_restart},
+                           "at_1e-8": at_tol,
+                           "serial_gpu_seconds": t_serial,
+                           "serial_gpu_fine_steps_per_s": N * w.m_fine / t_serial,
+                           "batched_iterations_vs_serial_steps_per_s": value / (N * w.m_fine / t_serial),
+                           "predictor_seconds": t_pred,
+                           "iterations": iters,
+                           "paper_speedup_model": model,
+                           "converged_small_workload": small},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": hU.numel() * 8,
+                        "d2h_bytes_per_step": hU.numel() * 8,
+                        "note": "the same timed iterations, each with the iterate copied in from pinned host "
+                                "memory and back out through the public API"},
+                "clocks": clk, "precision_variants": variants, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def bench_unit(args, torch, fsi, wl, dev, dist, rank, world):
+    """Profiling aids: one batched fine theta step (--unit fine_step) or one
+    single-slice coarse step (--unit coarse_step) of the 128 x 32 workload."""
+    w = wl.LARGE_128x32
+    if args.unit == "coarse_step":
+        args.slices = 1
+    ctx = fsi.Context(w, max_batch=args.slices)
+    n = ctx.n_dofs
+    stream = torch.cuda.current_stream(dev)
+    Uf = torch.zeros((args.slices, n), dtype=torch.float64, device=dev)
+    tf = [0.0] * args.slices      # first step of the trajectory, from rest
+    kf = w.k_fine if args.unit == "fine_step" else w.k_coarse
+    th = 0.5 + w.material.theta0 * kf if args.unit == "fine_step" else 1.0
+    names = fsi.kernel_names()
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fsi.profile_enable(names)
+        ctx.fsi_theta_step(Uf, tf, kf, th)
+    torch.cuda.synchronize()
+    shares = {nm: fsi.profile_read(nm)[0] for nm in names}
+    total_ms = sum(shares.values()) or 1.0
+    fsi.profile_enable([])
+    if args.kernel_table:
+        print("kernel event times of the last warm-up step (ms, share, launches):", file=sys.stderr)
+        for nm in sorted(shares, key=shares.get, reverse=True):
+            if shares[nm] > 0:
+                print("  %-20s %10.2f %6.2f%% %8d" % (nm, shares[nm], 100 * shares[nm] / total_ms,
+                                                   fsi.profile_read(nm)[1]), file=sys.stderr)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    l0 = fsi.launch_count()
+    _, sec = timed(stream, torch, lambda: [ctx.fsi_theta_step(Uf, tf, kf, th) for _ in range(args.steps)])
+    clk = clocks.stop()
+    value = args.slices * args.steps / sec
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": w.name, "unit": args.unit, "slices": args.slices},
+                      "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+                      "gpu_launches": fsi.launch_count() - l0}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -298,202 +677,13 @@ def main():
     dev = torch.device("cuda", local)
     build.build_library()
     if args.unit == "batch":
-        return bench_batch(args, torch, fsi, wl, dev)
-    if args.unit == "parareal3d":
-        return bench_3d(args, torch, fsi, wl, dev)
-    w = wl.LARGE_128x32
-    N = w.n_slices
-    fine_unit = args.unit in ("fine_step", "coarse_step")
-    if args.unit == "coarse_step":
-        args.slices = 1
-    ctx = fsi.Context(w, max_batch=args.slices if fine_unit else N)
-    n = ctx.n_dofs
-    U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    if fine_unit:
-        Uf = torch.zeros((args.slices, n), dtype=torch.float64, device=dev)
-        tf = [0.0] * args.slices      # first step of the trajectory, from rest
-        kf = w.k_fine if args.unit == "fine_step" else w.k_coarse
-        th = 0.5 + w.material.theta0 * kf if args.unit == "fine_step" else 1.0
-
-        def step():
-            _, st = ctx.fsi_theta_step(Uf, tf, kf, th)
-            return {"fine": st, "coarse": {}}
+        bench_batch(args, torch, fsi, wl, dev)
+    elif args.unit == "parareal3d":
+        bench_3d(args, torch, fsi, wl, dev)
+    elif args.unit in ("fine_step", "coarse_step"):
+        bench_unit(args, torch, fsi, wl, dev, dist, rank, world)
     else:
-        def step():
-            U[1:].zero_()
-            _, st = ctx.parareal_iterate(U, 1, 0.0)
-            return st
-
-    # warm-up; the last warm-up step also finds the dominant kernel
-    names = fsi.kernel_names()
-    for i in range(args.warmup):
-        if i == args.warmup - 1:
-            fsi.profile_enable(names)
-        st = step()
-    torch.cuda.synchronize()
-    shares = {nm: fsi.profile_read(nm)[0] for nm in names}
-    if not any(shares.values()):
-        shares["k_bsr_spmv"] = 1.0
-    dominant = max(shares, key=shares.get)
-    total_ms = sum(shares.values())
-    if args.kernel_table and rank == 0:
-        print("kernel event times of the last warm-up step (ms, share, launches):", file=sys.stderr)
-        for nm in sorted(shares, key=shares.get, reverse=True):
-            if shares[nm] > 0:
-                print("  %-20s %10.2f %6.2f%% %8d" % (nm, shares[nm], 100 * shares[nm] / total_ms,
-                                                   fsi.profile_read(nm)[1]), file=sys.stderr)
-    fsi.profile_enable([dominant])
-
-    # timed region
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = fsi.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        st = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches = fsi.launch_count() - l0
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    dom_ms, dom_n, dom_flops = fsi.profile_read(dominant)
-    fsi.profile_enable([])
-    per_step = args.slices if fine_unit else N * w.m_fine
-    ms, value = aggregate(ms, per_step * args.steps, dist, dev)
-
-    # serial single-slice reference on the same GPU (a few fine steps of slice 1)
-    Us = U[1:2].clone()
-    torch.cuda.synchronize()
-    s0 = time.perf_counter()
-    nser = 0 if fine_unit else 4
-    t0 = w.T / N
-    cur = Us
-    for j in range(nser):
-        cur, _ = ctx.fsi_theta_step(cur, [t0 + j * w.k_fine], w.k_fine, 0.5 + w.material.theta0 * w.k_fine)
-    torch.cuda.synchronize()
-    serial_rate = nser / (time.perf_counter() - s0) if nser else None
-
-    # the paper's speedup model, Eq. (eq:speedup), S = 1 / (r + (K / N)(1 + r)), with r the measured
-    # cost of one coarse slice step over one serial fine slice (m_fine single-slice fine steps)
-    model = None
-    if serial_rate:
-        ncs = 3
-        torch.cuda.synchronize()
-        s0 = time.perf_counter()
-        cur = Us
-        for j in range(ncs):
-            cur, _ = ctx.fsi_theta_step(cur, [t0 + j * w.k_coarse], w.k_coarse, 1.0)
-        torch.cuda.synchronize()
-        t_coarse = (time.perf_counter() - s0) / ncs
-        t_fine_slice = w.m_fine / serial_rate
-        r = t_coarse / t_fine_slice
-        model = {"r": r, "K": 1, "N": N, "S": 1.0 / (r + (1.0 / N) * (1.0 + r)),
-                 "coarse_step_s": t_coarse, "serial_fine_slice_s": t_fine_slice,
-                 "note": "model speedup with one processor per slice; the measured batched/serial ratio is "
-                         "the pass's speedup over the serial fine solve on the same GPU"}
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e and not fine_unit:
-        h_in = torch.zeros((1, n), dtype=torch.float64).pin_memory()
-        h_out = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(args.steps):
-            U[0:1].copy_(h_in, non_blocking=True)
-            U[1:].zero_()
-            ctx.parareal_iterate(U, 1, 0.0)
-            h_out.copy_(U, non_blocking=True)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        e2e = {"value": N * w.m_fine * args.steps / (ems / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": h_in.numel() * 8, "d2h_bytes_per_step": h_out.numel() * 8}
-
-    # precision variants on the same Parareal pass (one warm-up pass each), with
-    # their relative error against the FP64 pass just run (U holds its result)
-    variants = []
-    if not args.no_precision_variant and not fine_unit:
-        U64 = U.clone().view(N + 1, -1, 5)
-        tip = wl.tip_node(w)
-        desc = {1: "FP32 linear solver (FGMRES, multigrid, Vanka, operator) inside the FP64 Newton loop (Newton "
-                   "tolerance 1e-11); "
-                   "FP64 residual, J = det F, Parareal correction",
-                2: "FP64 FGMRES preconditioned by an FP32 multigrid V-cycle (FP32 Vanka, transfers, level "
-                   "operators); FP64 residual, J = det F, Parareal correction"}
-        for prec in (1, 2):
-            # the FP32 solver meets the 1e-8 target at a Newton tolerance of 1e-11 (1e-10 leaves ~7e-8)
-            ctxv = fsi.Context(w, max_batch=N, precision=prec, **({"newton_tol": 1e-11} if prec == 1 else {}))
-
-            def stepv():
-                U[1:].zero_()
-                _, sv = ctxv.parareal_iterate(U, 1, 0.0)
-                return sv
-            stepv()
-            torch.cuda.synchronize()
-            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            for _ in range(args.steps):
-                sv = stepv()
-            b1.record(stream)
-            torch.cuda.synchronize()
-            vms = b0.elapsed_time(b1)
-            Uv = U.view(N + 1, -1, 5)
-            err = {}
-            for name, sl in (("v", slice(0, 2)), ("u", slice(2, 4)), ("p", slice(4, 5))):
-                num = (Uv[1:, :, sl] - U64[1:, :, sl]).flatten(1).norm(dim=1)
-                den = U64[1:, :, sl].flatten(1).norm(dim=1)
-                err[name] = float((num / den).max())
-            tnum = (Uv[1:, tip, 2:4] - U64[1:, tip, 2:4]).norm(dim=1)
-            tden = U64[1:, tip, 2:4].norm(dim=1)
-            err["tip_displacement"] = float((tnum / tden).max())
-            variants.append({"precision": prec, "what": desc[prec],
-                             "value": N * w.m_fine * args.steps / (vms / 1000.0), "unit": UNIT,
-                             "ms_per_step": vms / args.steps, "max_rel_err_vs_fp64_pass": err,
-                             "newton_fine": sv["fine"], "newton_coarse": sv["coarse"]})
-            del ctxv
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample()
-
-    achieved = dom_flops / (dom_ms / 1000.0) / 1e12 if dom_ms > 0 and dom_flops > 0 else None
-    roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": (SPMV_TRAFFIC_8_SLICES * N / 8 if dominant == "k_bsr_spmv" and SPMV_TRAFFIC_8_SLICES
-                            else None),
-                "traffic_note": "DRAM bytes of one finest-level launch over the full batch, scaled from an 8-slice "
-                                "ncu capture (algorithmic 433 MB per 8 slices, ratio 1.04)", "share_of_kernel_time": shares[dominant] / total_ms if total_ms else None,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "fsi2d_q2_128x32_T2_64x32", "unit": args.unit, "n_dofs": n, "n_slices": N,
-                           "m_fine": w.m_fine, "m_coarse": w.m_coarse, "mg_levels": ctx.n_levels,
-                           "step": "parareal_iterate with 1 iteration: coarse predictor sweep + batched fine "
-                                   "sweep of all slices + corrected coarse sweep",
-                           "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
-                           "solver": {"newton_tol": w.newton_tol, "newton_eta": w.newton_eta,
-                                      "gmres_rtol_first": w.gmres_rtol_first, "gmres_rtol": w.gmres_rtol,
-                                      "gmres_restart": w.gmres_restart},
-                           "serial_gpu_fine_steps_per_s": serial_rate,
-                           "batched_vs_serial": value / serial_rate if serial_rate else None,
-                           "paper_speedup_model": model,
-                           "newton_fine": st["fine"], "newton_coarse": st["coarse"]},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "precision_variants": variants,
-                "gpu_launches": launches}
-        print(json.dumps(line))
+        bench_parareal(args, torch, fsi, wl, dev, dist, rank, world)
     if dist:
         dist.destroy_process_group()
 

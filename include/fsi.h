@@ -238,6 +238,24 @@ int fsi_coarse(fsi_ctx* ctx, int S, const double* U0, const double* t0, double* 
 int parareal_iterate(fsi_ctx* ctx, double* U, int max_iter, double tol,
                      fsi_parareal_stats* stats, void* stream);
 
+/* Continue the context's Parareal run (Sec. 3, Eq. (parareal:iteration)) by up
+ * to n_iter further iterations, numbered on from the run's last completed one:
+ * parareal_iterate(U, a) followed by parareal_continue(U, b) computes the same
+ * bits as parareal_iterate(U, a + b) (the same tol stops either early).
+ * parareal_iterate with max_iter = 0 runs only the predictor sweep, so
+ * successive parareal_continue(U, 1) calls step a run one iteration at a time.
+ * U: device [n_slices + 1][n_dofs], the U the previous call of the run returned
+ * (it may have been copied to the host and back in between, but not changed);
+ * the context keeps the coarse values of the last sweep. Iterations always use
+ * the serial schedule (results are identical to the pipelined one). No
+ * iteration runs past n_slices (the iterate is then the serial fine solution).
+ * stats->iterations is the run's iteration count after the call; the other
+ * counts and history rows cover this call's iterations. Errors: FSI_EINVAL when
+ * the context has no completed run (none yet, or its last Parareal call
+ * failed), and as parareal_iterate; a failed call ends the run. */
+int parareal_continue(fsi_ctx* ctx, double* U, int n_iter, double tol,
+                      fsi_parareal_stats* stats, void* stream);
+
 /* Jacobian of the same step residual with respect to the old state U_{n-1}
  * (Sec. 2.3: U_{n-1} enters the ALE mass term, the (1 - theta) terms, the
  * kinematic and harmonic rows and, through the cell-mean velocity, the
@@ -439,6 +457,21 @@ int fsi_batch_autotune(fsi_instance* inst, int n, const int* candidates, int n_c
 int fsi_profile_enable(unsigned long long kernel_mask);
 int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
                      double* total_flops);   /* algorithmic FP64 flops of the timed launches (0 if not counted) */
+/* Algorithmic DRAM bytes the library attributes to the timed launches of a
+ * kernel since fsi_profile_enable (the data each launch must move at least
+ * once: for the block-sparse product the blocks, the input and output vectors
+ * of every active slice and, once per launch, the index arrays); 0 for
+ * kernels without a byte count. Errors: FSI_EINVAL. */
+int fsi_profile_read_bytes(int kernel_id, double* total_bytes);
+
+/* FP64 FMA throughput probe (the paper has no counterpart; it measures the
+ * FP64 peak that the FP64 kernels' rooflines divide by): launches `blocks`
+ * CTAs of 256 threads on `stream`, each thread running eight independent FMA
+ * chains of `iters` steps, i.e. blocks * 256 * iters * 16 flops. sink: device
+ * pointer to one double (written only in a case no input reaches). The caller
+ * times the launch with events on the same stream. Errors: FSI_EINVAL, FSI_ECUDA. */
+int fsi_fp64_probe(int blocks, int iters, double seed, double* sink, void* stream);
+
 long long fsi_launch_count(int kernel_id);
 int fsi_kernel_count(void);
 const char* fsi_kernel_name(int kernel_id);

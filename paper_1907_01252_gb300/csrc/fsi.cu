@@ -340,19 +340,22 @@ struct Profiler {
   std::vector<int> rec_id;
   std::vector<size_t> rec_ev;   // first of the record's two pool events
   std::vector<double> rec_work;
+  std::vector<double> rec_bytes;
   // launches replayed inside CUDA graphs: summed after every replay
-  double gms[KI_COUNT] = {}, gwork[KI_COUNT] = {};
+  double gms[KI_COUNT] = {}, gwork[KI_COUNT] = {}, gbytes[KI_COUNT] = {};
   long long gcnt[KI_COUNT] = {};
   std::atomic<unsigned> epoch{1};   // bumped by fsi_profile_enable: graphs captured earlier are re-captured
 };
 Profiler g_prof;
 thread_local double g_pending_work = 0.0;   // algorithmic flops of the launch being issued
+thread_local double g_pending_bytes = 0.0;  // algorithmic DRAM bytes of the launch being issued
 
 // A timed launch recorded while a CUDA graph is being captured.
 struct CapRec {
   int id;
   size_t ev;
   double work_per_slice;
+  double bytes_per_slice;
 };
 struct Capture {
   bool on = false;
@@ -410,11 +413,13 @@ inline void prof_post(int id, size_t ev, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
   prof_record(g_prof.pool[ev + 1], st);
   if (g_cap.on) {
-    g_cap.recs.push_back({id, ev, g_pending_work / std::max(1, g_cap.n_act)});
+    g_cap.recs.push_back({id, ev, g_pending_work / std::max(1, g_cap.n_act),
+                          g_pending_bytes / std::max(1, g_cap.n_act)});
   } else {
     g_prof.rec_id.push_back(id);
     g_prof.rec_ev.push_back(ev);
     g_prof.rec_work.push_back(g_pending_work);
+    g_prof.rec_bytes.push_back(g_pending_bytes);
   }
 }
 
@@ -424,6 +429,15 @@ inline void prof_post(int id, size_t ev, cudaStream_t st) {
     g_pending_work = (work);                                 \
     LAUNCH(id, kern, grid, block, smem, st, __VA_ARGS__);    \
     g_pending_work = 0.0;                                    \
+  } while (0)
+
+// LAUNCH_WB records the flops and the algorithmic DRAM bytes (the data the
+// launch must move at least once) of the launch.
+#define LAUNCH_WB(work, bytes, id, kern, grid, block, smem, st, ...) \
+  do {                                                               \
+    g_pending_bytes = (bytes);                                       \
+    LAUNCH_W(work, id, kern, grid, block, smem, st, __VA_ARGS__);    \
+    g_pending_bytes = 0.0;                                           \
   } while (0)
 
 #define LAUNCH(id, kern, grid, block, smem, st, ...) \
@@ -469,6 +483,7 @@ struct fsi_ctx {
   // Parareal workspace
   double *Cold = nullptr, *Fv = nullptr, *Cnew = nullptr, *ppart = nullptr;
   int red_blocks = 0;
+  int pr_iter = -1;     // last completed iteration of the context's Parareal run (-1: none to continue)
   // pipelined Parareal: the sweeps run in a single-slice context of the same
   // mesh on their own stream; Uin holds the fine inputs of two iterations
   std::vector<double> mesh_xb, mesh_yb;
@@ -706,7 +721,10 @@ int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act
     nrows = L.h.n_nodes;
   }
   const double blocks = nrows == L.h.n_nodes ? (double)L.h.nnzb : (double)L.h.nnzb * nrows / L.h.n_nodes;
-  LAUNCH_W(50.0 * blocks * (double)g_nact, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
+  // per active slice: the blocks, x, y (and b); once per launch: the row list, row pointers and column indices
+  const double bytes = (double)g_nact * sizeof(T) * (25.0 * blocks + (double)L.n + (RES ? 10.0 : 5.0) * nrows) +
+                       4.0 * (blocks + 2.0 * nrows + 1.0);
+  LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
   return launch_check();
 }
 
@@ -996,6 +1014,7 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
           }
           g_prof.gms[r.id] += e;
           g_prof.gwork[r.id] += r.work_per_slice * c->n_act;
+          g_prof.gbytes[r.id] += r.bytes_per_slice * c->n_act;
           g_prof.gcnt[r.id] += 1;
         }
       }
@@ -1384,6 +1403,8 @@ constexpr int kNaMaxSlices = 256;
 constexpr size_t kNaCellOffset = 32 + kNaMaxSlices;     // 2304 bytes: 256-byte aligned
 static __device__ __align__(256) double g_na_scratch[kNaDoubles];
 
+namespace {
+
 constexpr int kNaMaxDevices = 64;
 double* g_na_ptr[kNaMaxDevices] = {};
 std::mutex g_na_mutex;
@@ -1403,6 +1424,8 @@ int na_scratch(double** out) {
   *out = g_na_ptr[dev];
   return FSI_OK;
 }
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -1432,51 +1455,107 @@ int correct_slice(fsi_ctx* c, int i, const double* Cn, double* U, double inc[3],
   return FSI_OK;
 }
 
-void record_iteration(fsi_parareal_stats& loc, int it, const double inc[3]) {
+// slot: the iteration's index among those of the current call (history row)
+void record_iteration(fsi_parareal_stats& loc, int it, const double inc[3], int slot) {
   loc.increment_v = inc[0];
   loc.increment_u = inc[1];
   loc.increment_p = inc[2];
-  if (loc.history && it - 1 < loc.history_len)
-    for (int f = 0; f < 3; ++f) loc.history[(it - 1) * 3 + f] = inc[f];
+  if (loc.history && slot < loc.history_len)
+    for (int f = 0; f < 3; ++f) loc.history[slot * 3 + f] = inc[f];
   loc.iterations = it;
+}
+
+// Parareal workspace, allocated on first use, all or nothing: Cold and Fv
+// [N][n], Cnew [n], and the per-block partial sums of the increments.
+int parareal_workspace(fsi_ctx* c) {
+  if (c->Cold) return FSI_OK;
+  const size_t N = (size_t)c->prm.n_slices, n = c->n;
+  const int nrb = 152;
+  double *cold = nullptr, *fv = nullptr, *cnew = nullptr, *ppart = nullptr;
+  std::vector<void*> got;
+  if (dalloc(got, &cold, N * n) || dalloc(got, &fv, N * n) || dalloc(got, &cnew, n) ||
+      dalloc(got, &ppart, (size_t)nrb * 6)) {
+    for (void* p : got) cudaFree(p);
+    return FSI_ENOMEM;
+  }
+  c->owned.insert(c->owned.end(), got.begin(), got.end());
+  c->red_blocks = nrb;
+  c->Fv = fv;
+  c->Cnew = cnew;
+  c->ppart = ppart;
+  c->Cold = cold;   // last: a non-null Cold means the whole workspace exists
+  return FSI_OK;
+}
+
+// The predictor sweep U[i+1] = C(U[i]) (iteration 0); keeps C(U[i]) in Cold.
+int parareal_predictor(fsi_ctx* c, double* U, fsi_parareal_stats& loc, cudaStream_t st) {
+  const int N = c->prm.n_slices;
+  const size_t n = c->n;
+  const double dt = c->prm.T / N;
+  for (int i = 0; i < N; ++i) {
+    const double t = i * dt;
+    TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t, c->Cold + (size_t)i * n, false, &loc.coarse, st));
+    CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    loc.coarse_steps += c->prm.m_coarse;
+  }
+  return FSI_OK;
+}
+
+// Iteration it >= 1 of the run: the fine solves of every slice not yet exact
+// (slices it-1 .. N-1, batched), then the corrected coarse sweep with the
+// correction of each slice; inc receives the iteration's largest relative
+// boundary increments of v, u and p.
+int parareal_one(fsi_ctx* c, double* U, int it, fsi_parareal_stats& loc, double inc[3], cudaStream_t st) {
+  const int N = c->prm.n_slices;
+  const size_t n = c->n;
+  const double dt = c->prm.T / N;
+  const int first = it - 1;
+  const int S = N - first;
+  std::vector<double> t(S);
+  for (int i = 0; i < S; ++i) t[i] = (first + i) * dt;
+  TRY(propagate_chunked(c, S, U + (size_t)first * n, t.data(), c->Fv + (size_t)first * n, true, &loc.fine, st));
+  loc.fine_steps += (long long)S * c->prm.m_fine;
+  inc[0] = inc[1] = inc[2] = 0.0;
+  for (int i = first; i < N; ++i) {
+    const double* Cn;
+    if (i == first) {
+      Cn = c->Cold + (size_t)i * n;   // unchanged input: C(U_i^it) - C(U_i^(it-1)) = 0 exactly
+    } else {
+      const double ti = i * dt;
+      TRY(propagate_chunked(c, 1, U + (size_t)i * n, &ti, c->Cnew, false, &loc.coarse, st));
+      loc.coarse_steps += c->prm.m_coarse;
+      Cn = c->Cnew;
+    }
+    TRY(correct_slice(c, i, Cn, U, inc, st));
+    if (i != first)
+      CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  return FSI_OK;
+}
+
+// Iterations it0 .. min(it_end, N) of the serial schedule; stops early once
+// the largest increment is <= tol. c->pr_iter follows the completed iterations.
+int parareal_iterations(fsi_ctx* c, double* U, int it0, int it_end, double tol, fsi_parareal_stats& loc,
+                        cudaStream_t st) {
+  const int N = c->prm.n_slices;
+  for (int it = it0; it <= it_end && it <= N; ++it) {
+    double inc[3];
+    c->pr_iter = -1;   // Cold and U are mid-update until the iteration completes
+    TRY(parareal_one(c, U, it, loc, inc, st));
+    c->pr_iter = it;
+    record_iteration(loc, it, inc, it - it0);
+    if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
+  }
+  return FSI_OK;
 }
 
 // The predictor sweep, then per iteration the fine solves of every slice not
 // yet exact (batched) followed by the corrected coarse sweep.
 int parareal_serial(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parareal_stats& loc, cudaStream_t st) {
-  const int N = c->prm.n_slices;
-  const size_t n = c->n;
-  const double dt = c->prm.T / N;
-  std::vector<double> t(N);
-  for (int i = 0; i < N; ++i) t[i] = i * dt;
-  for (int i = 0; i < N; ++i) {
-    TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cold + (size_t)i * n, false, &loc.coarse, st));
-    CK(cudaMemcpyAsync(U + (size_t)(i + 1) * n, c->Cold + (size_t)i * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    loc.coarse_steps += c->prm.m_coarse;
-  }
-  for (int it = 1; it <= max_iter && it <= N; ++it) {
-    const int first = it - 1;
-    const int S = N - first;
-    TRY(propagate_chunked(c, S, U + (size_t)first * n, &t[first], c->Fv + (size_t)first * n, true, &loc.fine, st));
-    loc.fine_steps += (long long)S * c->prm.m_fine;
-    double inc[3] = {0, 0, 0};
-    for (int i = first; i < N; ++i) {
-      const double* Cn;
-      if (i == first) {
-        Cn = c->Cold + (size_t)i * n;   // unchanged input: C(U_i^it) - C(U_i^(it-1)) = 0 exactly
-      } else {
-        TRY(propagate_chunked(c, 1, U + (size_t)i * n, &t[i], c->Cnew, false, &loc.coarse, st));
-        loc.coarse_steps += c->prm.m_coarse;
-        Cn = c->Cnew;
-      }
-      TRY(correct_slice(c, i, Cn, U, inc, st));
-      if (i != first)
-        CK(cudaMemcpyAsync(c->Cold + (size_t)i * n, c->Cnew, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-    record_iteration(loc, it, inc);
-    if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol) break;
-  }
-  return FSI_OK;
+  c->pr_iter = -1;
+  TRY(parareal_predictor(c, U, loc, st));
+  c->pr_iter = 0;
+  return parareal_iterations(c, U, 1, max_iter, tol, loc, st);
 }
 
 // Pipelined Parareal (the paper's implementation of Sec. 3 starts a slice's
@@ -1584,7 +1663,7 @@ int parareal_pipelined(fsi_ctx* c, double* U, int max_iter, double tol, fsi_para
                                cudaMemcpyDeviceToDevice, ss));
           CK(cudaStreamSynchronize(ss));
         }
-        record_iteration(loc, it, inc);
+        record_iteration(loc, it, inc, it - 1);
         std::lock_guard<std::mutex> lk(mu);
         if (std::max(inc[0], std::max(inc[1], inc[2])) <= tol || it == K) {
           stop = true;
@@ -1904,24 +1983,46 @@ int parareal_iterate(fsi_ctx* c, double* U, int max_iter, double tol, fsi_parare
   if (max_iter < 0) return fail(FSI_EINVAL, "negative iteration count");
   cudaStream_t st = (cudaStream_t)stream;
   const int N = c->prm.n_slices;
-  const size_t n = c->n;
   fsi_parareal_stats loc{};
   if (stats) {
     loc.history = stats->history;
     loc.history_len = stats->history_len;
   }
-  if (!c->Cold) {
-    c->red_blocks = 152;
-    if (dalloc(c->owned, &c->Cold, (size_t)N * n) || dalloc(c->owned, &c->Fv, (size_t)N * n) ||
-        dalloc(c->owned, &c->Cnew, n) || dalloc(c->owned, &c->ppart, (size_t)c->red_blocks * 6))
-      return FSI_ENOMEM;
-  }
+  TRY(parareal_workspace(c));
   int rc;
-  if (c->prm.pipeline_chunk > 0 && max_iter > 0 && N > 1)
+  c->pr_iter = -1;
+  if (c->prm.pipeline_chunk > 0 && max_iter > 0 && N > 1) {
     rc = parareal_pipelined(c, U, max_iter, tol, loc, st);
-  else
+    if (rc == FSI_OK) c->pr_iter = loc.iterations;
+  } else {
     rc = parareal_serial(c, U, max_iter, tol, loc, st);
-  if (rc != FSI_OK) return rc;
+  }
+  if (rc != FSI_OK) {
+    c->pr_iter = -1;
+    return rc;
+  }
+  if (stats) *stats = loc;
+  return FSI_OK;
+}
+
+int parareal_continue(fsi_ctx* c, double* U, int n_iter, double tol, fsi_parareal_stats* stats, void* stream) {
+  if (!c || !U) return fail(FSI_EINVAL, "null argument");
+  if (n_iter < 0) return fail(FSI_EINVAL, "negative iteration count");
+  if (c->pr_iter < 0 || !c->Cold)
+    return fail(FSI_EINVAL, "parareal_continue: no completed Parareal run to continue on this context");
+  cudaStream_t st = (cudaStream_t)stream;
+  fsi_parareal_stats loc{};
+  if (stats) {
+    loc.history = stats->history;
+    loc.history_len = stats->history_len;
+  }
+  loc.iterations = c->pr_iter;
+  const int it0 = c->pr_iter + 1;
+  const int rc = parareal_iterations(c, U, it0, c->pr_iter + n_iter, tol, loc, st);
+  if (rc != FSI_OK) {
+    c->pr_iter = -1;
+    return rc;
+  }
   if (stats) *stats = loc;
   return FSI_OK;
 }
@@ -1933,7 +2034,8 @@ int fsi_profile_enable(unsigned long long kernel_mask) {
   g_prof.rec_id.clear();
   g_prof.rec_ev.clear();
   g_prof.rec_work.clear();
-  for (int i = 0; i < KI_COUNT; ++i) g_prof.gms[i] = g_prof.gwork[i] = 0.0, g_prof.gcnt[i] = 0;
+  g_prof.rec_bytes.clear();
+  for (int i = 0; i < KI_COUNT; ++i) g_prof.gms[i] = g_prof.gwork[i] = g_prof.gbytes[i] = 0.0, g_prof.gcnt[i] = 0;
   ++g_prof.epoch;
   return FSI_OK;
 }
@@ -1958,6 +2060,22 @@ int fsi_profile_read(int kernel_id, double* total_ms, long long* timed_launches,
   *timed_launches = cnt + g_prof.gcnt[kernel_id];
   *total_flops = work + g_prof.gwork[kernel_id];
   return FSI_OK;
+}
+
+int fsi_profile_read_bytes(int kernel_id, double* total_bytes) {
+  if (kernel_id < 0 || kernel_id >= KI_COUNT || !total_bytes) return fail(FSI_EINVAL, "bad kernel id or null output");
+  double b = 0.0;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (size_t r = 0; r < g_prof.rec_id.size(); ++r)
+    if (g_prof.rec_id[r] == kernel_id) b += g_prof.rec_bytes[r];
+  *total_bytes = b + g_prof.gbytes[kernel_id];
+  return FSI_OK;
+}
+
+int fsi_fp64_probe(int blocks, int iters, double seed, double* sink, void* stream) {
+  if (blocks < 1 || iters < 1 || !sink) return fail(FSI_EINVAL, "fsi_fp64_probe: bad size or null sink");
+  k_fma_probe<<<blocks, FMA_PROBE_THREADS, 0, (cudaStream_t)stream>>>(iters, seed, sink);
+  return launch_check();
 }
 
 long long fsi_launch_count(int kernel_id) {

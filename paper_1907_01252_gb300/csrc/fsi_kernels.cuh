@@ -1311,3 +1311,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_parareal_correct(int n, const d
     partial[blockIdx.x * 6 + tid] = v;
   }
 }
+
+// FP64 FMA throughput probe (the denominator of the FP64 rooflines, measured
+// on the device in use): every thread runs eight independent FMA chains of
+// `iters` steps, 16 * iters flops per thread. The result is written only when
+// it equals a value no input produces, so the chains cannot be optimised away.
+constexpr int FMA_PROBE_THREADS = 256;
+__global__ void __launch_bounds__(FMA_PROBE_THREADS) k_fma_probe(int iters, double seed, double* sink) {
+  const double m = 1.0 + 1e-15, b = 1e-17;
+  double a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+#pragma unroll 8
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, b);
+    a1 = fma(a1, m, b);
+    a2 = fma(a2, m, b);
+    a3 = fma(a3, m, b);
+    a4 = fma(a4, m, b);
+    a5 = fma(a5, m, b);
+    a6 = fma(a6, m, b);
+    a7 = fma(a7, m, b);
+  }
+  const double sum = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+  if (sum == -seed - 1e300) sink[0] = sum;
+}

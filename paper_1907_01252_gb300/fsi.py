@@ -98,6 +98,7 @@ SIGNATURES = {
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "parareal_iterate": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
+    "parareal_continue": (_I, [_VP, _VP, _I, _D, C.POINTER(fsi_parareal_stats), _VP]),
     "fsi_dense_invert": (_I, [_I, _I, _VP, _VP, _I, _VP]),
     "fsi_mesh_size": (_I, [C.POINTER(fsi_mesh), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "fsi3d_mesh_size": (_I, [C.POINTER(fsi_mesh3d), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
@@ -126,6 +127,8 @@ SIGNATURES = {
     "fsi3_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong)]),
     "fsi_profile_enable": (_I, [C.c_ulonglong]),
     "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
+    "fsi_profile_read_bytes": (_I, [_I, C.POINTER(_D)]),
+    "fsi_fp64_probe": (_I, [_I, _I, _D, _VP, _VP]),
     "fsi_launch_count": (C.c_longlong, [_I]),
     "fsi_kernel_count": (_I, []),
     "fsi_kernel_name": (C.c_char_p, [_I]),
@@ -153,6 +156,20 @@ def profile_read(name):
     ms, cnt, fl = C.c_double(), C.c_longlong(), C.c_double()
     _check(lib.fsi_profile_read(kernel_names().index(name), C.byref(ms), C.byref(cnt), C.byref(fl)))
     return ms.value, cnt.value, fl.value
+
+
+def profile_read_bytes(name):
+    """Algorithmic DRAM bytes of a kernel's timed launches since profile_enable."""
+    lib = load_library()
+    b = C.c_double()
+    _check(lib.fsi_profile_read_bytes(kernel_names().index(name), C.byref(b)))
+    return b.value
+
+
+def fp64_probe(blocks, iters, sink, seed=1.0):
+    """Launch the FP64 FMA probe on the current stream (blocks * 256 * iters * 16 flops)."""
+    _check(load_library().fsi_fp64_probe(blocks, iters, seed, _ptr(sink), _stream()))
+    return blocks * 256 * iters * 16
 
 
 def launch_count(name=None):
@@ -397,6 +414,20 @@ class Context:
         d = st.as_dict()
         if history:
             d["history"] = hist[:d["iterations"]].tolist()
+        return U, d
+
+    def parareal_continue(self, U, n_iter, tol, history=False):
+        """Up to n_iter more iterations of the context's run on U (in place); the
+        stats' iteration count is the run's, the other counts this call's."""
+        st = fsi_parareal_stats()
+        hist = np.zeros((max(n_iter, 1), 3)) if history else None
+        if history:
+            st.history = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.history_len = n_iter
+        _check(self.lib.parareal_continue(self.handle, _ptr(U), n_iter, tol, C.byref(st), _stream()))
+        d = st.as_dict()
+        if history:
+            d["history"] = hist[:max(0, min(n_iter, d["iterations"]))].tolist()
         return U, d
 
 

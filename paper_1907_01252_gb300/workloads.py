@@ -224,3 +224,46 @@ def random_state(n_nodes, seed, v_scale=1.0, u_scale=2e-3, p_scale=100.0):
     U[:, 2:4] = u_scale * rng.uniform(-1.0, 1.0, (n_nodes, 2))
     U[:, 4] = p_scale * rng.uniform(-1.0, 1.0, n_nodes)
     return U
+
+
+def developed_state(w, t, seed, bend=2e-3):
+    """Seeded smooth nodal state [n_nodes, 5] resembling a developed flow at time t:
+    the ramped parabolic inflow profile carried through the channel and slowed
+    near the bar, a bending displacement of the bar (u_x growing with height,
+    fading into the fluid), a linear pressure drop, plus low-frequency seeded
+    perturbations of every field. Inputs only: no discrete equation is solved."""
+    rng = np.random.default_rng(seed)
+    xn, yn = node_axis(X_BREAKS, w.nx_seg), node_axis(Y_BREAKS, w.ny_seg)
+    X, Y = np.meshgrid(xn, yn)          # node (i, j) at [j, i]: id j * len(xn) + i
+    H = Y_BREAKS[-1]
+    m = w.material
+    s = 0.5 * (1.0 - math.cos(math.pi * t / m.ramp_t)) if t < m.ramp_t else 1.0
+    (x0, x1), (y0, y1) = SOLID_BOX
+    xc = 0.5 * (x0 + x1)
+    # distance-like weight to the bar (0 inside), used to fade the fields
+    dx = np.maximum(np.maximum(x0 - X, X - x1), 0.0)
+    dy = np.maximum(Y - y1, 0.0)
+    dist = np.hypot(dx, dy)
+    near = np.exp(-dist / 0.05)
+    inside = (X >= x0 - 1e-12) & (X <= x1 + 1e-12) & (Y <= y1 + 1e-12)
+
+    def mode(scale):
+        a = rng.uniform(-1.0, 1.0, (3, 3))
+        f = np.zeros_like(X)
+        for p in range(3):
+            for q in range(3):
+                f += a[p, q] * np.sin((p + 1) * math.pi * X / 2.0) * np.sin((q + 1) * math.pi * Y / H)
+        return scale * f
+
+    U = np.zeros(X.shape + (5,))
+    prof = 1.5 * m.vbar * s * 4.0 * Y * (H - Y) / H ** 2
+    U[..., 0] = prof * (1.0 - near) + mode(0.05 * s)
+    U[..., 1] = -0.3 * prof * near * np.sign(X - xc) + mode(0.02 * s)
+    U[..., 2] = bend * (np.minimum(Y, y1) / y1) ** 2 * np.where(inside, 1.0, near) + mode(bend * 0.05)
+    U[..., 3] = mode(bend * 0.05)
+    U[..., 4] = 50.0 * s * (2.0 - X) + mode(5.0 * s)
+    wall = (np.abs(Y) < 1e-12) | (np.abs(Y - H) < 1e-12) | (np.abs(X) < 1e-12) | (np.abs(X - X_BREAKS[-1]) < 1e-12)
+    U[..., 2][wall] = 0.0
+    U[..., 3][wall] = 0.0
+    U[..., 0:2][inside] *= 1e-2
+    return U.reshape(-1, 5)

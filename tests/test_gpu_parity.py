@@ -5,6 +5,8 @@ in a different order, so they agree to a few hundred ulps of the largest
 term (1e-12 relative to the largest entry). States after Newton solves agree
 to the 1e-10 relative accuracy the library targets (field by field: v, u, p).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -198,10 +200,18 @@ def test_fine_and_coarse_propagators_match_oracle():
         assert max(rel_field_errors(Uc[s], ref_c).values()) <= 1e-10
 
 
-def test_parareal_matches_oracle_iterates_and_reaches_serial():
-    w = wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4)
+# a short run, and the 16 x 4 workload as specified: T = 1, 8 slices of 16 fine
+# shifted Crank-Nicolson steps, one implicit-Euler coarse step per slice. Over
+# its 128 fine steps per iteration two solutions that each meet the Newton
+# stopping test at 1e-10 drift apart by about that much in the pressure, so
+# both sides solve that workload's Newton systems to 1e-12: the comparison
+# then sees the arithmetic, not where two stopping tests fall.
+@pytest.mark.parametrize("w", [wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4),
+                               dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-12)],
+                         ids=["short", "fsi2d_q2_16x4_T1_8x16"])
+def test_parareal_matches_oracle_iterates_and_reaches_serial(w):
     mesh = oracle_mesh(w)
-    model = of.FSIModel(mesh, w.material)
+    model = of.FSIModel(mesh, w.material, newton_tol=w.newton_tol)
     dt = w.T / w.n_slices
     fine = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine)
     coarse = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, 1, theta=1.0)
@@ -274,3 +284,63 @@ def test_cuda_graph_replay_is_bitwise_identical():
         U2, _ = ctx.fsi_theta_step(U1, [0.1 + k, 0.1 + k], k, 1.0)   # replays the captured graphs
         out.append(U2)
     assert torch.equal(out[0], out[1])
+
+
+def test_parareal_continue_is_bitwise_one_longer_run():
+    """A run stepped one iteration at a time (parareal_continue) computes the
+    bits of one parareal_iterate call with the summed iteration count, also
+    after a pipelined start and across a host round trip of the iterate."""
+    from paper_1907_01252_gb300 import fsi
+    w = wl.Workload("cont", nx=16, ny=4, T=0.5, n_slices=5, m_fine=3)
+    ctx = ctx_for(w, w.n_slices)
+    U0 = torch.zeros((w.n_slices + 1, ctx.n_dofs), dtype=torch.float64, device=DEV)
+    with pytest.raises(fsi.FsiError):          # nothing to continue yet
+        ctx.parareal_continue(U0.clone(), 1, 0.0)
+    Uref, sref = ctx.parareal_iterate(U0.clone(), 3, 0.0, history=True)
+    U = U0.clone()
+    _, s0 = ctx.parareal_iterate(U, 0, 0.0)
+    assert s0["iterations"] == 0
+    hist = []
+    for it in (1, 2, 3):
+        U = U.cpu().to(DEV)                    # the caller may keep the iterate on the host in between
+        _, st = ctx.parareal_continue(U, 1, 0.0, history=True)
+        assert st["iterations"] == it
+        hist += st["history"]
+    assert torch.equal(U, Uref)
+    assert np.array_equal(np.array(hist), np.array(sref["history"]))
+    U2 = U0.clone()
+    ctx.parareal_iterate(U2, 1, 0.0)
+    _, st = ctx.parareal_continue(U2, 2, 0.0)
+    assert st["iterations"] == 3 and torch.equal(U2, Uref)
+    # continuing after the pipelined schedule, and no iteration past n_slices
+    ctxp = ctx_for(w, w.n_slices, pipeline_chunk=2)
+    U3 = U0.clone()
+    ctxp.parareal_iterate(U3, 2, 0.0)
+    ctxp.parareal_continue(U3, 1, 0.0)
+    assert torch.equal(U3, Uref)
+    Un, _ = ctx.parareal_iterate(U0.clone(), w.n_slices, 0.0)
+    _, st = ctx.parareal_continue(U, 10, 0.0)
+    assert st["iterations"] == w.n_slices and torch.equal(U, Un)
+
+
+def test_theta_step_128x32_matches_oracle():
+    """The benchmarked mesh: 128 x 32 cells (83,525 dofs), so the solve runs the
+    whole multigrid hierarchy and the cluster inverse of the coarsest level.
+    Two slices from developed oracle states: an implicit-Euler step from rest
+    to full inflow at t = 0.3, and one fine step on from there; one fine
+    shifted Crank-Nicolson step of both, batched, against the oracle's steps."""
+    w = wl.LARGE_128x32
+    mesh = oracle_mesh(w)
+    model = of.FSIModel(mesh, w.material)
+    k = w.k_fine
+    th = model.theta_fine(k)
+    Ua = model.step(np.zeros((mesh.n_nodes, 5)), 0.25, 0.05, 1.0)
+    Ub = model.step(Ua, 0.3, k, th)
+    Uc = model.step(Ub, 0.3 + k, k, th)
+    ctx = ctx_for(w, 2)
+    assert ctx.n_levels >= 5
+    U1, st = ctx.fsi_theta_step(to_dev(np.stack([Ua, Ub])), [0.3, 0.3 + k], k, th)
+    got = U1.cpu().numpy().reshape(2, -1, 5)
+    for s, ref in enumerate((Ub, Uc)):
+        errs = rel_field_errors(got[s], ref)
+        assert max(errs.values()) <= 1e-10, (s, errs)
