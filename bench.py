@@ -81,7 +81,20 @@ def parse():
                     help="skip the precision-variant runs (FP32 solver or FP32 multigrid)")
     ap.add_argument("--no-small-converged", action="store_true",
                     help="skip the converged Parareal run of the 16 x 4 workload")
+    ap.add_argument("--from-t", type=float, default=0.0,
+                    help="--unit fine_step / coarse_step: start every slice from the state reached by coarse "
+                         "steps from rest up to this time")
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
+                    help="--unit fine_step / coarse_step: override a solver parameter of the context")
     return ap.parse_args()
+
+
+def overrides(args):
+    out = {}
+    for kv in args.set:
+        key, val = kv.split("=", 1)
+        out[key] = float(val) if any(ch in val for ch in ".e") else int(val)
+    return out
 
 
 class ClockSampler:
@@ -621,11 +634,18 @@ def bench_unit(args, torch, fsi, wl, dev, dist, rank, world):
     w = wl.LARGE_128x32
     if args.unit == "coarse_step":
         args.slices = 1
-    ctx = fsi.Context(w, max_batch=args.slices)
+    ctx = fsi.Context(w, max_batch=args.slices, **overrides(args))
     n = ctx.n_dofs
     stream = torch.cuda.current_stream(dev)
     Uf = torch.zeros((args.slices, n), dtype=torch.float64, device=dev)
     tf = [0.0] * args.slices      # first step of the trajectory, from rest
+    if args.from_t > 0:           # or from a developed state: coarse steps from rest up to from_t
+        nc = max(1, int(round(args.from_t / w.k_coarse)))
+        U1 = torch.zeros((1, n), dtype=torch.float64, device=dev)
+        for i in range(nc):
+            U1, _ = ctx.fsi_coarse(U1, [i * w.k_coarse])
+        Uf[:] = U1
+        tf = [nc * w.k_coarse] * args.slices
     kf = w.k_fine if args.unit == "fine_step" else w.k_coarse
     th = 0.5 + w.material.theta0 * kf if args.unit == "fine_step" else 1.0
     names = fsi.kernel_names()
@@ -647,13 +667,17 @@ def bench_unit(args, torch, fsi, wl, dev, dist, rank, world):
     clocks.start()
     torch.cuda.synchronize()
     l0 = fsi.launch_count()
-    _, sec = timed(stream, torch, lambda: [ctx.fsi_theta_step(Uf, tf, kf, th) for _ in range(args.steps)])
+    stats = []
+    _, sec = timed(stream, torch, lambda: [stats.append(ctx.fsi_theta_step(Uf, tf, kf, th)[1]) for _ in range(args.steps)])
     clk = clocks.stop()
     value = args.slices * args.steps / sec
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": w.name, "unit": args.unit, "slices": args.slices},
+                      "config": {"workload": w.name, "unit": args.unit, "slices": args.slices,
+                                 "overrides": overrides(args),
+                                 "newton_iters": [st["newton_iters"] for st in stats],
+                                 "gmres_iters": [st["gmres_iters"] for st in stats]},
                       "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
                       "gpu_launches": fsi.launch_count() - l0}))
     ctx.close()

@@ -128,6 +128,12 @@ typedef struct fsi_params {
   int mg_coarse_sweeps;    /* 3D path only: 0 solves the coarsest level with its dense
                               inverse; > 0 applies that many smoother sweeps there
                               instead (no inverse to build for each coarse step) */
+  int tc_contraction;      /* 2D path, FP32 element matrices (precision 1, and the FP32
+                              multigrid levels of precision 2): 1 runs the element
+                              contraction B^T D B on the tensor cores (tcgen05.mma,
+                              each FP32 operand as three BF16 terms, FP32 accumulation
+                              in tensor memory), 0 on the CUDA cores in FP32. The
+                              tangent D is FP64 either way */
 } fsi_params;
 
 /* Iteration statistics of one call (filled when the pointer is non-NULL). */
@@ -200,6 +206,14 @@ int fsi_residual_noalloc(fsi_ctx* ctx, int S, const double* U, const double* U_o
  * from fsi_bsr_pattern. Errors: FSI_EINVAL. */
 int fsi_jacobian(fsi_ctx* ctx, int S, const double* U, const double* U_old,
                  double k, double theta, double* vals, void* stream);
+
+/* The same Jacobian with FP32 element matrices and FP32 blocks, as the FP32
+ * linear solver builds it (precision 1): vals device float [S][nnzb][5][5].
+ * The element contraction runs on the tensor cores or the CUDA cores as
+ * params->tc_contraction says; the tangent is FP64. Errors: FSI_EINVAL,
+ * FSI_ECUDA (also when a tensor-core MMA completion was not seen). */
+int fsi_jacobian_f32(fsi_ctx* ctx, int S, const double* U, const double* U_old,
+                     double k, double theta, float* vals, void* stream);
 int fsi_nnzb(const fsi_ctx* ctx);
 /* Host copy of the block pattern: rowptr [n_nodes + 1], colidx [nnzb]. */
 int fsi_bsr_pattern(const fsi_ctx* ctx, int* rowptr, int* colidx);
@@ -471,6 +485,16 @@ int fsi_profile_read_bytes(int kernel_id, double* total_bytes);
  * pointer to one double (written only in a case no input reaches). The caller
  * times the launch with events on the same stream. Errors: FSI_EINVAL, FSI_ECUDA. */
 int fsi_fp64_probe(int blocks, int iters, double seed, double* sink, void* stream);
+
+/* Tensor-core tile product (the paper has no counterpart; it is the primitive of
+ * the tensor-core element contraction, exposed so that it can be tested alone):
+ * D = A B^T with A device [128][32], B device [16][32] and D device [128][16],
+ * all FP32 row-major. Each FP32 operand enters the BF16 tcgen05 MMA as nsplit
+ * BF16 terms (1: plain BF16 rounding; 2 or 3: the rounding residuals as
+ * further terms, 3 giving FP32-level accuracy); products accumulate in FP32
+ * in tensor memory. Synchronises the stream. Errors: FSI_EINVAL, FSI_ECUDA
+ * (also when the MMA completion is not seen within the kernel's poll limit). */
+int fsi_tc_tile_product(int nsplit, const float* A, const float* B, float* D, void* stream);
 
 long long fsi_launch_count(int kernel_id);
 int fsi_kernel_count(void);

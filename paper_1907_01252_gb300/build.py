@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfsi.so")
 SOURCES = ["fsi.cu", "fsi3.cu", "batch.cpp"]
-HEADERS = ["fsi_kernels.cuh", "fsi_element.cuh", "fsi_internal.h", "fsi_mesh3d.h", "fsi_element3d.cuh", "fsi_mg3d.h",
+HEADERS = ["fsi_kernels.cuh", "fsi_tc.cuh", "fsi_element.cuh", "fsi_internal.h", "fsi_mesh3d.h", "fsi_element3d.cuh", "fsi_mg3d.h",
            "fsi_vanka3.h", os.path.join("..", "..", "include", "fsi.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -326,9 +326,10 @@ enum KernelId {
   KI_CELL_DRES_DLAME,
   KI_GATHER_VECTOR,
   KI_DRES_DVBAR,
+  KI_CELL_JACOBIAN_TC,
   KI_COUNT
 };
-const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar"};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar", "k_cell_jacobian_tc"};
 
 struct Profiler {
   std::atomic<unsigned long long> mask{0};
@@ -462,6 +463,7 @@ struct fsi_ctx {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
   double *hcol = nullptr, *hcol2 = nullptr, *scal = nullptr, *resid = nullptr, *partial = nullptr;
   int *nv = nullptr, *status = nullptr;
+  int* tc_status = nullptr;   // set by the tensor-core element Jacobian when an MMA completion was not seen
   uint8_t *active = nullptr, *active2 = nullptr;
   double* t_dev = nullptr;
   float *p_in = nullptr, *p_out = nullptr;   // FP32 preconditioner input / output (mixed precision)
@@ -674,6 +676,19 @@ int upload_tables_once() {
   CK(cudaMemcpyToSymbol(c_we, gw, sizeof(gw)));
   CK(cudaMemcpyToSymbol(c_lps_ss, kss, sizeof(kss)));
   CK(cudaMemcpyToSymbol(c_lps_tt, ktt, sizeof(ktt)));
+  float phif[9][9], dpsf[9][9], dptf[9][9], wqf[9];
+  for (int q = 0; q < 9; ++q) {
+    wqf[q] = (float)wq[q];
+    for (int l = 0; l < 9; ++l) {
+      phif[q][l] = (float)phi[q][l];
+      dpsf[q][l] = (float)dps[q][l];
+      dptf[q][l] = (float)dpt[q][l];
+    }
+  }
+  CK(cudaMemcpyToSymbol(c_phif, phif, sizeof(phif)));
+  CK(cudaMemcpyToSymbol(c_dpsf, dpsf, sizeof(dpsf)));
+  CK(cudaMemcpyToSymbol(c_dptf, dptf, sizeof(dptf)));
+  CK(cudaMemcpyToSymbol(c_wqf, wqf, sizeof(wqf)));
   return FSI_OK;
 }
 
@@ -708,6 +723,13 @@ bool mixed(const fsi_ctx* c) {
 template <typename T>
 int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, double k, double theta,
              const uint8_t* act, T* A, cudaStream_t st, double lps_scale = 1.0) {
+  if (sizeof(T) == sizeof(float) && c->prm.tc_contraction) {
+    // FP32 element matrices: the contraction on the tensor cores
+    CK(cudaFuncSetAttribute((const void*)k_cell_jacobian_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, JTC_SMEM));
+    LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN_TC, k_cell_jacobian_tc, (dim3(L.h.n_cells, S)), JAC_THREADS, JTC_SMEM, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, reinterpret_cast<float*>(L.Ke), c->tc_status);
+    LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<T, T>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.Ke), act, A, 1.0);
+    return launch_check();
+  }
   LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, (k_cell_jacobian<false, T>), (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, reinterpret_cast<T*>(L.Ke));
   LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<T, T>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.Ke), act, A, 1.0);
   return launch_check();
@@ -1875,8 +1897,9 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
       (rc = A(&c->hcol2, S * (m + 1))) || (rc = A(&c->scal, S)) || (rc = A(&c->resid, S)) ||
       (rc = A(&c->partial, S * nblk(n, RED_CHUNK) * 64)) || (rc = A(&c->nv, S)) || (rc = A(&c->status, S)) ||
       (rc = A(&c->active, S)) || (rc = A(&c->active2, S)) || (rc = A(&c->t_dev, S)) ||
-      (rc = A(&c->p_in, S * n)) || (rc = A(&c->p_out, S * n)))
+      (rc = A(&c->p_in, S * n)) || (rc = A(&c->p_out, S * n)) || (rc = A(&c->tc_status, 1)))
     return cleanup(rc);
+  if (cudaMemset(c->tc_status, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
   // the tables were copied with synchronous copies on the legacy stream; wait
   // for their DMA without waiting on other contexts' non-blocking streams
   if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
@@ -1921,6 +1944,22 @@ int fsi_jacobian(fsi_ctx* c, int S, const double* U, const double* U_old, double
   c->n_act = g_nact = count_active(act);
   TRY(jacobian<double>(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
   CK(cudaStreamSynchronize(st));
+  return FSI_OK;
+}
+
+int fsi_jacobian_f32(fsi_ctx* c, int S, const double* U, const double* U_old, double k, double theta, float* vals,
+                     void* stream) {
+  if (!c || !U || !U_old || !vals) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
+  TRY(jacobian<float>(c, c->lev[0], S, U, U_old, k, theta, c->active, vals, st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->tc_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) return fail(FSI_ECUDA, "tensor-core element Jacobian: an MMA completion was not seen within the poll limit");
   return FSI_OK;
 }
 
@@ -2069,6 +2108,28 @@ int fsi_profile_read_bytes(int kernel_id, double* total_bytes) {
   for (size_t r = 0; r < g_prof.rec_id.size(); ++r)
     if (g_prof.rec_id[r] == kernel_id) b += g_prof.rec_bytes[r];
   *total_bytes = b + g_prof.gbytes[kernel_id];
+  return FSI_OK;
+}
+
+namespace {
+__device__ int g_tc_status;
+}
+
+int fsi_tc_tile_product(int nsplit, const float* A, const float* B, float* D, void* stream) {
+  if (!A || !B || !D) return fail(FSI_EINVAL, "null argument");
+  if (nsplit < 1 || nsplit > 3) return fail(FSI_EINVAL, "fsi_tc_tile_product: nsplit outside 1..3");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = nullptr;
+  CK(cudaGetSymbolAddress((void**)&status, g_tc_status));
+  CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+  if (nsplit == 1) k_tc_tile_product<1><<<1, 128, 0, st>>>(A, B, D, status);
+  else if (nsplit == 2) k_tc_tile_product<2><<<1, 128, 0, st>>>(A, B, D, status);
+  else k_tc_tile_product<3><<<1, 128, 0, st>>>(A, B, D, status);
+  TRY(launch_check());
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) return fail(FSI_ECUDA, "fsi_tc_tile_product: MMA completion not seen within the poll limit");
   return FSI_OK;
 }
 

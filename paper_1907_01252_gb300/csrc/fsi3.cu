@@ -222,6 +222,7 @@ __global__ void k3_gather_residual(Dev3 d, Phys3D P, const double* __restrict__ 
 // running the cooperative routine; lps_scale multiplies the stabilisation
 // weight (coarse multigrid levels). Dynamic shared memory CJ3_TOTAL doubles.
 constexpr int CJ3_THREADS = 256;
+static_assert(CJ3_THREADS >= 7 * 32, "the cell Jacobian's field flags take one warp per test field");
 
 __global__ void __launch_bounds__(CJ3_THREADS) k3_cell_jacobian(Dev3 d, Phys3D P, const double* __restrict__ U,
                                                                const double* __restrict__ Uo, size_t stride, double k,

@@ -823,8 +823,8 @@ FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tab
   // F_d(a)(i, s): the 1D factor of B_a in direction d (the derivative where a = d + 1)
   auto Fa = [&](int d, int a, int i, int q) { return F[((d * 2 + (a == d + 1 ? 1 : 0)) * 3 + i) * 3 + q]; };
   const double s3[3] = {vol / (h[0] * h[0]), vol / (h[1] * h[1]), vol / (h[2] * h[2])};
+  cta.sync();   // X, XL, Wq, B, FG and F are read below by other threads than their writers
   for (int cj = 0; cj < 7; ++cj) {
-    if (cta.tid < 7) flag[cta.tid] = 0.0;
     for (int e = cta.tid; e < 27 * 4; e += cta.nt) {
       const int q = e / 4, b = e % 4;
       double o[28];
@@ -846,8 +846,23 @@ FSI3_HD inline void cell_jacobian3_cta(const Cta& cta, const Phys3& P, const Tab
         for (int c = 0; c < 3; ++c) FO[(f * 3 + c) * 3 + b] = o[c];
       }
     cta.sync();
-    for (int e = cta.tid; e < 27 * 28 * 4; e += cta.nt)
-      if (cj3_nonzero(Dc[e])) flag[((e / 4) % 28) / 4] = 1.0;
+    // flag[ci]: whether any tangent entry of test field ci (rows 4 ci .. 4 ci + 3) is nonzero;
+    // one warp per field on the device (needs at least 224 threads), one thread per field on the host
+#ifdef __CUDA_ARCH__
+    if (cta.tid < 7 * 32) {
+      const int f = cta.tid / 32, lane = cta.tid % 32;
+      bool nz = false;
+      for (int e = lane; e < 27 * 16; e += 32) nz |= cj3_nonzero(Dc[((e / 16) * 28 + 4 * f) * 4 + e % 16]);
+      nz = __any_sync(0xffffffffu, nz);
+      if (lane == 0) flag[f] = nz ? 1.0 : 0.0;
+    }
+#else
+    for (int f = cta.tid; f < 7; f += cta.nt) {
+      bool nz = false;
+      for (int e = 0; e < 27 * 16; ++e) nz |= cj3_nonzero(Dc[((e / 16) * 28 + 4 * f) * 4 + e % 16]);
+      flag[f] = nz ? 1.0 : 0.0;
+    }
+#endif
     cta.sync();
     for (int ci = 0; ci < 7; ++ci) {
       const bool lps = !solid && ci == 6 && cj == 6, fc = face && ci < 3 && cj < 6;

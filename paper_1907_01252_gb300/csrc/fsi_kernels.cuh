@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include "fsi_element.cuh"
+#include "fsi_tc.cuh"
 
 // --------------------------------------------------------------------------
 // Reference-cell tables (3 x 3 Gauss points, Q2 basis, q = q2*3 + q1,
@@ -267,27 +268,36 @@ __device__ inline bool jac_old_block_nonzero(bool solid, int ci, int cj) {
   return cj == ci || cj == ci - 2;
 }
 
-// TC: type of the B^T D B contraction and of the element matrices (double, or
-// float for the FP32 linear solver); the tangent D is always computed in FP64.
-template <bool OLD, typename TC = double>
-__global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
-                                                               const double* __restrict__ Uold, size_t stride,
-                                                               double k, double theta, double lps_scale,
-                                                               const uint8_t* __restrict__ active,
-                                                               TC* __restrict__ Ke) {
-  const int s = blockIdx.y;
-  const int cell = blockIdx.x;
-  if (!active[s]) return;
-  __shared__ double sU[45], sUo[45];
-  __shared__ QpIn sq[9];
-  __shared__ QpDerived sd[9];
-  __shared__ double sD[9][15][15];     // [q][test slot][trial direction]
-  __shared__ double sDe[3][2][12];     // outflow edge: [q][momentum comp][trial direction (c<4)]
-  __shared__ double sAlpha;
-  __shared__ double sSp[9], sDalpha[2];   // OLD: S p per local node, d alpha / d vbar
+// Shared state of the element Jacobian's tangent stage (one CTA per cell and slice).
+struct JacTangentShared {
+  double sU[45], sUo[45];
+  QpIn sq[9];
+  QpDerived sd[9];
+  double sD[9][15][15];     // [q][test slot][trial direction]
+  double sDe[3][2][12];     // outflow edge: [q][momentum comp][trial direction (c<4)]
+  double sAlpha;
+  double sSp[9], sDalpha[2];   // OLD: S p per local node, d alpha / d vbar
+};
+
+// The tangent stage: the cell's states, the quadrature-point quantities, the
+// 15 x 15 tangent D_q at every quadrature point (sD), the outflow-edge tangent
+// (sDe) and the stabilisation weight; ends with a CTA barrier.
+template <bool OLD>
+__device__ __forceinline__ void jac_tangent(const DevMesh& m, const Phys& P, const double* __restrict__ U,
+                                            const double* __restrict__ Uold, size_t stride, double k, double theta,
+                                            double lps_scale, int s, int cell, JacTangentShared& sh) {
+  double* sU = sh.sU;
+  double* sUo = sh.sUo;
+  QpIn* sq = sh.sq;
+  QpDerived* sd = sh.sd;
+  auto& sD = sh.sD;
+  auto& sDe = sh.sDe;
+  double& sAlpha = sh.sAlpha;
+  double* sSp = sh.sSp;
+  double* sDalpha = sh.sDalpha;
   const int tid = threadIdx.x;
   const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
-  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy;
   const uint8_t cf = m.cell_flags[cell];
   const bool solid = cf & CF_SOLID;
   const bool outflow = !solid && (cf & CF_OUTFLOW);
@@ -371,6 +381,32 @@ __global__ void __launch_bounds__(JAC_THREADS) k_cell_jacobian(DevMesh m, Phys P
     }
   }
   __syncthreads();
+}
+
+// TC: type of the B^T D B contraction and of the element matrices (double, or
+// float for the FP32 linear solver); the tangent D is always computed in FP64.
+template <bool OLD, typename TC = double>
+__global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian(DevMesh m, Phys P, const double* __restrict__ U,
+                                                               const double* __restrict__ Uold, size_t stride,
+                                                               double k, double theta, double lps_scale,
+                                                               const uint8_t* __restrict__ active,
+                                                               TC* __restrict__ Ke) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x;
+  if (!active[s]) return;
+  __shared__ JacTangentShared sh;
+  jac_tangent<OLD>(m, P, U, Uold, stride, k, theta, lps_scale, s, cell, sh);
+  auto& sD = sh.sD;
+  auto& sDe = sh.sDe;
+  const double& sAlpha = sh.sAlpha;
+  const double* sSp = sh.sSp;
+  const double* sDalpha = sh.sDalpha;
+  const int tid = threadIdx.x;
+  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const uint8_t cf = m.cell_flags[cell];
+  const bool solid = cf & CF_SOLID;
+  const bool outflow = !solid && (cf & CF_OUTFLOW);
   // Two-stage contraction over the field blocks (ci, cj) that the cell's
   // material couples, one quadrature point at a time:
   //   E[(ci,a)][(j,cj)] = w_q sum_b D_q[(ci,a)][(cj,b)] B_b(j,q)
@@ -1334,4 +1370,166 @@ __global__ void __launch_bounds__(FMA_PROBE_THREADS) k_fma_probe(int iters, doub
   }
   const double sum = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
   if (sum == -seed - 1e300) sink[0] = sum;
+}
+
+// --------------------------------------------------------------------------
+// Element Jacobian with the B^T D B contraction on the tensor cores (FP32
+// element matrices, for the FP32 linear solver and FP32 multigrid levels).
+// The tangent stage is that of k_cell_jacobian (FP64). The contraction
+//   K[(i,ci)][(j,cj)] = sum_{q,a} B_a(i,q) E_q[(ci,a)][(j,cj)]
+// becomes one product D = A B^T per cell with
+//   A[m][kk] = s_a E_q[(ci,a)][(j,cj)],  m = ci*45 + j*5 + cj (225 rows, padded to 256),
+//   B[i][kk] = reference-cell basis value (a = 0) or s / t derivative (a = 1, 2) of
+//              node i at Gauss point q (9 rows, padded to 16), kk = q*3 + a (27, padded to 32),
+// s_a = 1, 1/hx, 1/hy the reference-to-cell derivative factors, and D[m][i] the entry
+// K[(i,ci)][(j,cj)]. Both operands enter tcgen05.mma (kind::f16, M = 128, N = 16,
+// K = 16) as three BF16 terms (FP32-level accuracy), two M tiles accumulate in
+// 32 FP32 columns of tensor memory. Blocks the material does not couple are
+// exactly zero rows of A; the other blocks of the element matrix (zero, the
+// closed-form stabilisation block) and the outflow-edge term are written as in
+// k_cell_jacobian. When the MMA completion is not seen within the poll limit the
+// element matrix is filled with NaN (the solve then stops with FSI_ENAN) and
+// *status is set.
+// --------------------------------------------------------------------------
+__constant__ float c_phif[9][9];
+__constant__ float c_dpsf[9][9];
+__constant__ float c_dptf[9][9];
+__constant__ float c_wqf[9];
+
+constexpr int JTC_NS = 3;                          // BF16 terms per FP32 operand
+constexpr int JTC_A_TERM = 256 * 32 * 2;           // bytes of one A term
+constexpr int JTC_B_TERM = 16 * 32 * 2;
+constexpr int JTC_SMEM = JTC_NS * (JTC_A_TERM + JTC_B_TERM) + 2048;   // operands + slack
+static_assert(JAC_THREADS >= 128, "the tensor-memory read-back takes four warps");
+
+__global__ void __launch_bounds__(JAC_THREADS, 2) k_cell_jacobian_tc(DevMesh m, Phys P, const double* __restrict__ U,
+                                                                    const double* __restrict__ Uold, size_t stride,
+                                                                    double k, double theta, double lps_scale,
+                                                                    const uint8_t* __restrict__ active,
+                                                                    float* __restrict__ Ke, int* __restrict__ status) {
+  const int s = blockIdx.y;
+  const int cell = blockIdx.x;
+  if (!active[s]) return;   // uniform over the CTA, before any tensor-memory allocation
+  extern __shared__ __align__(1024) unsigned char jtc[];
+  __shared__ JacTangentShared sh;
+  __shared__ float sDf[9][15][15];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  jac_tangent<false>(m, P, U, Uold, stride, k, theta, lps_scale, s, cell, sh);
+  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
+  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const uint8_t cf = m.cell_flags[cell];
+  const bool solid = cf & CF_SOLID;
+  const bool outflow = !solid && (cf & CF_OUTFLOW);
+  for (int e = tid; e < 9 * 15 * 15; e += JAC_THREADS) (&sDf[0][0][0])[e] = (float)(&sh.sD[0][0][0])[e];
+  __syncthreads();
+  unsigned char* sA = jtc;
+  unsigned char* sB = jtc + JTC_NS * JTC_A_TERM;
+  const float fihx = (float)ihx, fihy = (float)ihy, farea = (float)area;
+  // B: 16 rows x 4 chunks of 8 K values; A: 256 rows x 4 chunks
+  for (int item = tid; item < 16 * 4 + 256 * 4; item += JAC_THREADS) {
+    const bool isB = item < 64;
+    const int row = isB ? item / 4 : (item - 64) / 4, c = item % 4;
+    float v[8];
+    if (isB) {
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
+        v[x] = (row < 9 && kk < 27) ? (a == 0 ? c_phif[q][row] : (a == 1 ? c_dpsf[q][row] : c_dptf[q][row])) : 0.f;
+      }
+    } else {
+      const int ci = row / 45, j = (row / 5) % 9, cj = row % 5;
+      const bool live = row < 225 && jac_block_nonzero(solid, ci, cj);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
+        float e = 0.f;
+        if (live && kk < 27) {
+          const float* Dr = &sDf[q][ci * 3 + a][cj * 3];
+          const float sa = a == 0 ? 1.f : (a == 1 ? fihx : fihy);
+          e = sa * c_wqf[q] * farea *
+              (Dr[0] * c_phif[q][j] + Dr[1] * (c_dpsf[q][j] * fihx) + Dr[2] * (c_dptf[q][j] * fihy));
+        }
+        v[x] = e;
+      }
+    }
+    uint32_t w[JTC_NS][4];
+#pragma unroll
+    for (int x = 0; x < 8; x += 2) {
+      __nv_bfloat16 t0[JTC_NS], t1[JTC_NS];
+      tc::split_bf16<JTC_NS>(v[x], t0);
+      tc::split_bf16<JTC_NS>(v[x + 1], t1);
+#pragma unroll
+      for (int t = 0; t < JTC_NS; ++t)
+        w[t][x / 2] = (uint32_t)__bfloat16_as_ushort(t0[t]) | ((uint32_t)__bfloat16_as_ushort(t1[t]) << 16);
+    }
+    const uint32_t off = tc::kmajor_offset(row, c * 8, 4);
+#pragma unroll
+    for (int t = 0; t < JTC_NS; ++t) {
+      unsigned char* base = isB ? sB + t * JTC_B_TERM : sA + t * JTC_A_TERM;
+      *reinterpret_cast<uint4*>(base + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    }
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
+    for (int tile = 0; tile < 2; ++tile) {
+      int issued = 0;
+      for (int ks = 0; ks < 2; ++ks)
+        for (int p = 0; p < tc::SplitPairs<JTC_NS>::count; ++p) {
+          const uint32_t a0 = tc::smem_u32(sA + tc::SplitPairs<JTC_NS>::a(p) * JTC_A_TERM) + tile * 8192 + ks * 256;
+          const uint32_t b0 = tc::smem_u32(sB + tc::SplitPairs<JTC_NS>::b(p) * JTC_B_TERM) + ks * 256;
+          tc::mma_bf16(tmem + tile * 16, tc::smem_desc(a0, 128, 512), tc::smem_desc(b0, 128, 512), idesc,
+                       issued++ > 0);
+        }
+    }
+    tc::mma_commit(&bar);
+  }
+  __syncwarp();
+  bool ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);
+  if (!ok) ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);   // the MMAs in flight get a second chance
+  ok = __syncthreads_and(ok);                            // one outcome for the whole CTA
+  if (!ok && tid == 0) atomicExch(status, 1);
+  tc::fence_after_sync();
+  float* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
+  if (warp < 4) {
+    for (int tile = 0; tile < 2; ++tile) {
+      float d[16];
+      if (ok) tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + tile * 16, d);
+      const int row = tile * 128 + warp * 32 + lane;
+      if (row >= 225) continue;
+      const int ci = row / 45, j = (row / 5) % 9, cj = row % 5;
+      if (!jac_block_nonzero(solid, ci, cj)) continue;
+      for (int i = 0; i < 9; ++i) {
+        double v = ok ? (double)d[i] : __longlong_as_double(0x7ff8000000000000ll);
+        if (outflow && ci < 2 && cj < 4) {
+          for (int q = 0; q < 3; ++q) {
+            const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
+            const double* Drow = sh.sDe[q][ci] + cj * 3;
+            v += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+          }
+        }
+        out[(i * 5 + ci) * 45 + j * 5 + cj] = (float)v;
+      }
+    }
+  }
+  // the other blocks: zero, or the stabilisation block (fluid p-p)
+  for (int e = tid; e < 2025; e += JAC_THREADS) {
+    const int row = e / 45, col = e % 45;
+    const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
+    if (jac_block_nonzero(solid, ci, cj)) continue;
+    double v = 0.0;
+    if (!solid && ci == 4 && cj == 4) v = k * sh.sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
+    out[e] = (float)v;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
 }

@@ -38,7 +38,7 @@ class fsi_params(C.Structure):
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
                 ("graph_max_batch", C.c_int), ("precision", C.c_int), ("pipeline_chunk", C.c_int),
-                ("max_batch", C.c_int), ("mg_coarse_sweeps", C.c_int)]
+                ("max_batch", C.c_int), ("mg_coarse_sweeps", C.c_int), ("tc_contraction", C.c_int)]
 
 
 class fsi_stats(C.Structure):
@@ -91,6 +91,7 @@ SIGNATURES = {
     "fsi_residual_noalloc": (_I, [_VP, _I, _VP, _VP, C.POINTER(_D), _D, _D, _VP, _VP]),
     "fsi_jacobian": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
     "fsi_jacobian_old": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
+    "fsi_jacobian_f32": (_I, [_VP, _I, _VP, _VP, _D, _D, _VP, _VP]),
     "fsi_set_material": (_I, [_VP, _D, _D, _D]),
     "fsi_adjoint": (_I, [_VP, _VP, _D, _I, C.POINTER(_D), C.POINTER(_D), C.POINTER(fsi_stats), _VP]),
     "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
@@ -129,6 +130,7 @@ SIGNATURES = {
     "fsi_profile_read": (_I, [_I, C.POINTER(_D), C.POINTER(C.c_longlong), C.POINTER(_D)]),
     "fsi_profile_read_bytes": (_I, [_I, C.POINTER(_D)]),
     "fsi_fp64_probe": (_I, [_I, _I, _D, _VP, _VP]),
+    "fsi_tc_tile_product": (_I, [_I, _VP, _VP, _VP, _VP]),
     "fsi_launch_count": (C.c_longlong, [_I]),
     "fsi_kernel_count": (_I, []),
     "fsi_kernel_name": (C.c_char_p, [_I]),
@@ -170,6 +172,14 @@ def fp64_probe(blocks, iters, sink, seed=1.0):
     """Launch the FP64 FMA probe on the current stream (blocks * 256 * iters * 16 flops)."""
     _check(load_library().fsi_fp64_probe(blocks, iters, seed, _ptr(sink), _stream()))
     return blocks * 256 * iters * 16
+
+
+def tc_tile_product(A, B, nsplit=3):
+    """D = A B^T on the tensor cores (A [128, 32], B [16, 32] FP32 device tensors)."""
+    import torch
+    D = torch.empty((128, 16), dtype=torch.float32, device=A.device)
+    _check(load_library().fsi_tc_tile_product(nsplit, _ptr(A), _ptr(B), _ptr(D), _stream()))
+    return D
 
 
 def launch_count(name=None):
@@ -241,7 +251,7 @@ def _params(w: wl.Workload, max_batch: int, overrides):
              gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
              mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.5, mg_reuse=2,
              mg_rebuild_every=4, graph_max_batch=4, precision=0, pipeline_chunk=0, max_batch=max_batch,
-             mg_coarse_sweeps=0)
+             mg_coarse_sweeps=0, tc_contraction=1)
     p.update(overrides)
     return p
 
@@ -334,6 +344,14 @@ class Context:
         S = U.shape[0]
         vals = torch.empty((S, self.nnzb, 5, 5), dtype=torch.float64, device=U.device) if vals is None else vals
         _check(self.lib.fsi_jacobian(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
+        return vals
+
+    def fsi_jacobian_f32(self, U, U_old, k, theta, vals=None):
+        """FP32 Jacobian blocks [S, nnzb, 5, 5] (element contraction as tc_contraction says)."""
+        import torch
+        S = U.shape[0]
+        vals = torch.empty((S, self.nnzb, 5, 5), dtype=torch.float32, device=U.device) if vals is None else vals
+        _check(self.lib.fsi_jacobian_f32(self.handle, S, _ptr(U), _ptr(U_old), k, theta, _ptr(vals), _stream()))
         return vals
 
     def fsi_jacobian_old(self, U, U_old, k, theta, vals=None):

@@ -5,19 +5,15 @@ Tolerances as in 2D: the residual and the Jacobian are the same finite sums in a
 order (1e-12 relative to the largest entry of a field; 1e-10 per field block of the
 Jacobian, whose entries span ~16 decades); Newton-solved states to 1e-9 per field.
 
-These tests are gated by FSI3_GPU=1: the 3D kernels have been checked on the CPU
-(the same per-entry code, tests/test_element3d_host.py), and their first GPU run is
-a deliberate step, not a side effect of a full -m gpu run.
+The cooperative cell routines the kernels run are also checked on the CPU: against
+the oracle (tests/test_element3d_host.py) and for races with one host thread per
+CUDA thread (tests/test_cta_races.py).
 """
-import os
-
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("FSI3_GPU") != "1",
-                                 reason="3D CUDA path not yet run on a GPU (set FSI3_GPU=1)")]
+pytestmark = pytest.mark.gpu
 
 from oracle import fsi_nd as on  # noqa: E402
 from paper_1907_01252_gb300 import workloads as wl  # noqa: E402
@@ -149,7 +145,9 @@ def test_3d_parareal_iterate_matches_oracle():
     fine = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine)  # noqa: E731
     U0 = np.zeros((mesh.n_nodes, 7))
     ref = opr.parareal(U0, w.n_slices, coarse, fine, 1)[1]
-    ctx = ctx_for(w, w.n_slices)
+    # the velocities are small at these early times (max 0.07), so the GPU solves its Newton
+    # systems to the oracle's 1e-12 too (the tolerance is absolute below a unit residual)
+    ctx = ctx_for(w, w.n_slices, newton_tol=1e-12)
     U = torch.zeros((w.n_slices + 1, ctx.n_dofs), dtype=torch.float64, device=DEV)
     U, st = ctx.fsi3_parareal(U, 1, 0.0)
     assert st["iterations"] == 1

@@ -204,10 +204,11 @@ def test_fine_and_coarse_propagators_match_oracle():
 # shifted Crank-Nicolson steps, one implicit-Euler coarse step per slice. Over
 # its 128 fine steps per iteration two solutions that each meet the Newton
 # stopping test at 1e-10 drift apart by about that much in the pressure, so
-# both sides solve that workload's Newton systems to 1e-12: the comparison
-# then sees the arithmetic, not where two stopping tests fall.
+# both sides solve that workload's Newton systems to 1e-11 (just above the
+# residual's round-off floor of about 1.5e-12 relative): the comparison then
+# sees the arithmetic, not where two stopping tests fall.
 @pytest.mark.parametrize("w", [wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4),
-                               dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-12)],
+                               dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-11)],
                          ids=["short", "fsi2d_q2_16x4_T1_8x16"])
 def test_parareal_matches_oracle_iterates_and_reaches_serial(w):
     mesh = oracle_mesh(w)
@@ -308,19 +309,20 @@ def test_parareal_continue_is_bitwise_one_longer_run():
         hist += st["history"]
     assert torch.equal(U, Uref)
     assert np.array_equal(np.array(hist), np.array(sref["history"]))
-    U2 = U0.clone()
-    ctx.parareal_iterate(U2, 1, 0.0)
-    _, st = ctx.parareal_continue(U2, 2, 0.0)
-    assert st["iterations"] == 3 and torch.equal(U2, Uref)
-    # continuing after the pipelined schedule, and no iteration past n_slices
+    # continuing after the pipelined schedule
     ctxp = ctx_for(w, w.n_slices, pipeline_chunk=2)
     U3 = U0.clone()
     ctxp.parareal_iterate(U3, 2, 0.0)
     ctxp.parareal_continue(U3, 1, 0.0)
     assert torch.equal(U3, Uref)
-    Un, _ = ctx.parareal_iterate(U0.clone(), w.n_slices, 0.0)
-    _, st = ctx.parareal_continue(U, 10, 0.0)
-    assert st["iterations"] == w.n_slices and torch.equal(U, Un)
+    # no iteration runs past n_slices; a new parareal_iterate starts a new run of the context
+    Un, _ = ctxp.parareal_iterate(U0.clone(), w.n_slices, 0.0)
+    U2 = U0.clone()
+    ctx.parareal_iterate(U2, 1, 0.0)
+    _, st = ctx.parareal_continue(U2, 2, 0.0)
+    assert st["iterations"] == 3 and torch.equal(U2, Uref)
+    _, st = ctx.parareal_continue(U2, 10, 0.0)
+    assert st["iterations"] == w.n_slices and torch.equal(U2, Un)
 
 
 def test_theta_step_128x32_matches_oracle():
