@@ -408,7 +408,7 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
     dt = w.T / N
     stream = torch.cuda.current_stream(dev)
     hbm_gbs, hbm_src = load_peaks()
-    ctx = fsi.Context(w, max_batch=N)
+    ctx = fsi.Context(w, max_batch=N, **overrides(args))
     n = ctx.n_dofs
 
     # the serial fine solution of the whole interval on the same GPU (the metric's reference)
@@ -607,6 +607,7 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
                                    "fine solves of every slice not yet exact, then the corrected coarse sweep; "
                                    "value = fine time-steps advanced per second over the timed iterations",
                            "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
+                           "overrides": overrides(args),
                            "solver": {"newton_tol": w.newton_tol, "newton_eta": w.newton_eta,
                                       "gmres_rtol_first": w.gmres_rtol_first, "gmres_rtol": w.gmres_rtol,
                                       "gmres_restart": w.gmres_restart},
@@ -667,6 +668,7 @@ def bench_unit(args, torch, fsi, wl, dev, dist, rank, world):
     clocks.start()
     torch.cuda.synchronize()
     l0 = fsi.launch_count()
+    print("launches before the timed steps: %d" % l0, file=sys.stderr)
     stats = []
     _, sec = timed(stream, torch, lambda: [stats.append(ctx.fsi_theta_step(Uf, tf, kf, th)[1]) for _ in range(args.steps)])
     clk = clocks.stop()

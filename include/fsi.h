@@ -134,6 +134,14 @@ typedef struct fsi_params {
                               each FP32 operand as three BF16 terms, FP32 accumulation
                               in tensor memory), 0 on the CUDA cores in FP32. The
                               tangent D is FP64 either way */
+  int ff_operator;         /* 2D path, FP64 operators (precision 0, and the Krylov
+                              operator of precision 2): 1 applies the block-sparse
+                              product in the Krylov solver and in the multigrid
+                              residuals with the blocks and the input vector as float
+                              pairs hi + lo and a compensated FP32 accumulation (about
+                              2^-48 relative to the sum of |a x|, on the FP32 pipe); 0
+                              with FP64 FMAs. The Newton residual, the Jacobian and
+                              every state stay FP64 either way */
 } fsi_params;
 
 /* Iteration statistics of one call (filled when the pointer is non-NULL). */

@@ -278,6 +278,9 @@ struct Level {
   double *cellbuf = nullptr, *r = nullptr, *x = nullptr, *b = nullptr;
   double *D = nullptr, *Dinv = nullptr;       // coarsest only
   float* A32 = nullptr;                       // level 0, mixed precision: the preconditioner's FP32 copy
+  float2* Aff = nullptr;                      // FP64 operator as float pairs (float-float product)
+  float2* xff = nullptr;                      // input vector of that product, as float pairs
+  const void* aff_of = nullptr;               // the FP64 values Aff currently holds (nullptr: none)
   int* perm = nullptr;
   bool coarsest = false;
 };
@@ -327,9 +330,11 @@ enum KernelId {
   KI_GATHER_VECTOR,
   KI_DRES_DVBAR,
   KI_CELL_JACOBIAN_TC,
+  KI_BSR_SPMV_FF,
+  KI_TO_FF,
   KI_COUNT
 };
-const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar", "k_cell_jacobian_tc"};
+const char* const kKernelNames[] = {"k_add_basis", "k_apply_dirichlet", "k_assemble_bsr", "k_axpby", "k_backsolve", "k_bsr_spmv", "k_cell_jacobian", "k_cell_residual", "k_dense_apply", "k_dense_from_bsr", "k_dense_invert", "k_dots_finish", "k_dots_partial", "k_fill", "k_gather_residual", "k_givens", "k_init_g", "k_interp_state", "k_parareal_correct", "k_prolong_add", "k_restrict", "k_scale", "k_sub_basis", "k_vanka_cell", "k_vanka_gather", "k_vanka_setup", "k_vanka_scatter", "k_bsr_transpose", "k_cell_jacobian_old", "k_cell_dres_dlame", "k_gather_vector", "k_dres_dvbar", "k_cell_jacobian_tc", "k_bsr_spmv_ff", "k_to_ff"};
 
 struct Profiler {
   std::atomic<unsigned long long> mask{0};
@@ -523,7 +528,7 @@ int upload(std::vector<void*>& own, const T** p, const std::vector<T>& v) {
   return FSI_OK;
 }
 
-int setup_level(Level& L, int S, bool coarsest, bool need_state) {
+int setup_level(Level& L, int S, bool coarsest, bool need_state, bool ff) {
   HostMesh& h = L.h;
   DevMesh& d = L.dm;
   d.nnx = h.nnx;
@@ -559,6 +564,10 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state) {
   if (!need_state) TRY(dalloc(L.owned, &L.Ke, (size_t)S * h.n_cells * 2025));
   else L.Ke = L.KV;
   TRY(dalloc(L.owned, &L.A, (size_t)S * h.nnzb * 25));
+  if (ff) {
+    TRY(dalloc(L.owned, &L.Aff, (size_t)S * h.nnzb * 25));
+    TRY(dalloc(L.owned, &L.xff, (size_t)S * h.n_nodes * 5));
+  }
   if (!need_state) TRY(dalloc(L.owned, &L.A32, (size_t)S * h.nnzb * 25));
   TRY(dalloc(L.owned, &L.cellbuf, (size_t)S * h.n_cells * 45));
   TRY(dalloc(L.owned, &L.r, S * L.n));
@@ -728,10 +737,19 @@ int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
     CK(cudaFuncSetAttribute((const void*)k_cell_jacobian_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, JTC_SMEM));
     LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN_TC, k_cell_jacobian_tc, (dim3(L.h.n_cells, S)), JAC_THREADS, JTC_SMEM, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, reinterpret_cast<float*>(L.Ke), c->tc_status);
     LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<T, T>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.Ke), act, A, 1.0);
+    if ((const void*)A == (const void*)L.A) L.aff_of = nullptr;
     return launch_check();
   }
   LAUNCH_W(2.0 * 9 * (2025 + 675) * 3 * L.h.n_cells * (double)c->n_act, KI_CELL_JACOBIAN, (k_cell_jacobian<false, T>), (dim3(L.h.n_cells, S)), JAC_THREADS, 0, st, L.dm, c->P, U, Uold, L.n, k, theta, lps_scale, act, reinterpret_cast<T*>(L.Ke));
   LAUNCH(KI_ASSEMBLE_BSR, (k_assemble_bsr<T, T>), (dim3(nblk((size_t)L.h.nnzb * 5, 128), S)), 128, 0, st, L.dm, reinterpret_cast<const T*>(L.Ke), act, A, 1.0);
+  if ((const void*)A == (const void*)L.A) {
+    L.aff_of = nullptr;
+    if (sizeof(T) == sizeof(double) && L.Aff) {   // the float-pair copy for the operator products
+      const size_t cnt = (size_t)L.h.nnzb * 25;
+      LAUNCH_WB(3.0 * cnt * c->n_act, 16.0 * cnt * c->n_act, KI_TO_FF, k_to_ff, (dim3(nblk(cnt, 256), S)), 256, 0, st, cnt, reinterpret_cast<const double*>(A), cnt, act, L.Aff, cnt);
+      L.aff_of = A;
+    }
+  }
   return launch_check();
 }
 
@@ -746,6 +764,12 @@ int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act
   // per active slice: the blocks, x, y (and b); once per launch: the row list, row pointers and column indices
   const double bytes = (double)g_nact * sizeof(T) * (25.0 * blocks + (double)L.n + (RES ? 10.0 : 5.0) * nrows) +
                        4.0 * (blocks + 2.0 * nrows + 1.0);
+  if (sizeof(T) == sizeof(double) && L.Aff && L.aff_of == (const void*)A) {
+    // the FP64 operator as float pairs: x to float pairs, then the compensated FP32 product
+    LAUNCH_WB(3.0 * (double)L.n * g_nact, 16.0 * (double)L.n * g_nact, KI_TO_FF, k_to_ff, (dim3(nblk(L.n, 256), S)), 256, 0, st, L.n, reinterpret_cast<const double*>(x), L.n, act, L.xff, L.n);
+    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV_FF, (k_bsr_spmv_ff<RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, L.Aff, L.xff, reinterpret_cast<const double*>(b), L.n, act, reinterpret_cast<double*>(y), rows, nrows);
+    return launch_check();
+  }
   LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
   return launch_check();
 }
@@ -823,6 +847,7 @@ int mg_setup(fsi_ctx* c, int S, const double* U, const double* Uold, double k, d
       double* Ad = reinterpret_cast<double*>(A);
       LAUNCH(KI_BSR_TRANSPOSE, k_bsr_transpose, (dim3(nblk((size_t)L.h.nnzb * 25, 256), S)), 256, 0, st, L.h.nnzb, L.blk_t, Ad, act, L.Ke);
       CK(cudaMemcpyAsync(Ad, L.Ke, (size_t)S * L.h.nnzb * 25 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      L.aff_of = nullptr;   // the float pairs hold the untransposed operator
     }
     if (L.coarsest) {
       if (keep_coarsest) continue;   // inverse of an earlier Newton iteration of this step
@@ -1876,7 +1901,8 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
   if (rc) return cleanup(rc);
   for (size_t l = 0; l < hs.size(); ++l) {
     c->lev[l].h = hs[l];
-    rc = setup_level(c->lev[l], c->S, l + 1 == hs.size(), l > 0);
+    const bool ff = p->ff_operator && (p->precision == 0 || (p->precision == 2 && l == 0));
+    rc = setup_level(c->lev[l], c->S, l + 1 == hs.size(), l > 0, ff);
     if (rc) return cleanup(rc);
     if (l > 0 && (rc = setup_transfer(c->lev[l], c->lev[l - 1]))) return cleanup(rc);
   }

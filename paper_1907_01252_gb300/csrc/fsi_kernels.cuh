@@ -1533,3 +1533,52 @@ __global__ void __launch_bounds__(JAC_THREADS, 2) k_cell_jacobian_tc(DevMesh m, 
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 32);
 }
+
+// --------------------------------------------------------------------------
+// Float-float operator product for FP64 operators. GB300 runs FP64 at 1/64 of
+// the FP32 rate, which caps the FP64 block-sparse product (one FMA per 8-byte
+// value) below the HBM bandwidth. Here the blocks and the input vector are
+// carried as float pairs hi + lo (the same 8 bytes per value, 2^-48 relative)
+// and every row is accumulated with error-free FP32 transformations in the
+// manner of the compensated dot product Dot2 (fsi_ff.h): about 19 FP32
+// operations per term on the FP32 pipe, an accuracy of order 2^-48 relative
+// to the sum of |a x|, close to that of the FP64 product.
+// --------------------------------------------------------------------------
+#include "fsi_ff.h"
+
+// out[s][i] = (hi, lo) of x[s][i] for active slices
+__global__ void k_to_ff(size_t n, const double* __restrict__ x, size_t xstride, const uint8_t* __restrict__ active,
+                        float2* __restrict__ out, size_t ostride) {
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const fsiff::ff v = fsiff::split(x[s * xstride + i]);
+    out[s * ostride + i] = make_float2(v.hi, v.lo);
+  }
+}
+
+template <bool RESIDUAL>
+__global__ void k_bsr_spmv_ff(DevMesh m, const float2* __restrict__ A, const float2* __restrict__ x,
+                              const double* __restrict__ bvec, size_t stride, const uint8_t* __restrict__ active,
+                              double* __restrict__ y, const int* __restrict__ rows, int nrows) {
+  const int s = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!active[s] || t >= nrows * 5) return;
+  const int i = rows[t / 5], c = t % 5;
+  const float2* As = A + (size_t)s * m.nnzb * 25 + c * 5;
+  const float2* xs = x + s * stride;
+  fsiff::ffacc acc;
+  const int b1 = m.rowptr[i + 1];
+  for (int b = m.rowptr[i]; b < b1; ++b) {
+    const float2* blk = As + (size_t)b * 25;
+    const float2* xj = xs + (size_t)m.colidx[b] * 5;
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+      const float2 a = blk[e], v = xj[e];
+      fsiff::fma_ff(acc, fsiff::ff{a.x, a.y}, fsiff::ff{v.x, v.y});
+    }
+  }
+  const size_t o = s * stride + (size_t)i * 5 + c;
+  const double r = fsiff::result(acc);
+  y[o] = RESIDUAL ? bvec[o] - r : r;
+}

@@ -38,7 +38,8 @@ class fsi_params(C.Structure):
                 ("mg_smoother", C.c_int),
                 ("mg_coarse_lps", C.c_double), ("mg_reuse", C.c_int), ("mg_rebuild_every", C.c_int),
                 ("graph_max_batch", C.c_int), ("precision", C.c_int), ("pipeline_chunk", C.c_int),
-                ("max_batch", C.c_int), ("mg_coarse_sweeps", C.c_int), ("tc_contraction", C.c_int)]
+                ("max_batch", C.c_int), ("mg_coarse_sweeps", C.c_int), ("tc_contraction", C.c_int),
+                ("ff_operator", C.c_int)]
 
 
 class fsi_stats(C.Structure):
@@ -251,7 +252,7 @@ def _params(w: wl.Workload, max_batch: int, overrides):
              gmres_rtol_first=w.gmres_rtol_first, newton_eta=w.newton_eta,
              mg_coarsest_max_dofs=400, mg_smooth=2, mg_omega=0.6, mg_smoother=0, mg_coarse_lps=0.5, mg_reuse=2,
              mg_rebuild_every=4, graph_max_batch=4, precision=0, pipeline_chunk=0, max_batch=max_batch,
-             mg_coarse_sweeps=0, tc_contraction=1)
+             mg_coarse_sweeps=0, tc_contraction=1, ff_operator=0)
     p.update(overrides)
     return p
 
@@ -396,6 +397,7 @@ class Context:
         if rc != FSI_OK:
             err = FsiError(rc, self.lib.fsi_last_error().decode())
             err.slice_status = ss.tolist()
+            err.stats = st.as_dict()
             raise err
         d = st.as_dict()
         d["slice_status"] = ss.tolist()

@@ -346,3 +346,30 @@ def test_theta_step_128x32_matches_oracle():
     for s, ref in enumerate((Ub, Uc)):
         errs = rel_field_errors(got[s], ref)
         assert max(errs.values()) <= 1e-10, (s, errs)
+
+
+def test_float_float_operator_product_keeps_the_parity_bar():
+    """The Krylov operator and the multigrid residuals applied with float-pair
+    blocks and a compensated FP32 accumulation (ff_operator = 1): the theta step
+    still meets the 1e-10 bar against the oracle, stays within 1e-12 of the FP64
+    product, and a batch still equals its solo runs bit for bit."""
+    w = wl.SMALL_16x4
+    mesh = oracle_mesh(w)
+    k = w.k_fine
+    model, states = developed_states(w, mesh, 12, k)
+    pick = [5, 11]
+    U0 = np.stack([states[i] for i in pick])
+    t0 = [(i + 1) * k for i in pick]
+    th = 0.5 + k
+    ctx = ctx_for(w, 2, ff_operator=1)
+    ctx64 = ctx_for(w, 2, ff_operator=0)
+    Ub, st = ctx.fsi_theta_step(to_dev(U0), t0, k, th)
+    U64, st64 = ctx64.fsi_theta_step(to_dev(U0), t0, k, th)
+    got, g64 = Ub.cpu().numpy().reshape(2, -1, 5), U64.cpu().numpy().reshape(2, -1, 5)
+    for s, i in enumerate(pick):
+        ref = model.step(U0[s], t0[s], k, th)
+        assert max(rel_field_errors(got[s], ref).values()) <= 1e-10
+        assert max(rel_field_errors(got[s], g64[s]).values()) <= 1e-12
+        Us, _ = ctx.fsi_theta_step(to_dev(U0[s:s + 1]), [t0[s]], k, th)
+        assert torch.equal(Us[0], Ub[s])
+    assert st["newton_iters"] == st64["newton_iters"]
