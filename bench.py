@@ -260,7 +260,7 @@ def bench_3d(args, torch, fsi, wl, dev):
     32 x 8 x 8 channel workload per step, all 32 slices' fine solves batched."""
     w = wl.CHANNEL3D_32x8x8
     N = w.n_slices
-    ctx = fsi.Context3D(w, max_batch=N)
+    ctx = fsi.Context3D(w, max_batch=N, **overrides(args))
     U = torch.zeros((N + 1, ctx.n_dofs), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 

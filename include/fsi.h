@@ -42,7 +42,10 @@ enum {
   FSI_ENOMEM = -2,    /* device allocation failed */
   FSI_ECUDA = -3,     /* CUDA runtime error */
   FSI_ENEWTON = -4,   /* Newton did not reach its tolerance within newton_maxit */
-  FSI_EGMRES = -5,    /* FGMRES did not reach its tolerance within gmres_maxit */
+  FSI_EGMRES = -5,    /* as FSI_ENEWTON, after at least one of the slice's FGMRES solves
+                         stopped at gmres_maxit (such a solve's correction is still
+                         applied; a slice whose Newton iteration converges anyway
+                         succeeds) */
   FSI_EJAC = -6,      /* singular local block (Vanka or coarsest solve) or J <= 0 */
   FSI_ENAN = -7,      /* non-finite residual */
   FSI_EDIVERGE = -8   /* Parareal increment is not finite */
@@ -129,11 +132,13 @@ typedef struct fsi_params {
                               inverse; > 0 applies that many smoother sweeps there
                               instead (no inverse to build for each coarse step) */
   int tc_contraction;      /* 2D path, FP32 element matrices (precision 1, and the FP32
-                              multigrid levels of precision 2): 1 runs the element
-                              contraction B^T D B on the tensor cores (tcgen05.mma,
-                              each FP32 operand as three BF16 terms, FP32 accumulation
-                              in tensor memory), 0 on the CUDA cores in FP32. The
-                              tangent D is FP64 either way */
+                              multigrid levels of precision 2): 1 computes the tangent D
+                              in FP32 and runs the element contraction B^T D B on the
+                              tensor cores (tcgen05.mma, each FP32 operand as three BF16
+                              terms, FP32 accumulation in tensor memory); 0 computes D
+                              in FP64 and contracts on the CUDA cores in FP32. These
+                              matrices only feed the FP32 solver; the Newton residual
+                              stays FP64 either way */
   int ff_operator;         /* 2D path, FP64 operators (precision 0, and the Krylov
                               operator of precision 2): 1 applies the block-sparse
                               product in the Krylov solver and in the multigrid
@@ -217,8 +222,8 @@ int fsi_jacobian(fsi_ctx* ctx, int S, const double* U, const double* U_old,
 
 /* The same Jacobian with FP32 element matrices and FP32 blocks, as the FP32
  * linear solver builds it (precision 1): vals device float [S][nnzb][5][5].
- * The element contraction runs on the tensor cores or the CUDA cores as
- * params->tc_contraction says; the tangent is FP64. Errors: FSI_EINVAL,
+ * Tangent and element contraction as params->tc_contraction says (FP32 tangent
+ * and tensor cores, or FP64 tangent and CUDA cores). Errors: FSI_EINVAL,
  * FSI_ECUDA (also when a tensor-core MMA completion was not seen). */
 int fsi_jacobian_f32(fsi_ctx* ctx, int S, const double* U, const double* U_old,
                      double k, double theta, float* vals, void* stream);

@@ -25,6 +25,7 @@
 #include <mutex>
 #include <tuple>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1132,6 +1133,19 @@ int newton_correction(fsi_ctx* c, int S, double k, double theta, int it, int reu
   return rc;
 }
 
+// FSI_TRACE_NEWTON set in the environment: the residual history of every slice
+// whose step fails, and every FGMRES solve that stops at its limit, go to stderr.
+bool trace_newton() {
+  static const bool on = std::getenv("FSI_TRACE_NEWTON") != nullptr;
+  return on;
+}
+void trace_slice(const char* path, int s, double t_old, double k, int code, const std::vector<double>& h) {
+  std::fprintf(stderr, "[fsi trace] %s slice %d t=%.6g k=%.6g status %d, Newton residuals:", path, s, t_old + k, k,
+               code);
+  for (double x : h) std::fprintf(stderr, " %.3e", x);
+  std::fprintf(stderr, "\n");
+}
+
 // One theta step for S slices (Newton + FGMRES/multigrid).
 // reuse: what the preconditioner keeps across Newton iterations (see mg_reuse);
 // hierarchy_valid: the multigrid hierarchy of an earlier step of the same
@@ -1155,6 +1169,11 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
   TRY(launch_check());
   std::vector<double> r0(S, 0.0), nr(S);
   std::vector<int> nit(S, 0), why(S, 0);   // why: first failure code per slice
+  // gmiss: an FGMRES solve of the slice stopped at its iteration limit. Its correction is
+  // still applied (inexact Newton); the slice fails only if Newton then fails (FSI_EGMRES)
+  std::vector<uint8_t> gmiss(S, 0);
+  const bool trace = trace_newton();
+  std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
   for (int it = 0;; ++it) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
@@ -1172,13 +1191,15 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
         continue;
       }
       if (it == 0) r0[s] = nr[s];
+      if (trace) hist[s].push_back(nr[s]);
       if (it >= 1 && nr[s] <= c->prm.newton_tol * std::max(r0[s], 1.0)) {
         act[s] = 0;
         continue;
       }
       if (it >= c->prm.newton_maxit) {
-        status = FSI_ENEWTON;
-        if (!why[s]) why[s] = FSI_ENEWTON;
+        if (!why[s]) why[s] = gmiss[s] ? FSI_EGMRES : FSI_ENEWTON;
+        if (status == FSI_OK) status = why[s];
+        if (trace) trace_slice("2D", s, t_old[s], k, why[s], hist[s]);
         act[s] = 0;
         continue;
       }
@@ -1219,10 +1240,16 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
         status = why[s] = FSI_EJAC;
         act[s] = 0;
       }
-      if (act[s] && !why[s] && (int)c->slice_code.size() == S && c->slice_code[s]) why[s] = c->slice_code[s];
+      const int code = (int)c->slice_code.size() == S ? c->slice_code[s] : 0;
+      if (act[s] && code == FSI_EGMRES) {
+        gmiss[s] = 1;
+        if (trace) std::fprintf(stderr, "[fsi trace] 2D slice %d t=%.6g Newton it %d: FGMRES at its limit\n", s,
+                                t_old[s] + k, it);
+      } else if (act[s] && !why[s] && code) {
+        why[s] = code;
+      }
     }
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed: " + g_err);
-    if (rc == FSI_EGMRES) status = FSI_EGMRES;
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (stats) {

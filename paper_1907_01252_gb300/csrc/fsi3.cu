@@ -18,6 +18,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -934,7 +935,11 @@ int dots3(fsi3_ctx* c, int S, int nv, const double* V, size_t vstride, size_t vs
 // Hessenberg matrices and Givens rotations on the host (one synchronisation per iteration).
 template <typename T>
 int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t> act, double rtol,
-            const std::vector<double>& target, fsi_stats* stats, cudaStream_t st) {
+            const std::vector<double>& target, fsi_stats* stats, cudaStream_t st, std::vector<int>* codes = nullptr) {
+  // codes (optional, [S]): FSI_EGMRES or FSI_ENAN for the slices that stopped that way
+  auto mark = [&](int s, int code) {
+    if (codes) (*codes)[s] = code;
+  };
   fsi3_level& L = c->lev[0];
   const size_t n = c->n;
   const int m = c->m;
@@ -952,6 +957,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
     const double bn = std::sqrt(hb[(size_t)s * 64]);
     if (!std::isfinite(bn)) {
       status = FSI_ENAN;
+      mark(s, FSI_ENAN);
       act[s] = 0;
       continue;
     }
@@ -974,6 +980,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
       const double beta = std::sqrt(h1[(size_t)s * 64]);
       if (!std::isfinite(beta)) {
         status = FSI_ENAN;
+        mark(s, FSI_ENAN);
         act[s] = cyc[s] = 0;
         continue;
       }
@@ -983,6 +990,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
       }
       if (its[s] >= c->prm.gmres_maxit) {
         status = FSI_EGMRES;
+        mark(s, FSI_EGMRES);
         act[s] = cyc[s] = 0;
         continue;
       }
@@ -1051,6 +1059,7 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
         ++its[s];
         if (!std::isfinite(gs[j + 1])) {
           status = FSI_ENAN;
+          mark(s, FSI_ENAN);
           run[s] = 0;
           act[s] = 0;
         } else if (std::fabs(gs[j + 1]) <= tgt[s] || its[s] >= c->prm.gmres_maxit || !(den > 0.0)) {
@@ -1109,6 +1118,11 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
   TRY3(launched3());
   std::vector<double> r0(S, 0.0), nr(S), hr;
   std::vector<int> nit(S, 0), why(S, 0);
+  // gmiss: an FGMRES solve of the slice stopped at its iteration limit; its correction is
+  // still applied (inexact Newton), and the slice fails only if Newton then fails (FSI_EGMRES)
+  std::vector<uint8_t> gmiss(S, 0);
+  const bool trace = std::getenv("FSI_TRACE_NEWTON") != nullptr;
+  std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
   for (int it = 0;; ++it) {
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
@@ -1124,13 +1138,20 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
         continue;
       }
       if (it == 0) r0[s] = nr[s];
+      if (trace) hist[s].push_back(nr[s]);
       if (it >= 1 && nr[s] <= c->prm.newton_tol * std::max(r0[s], 1.0)) {
         act[s] = 0;
         continue;
       }
       if (it >= c->prm.newton_maxit) {
-        status = FSI_ENEWTON;
-        if (!why[s]) why[s] = FSI_ENEWTON;
+        if (!why[s]) why[s] = gmiss[s] ? FSI_EGMRES : FSI_ENEWTON;
+        if (status == FSI_OK) status = why[s];
+        if (trace) {
+          std::fprintf(stderr, "[fsi trace] 3D slice %d t=%.6g k=%.6g status %d, Newton residuals:", s,
+                       t_old[s] + k, k, why[s]);
+          for (double x : hist[s]) std::fprintf(stderr, " %.3e", x);
+          std::fprintf(stderr, "\n");
+        }
         act[s] = 0;
         continue;
       }
@@ -1158,8 +1179,9 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
     }
     P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, -1.0, c->R, n, 0.0, c->active, c->bk, n);
     TRY3(launched3());
-    int rc = c->mg32 ? fgmres3<float>(c, S, c->bk, c->xk, act, rtol, target, stats, st)
-                     : fgmres3<double>(c, S, c->bk, c->xk, act, rtol, target, stats, st);
+    std::vector<int> codes(S, 0);
+    int rc = c->mg32 ? fgmres3<float>(c, S, c->bk, c->xk, act, rtol, target, stats, st, &codes)
+                     : fgmres3<double>(c, S, c->bk, c->xk, act, rtol, target, stats, st, &codes);
     CK3(cudaMemcpyAsync(st_h.data(), c->status, S * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK3(cudaStreamSynchronize(st));
     for (int s = 0; s < S; ++s)
@@ -1168,7 +1190,17 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
         act[s] = 0;
       }
     if (rc != FSI_OK && rc != FSI_EGMRES && rc != FSI_ENAN) return rc;
-    if (rc == FSI_EGMRES || rc == FSI_ENAN) status = rc;
+    for (int s = 0; s < S; ++s) {
+      if (!act[s]) continue;
+      if (codes[s] == FSI_EGMRES) {
+        gmiss[s] = 1;
+        if (trace) std::fprintf(stderr, "[fsi trace] 3D slice %d t=%.6g Newton it %d: FGMRES at its limit\n", s,
+                                t_old[s] + k, it);
+      } else if (codes[s] == FSI_ENAN) {
+        if (!why[s]) why[s] = FSI_ENAN;
+        status = FSI_ENAN;
+      }
+    }
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, 1.0, c->xk, n, 1.0, c->active, c->Uit, n);
     TRY3(launched3());

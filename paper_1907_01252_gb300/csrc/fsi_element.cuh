@@ -19,26 +19,47 @@
 //   c = 4     divergence row (fluid cells, value slot)
 #pragma once
 
-struct M2 {
-  double a, b, c, d;  // [[a, b], [c, d]]
+// 2 x 2 matrices of the scalar type R: double for the residual and the FP64
+// tangent, float for the tangent of FP32 element matrices.
+template <typename R>
+struct M2T {
+  R a, b, c, d;  // [[a, b], [c, d]]
 };
+using M2 = M2T<double>;
 
 __host__ __device__ inline M2 m2(double a, double b, double c, double d) { return M2{a, b, c, d}; }
-__host__ __device__ inline M2 operator+(M2 x, M2 y) { return m2(x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d); }
-__host__ __device__ inline M2 operator-(M2 x, M2 y) { return m2(x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d); }
-__host__ __device__ inline M2 operator*(double s, M2 x) { return m2(s * x.a, s * x.b, s * x.c, s * x.d); }
-__host__ __device__ inline M2 mul(M2 x, M2 y) {
-  return m2(x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d);
+template <typename R>
+__host__ __device__ inline M2T<R> operator+(M2T<R> x, M2T<R> y) {
+  return M2T<R>{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d};
 }
-__host__ __device__ inline M2 tp(M2 x) { return m2(x.a, x.c, x.b, x.d); }
-__host__ __device__ inline double det(M2 x) { return x.a * x.d - x.b * x.c; }
-__host__ __device__ inline M2 adj(M2 x) { return m2(x.d, -x.b, -x.c, x.a); }   // adj(F) = det(F) F^{-1}
-__host__ __device__ inline double trace(M2 x) { return x.a + x.d; }
-__host__ __device__ inline void mv(M2 x, const double* v, double* out) {
+template <typename R>
+__host__ __device__ inline M2T<R> operator-(M2T<R> x, M2T<R> y) {
+  return M2T<R>{x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d};
+}
+template <typename R>
+__host__ __device__ inline M2T<R> operator*(R s, M2T<R> x) {
+  return M2T<R>{s * x.a, s * x.b, s * x.c, s * x.d};
+}
+template <typename R>
+__host__ __device__ inline M2T<R> mul(M2T<R> x, M2T<R> y) {
+  return M2T<R>{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+template <typename R>
+__host__ __device__ inline M2T<R> tp(M2T<R> x) { return M2T<R>{x.a, x.c, x.b, x.d}; }
+template <typename R>
+__host__ __device__ inline R det(M2T<R> x) { return x.a * x.d - x.b * x.c; }
+template <typename R>
+__host__ __device__ inline M2T<R> adj(M2T<R> x) { return M2T<R>{x.d, -x.b, -x.c, x.a}; }   // adj(F) = det(F) F^{-1}
+template <typename R>
+__host__ __device__ inline R trace(M2T<R> x) { return x.a + x.d; }
+template <typename R>
+__host__ __device__ inline void mv(M2T<R> x, const R* v, R* out) {
   out[0] = x.a * v[0] + x.b * v[1];
   out[1] = x.c * v[0] + x.d * v[1];
 }
-__host__ __device__ inline M2 eye2() { return m2(1.0, 0.0, 0.0, 1.0); }
+template <typename R>
+__host__ __device__ inline M2T<R> eye2t() { return M2T<R>{R(1), R(0), R(0), R(1)}; }
+__host__ __device__ inline M2 eye2() { return eye2t<double>(); }
 
 struct Phys {
   double rho_f, nu_f, rho_s, mu_s, lambda_s;
@@ -47,49 +68,54 @@ struct Phys {
 };
 
 // State at one quadrature point: new and old values and gradients.
-struct QpIn {
-  double v[2], u[2], p;
-  M2 G, Hu;             // grad v, grad u at t_n
-  double vo[2], uo[2];
-  M2 Go, Huo;           // grad v, grad u at t_{n-1}
+template <typename R>
+struct QpInT {
+  R v[2], u[2], p;
+  M2T<R> G, Hu;         // grad v, grad u at t_n
+  R vo[2], uo[2];
+  M2T<R> Go, Huo;       // grad v, grad u at t_{n-1}
 };
+using QpIn = QpInT<double>;
 
 // Quantities shared by the flux and its linearisation.
-struct QpDerived {
-  M2 F, A, C, Q;        // t_n: F, adj F, cof F, Q = G A C + C G^T C
-  double J;
-  M2 Fo, Ao, Co, Qo;
-  double Jo;
-  M2 Gh, Bh;            // midpoint grad v, F_{n-1/2}^{-1}
-  double Jh;            // (J_{n-1} + J_n) / 2
-  double w[2];          // u_n - u_{n-1}
-  double M[2];          // Gh Bh w
+template <typename R>
+struct QpDerivedT {
+  M2T<R> F, A, C, Q;    // t_n: F, adj F, cof F, Q = G A C + C G^T C
+  R J;
+  M2T<R> Fo, Ao, Co, Qo;
+  R Jo;
+  M2T<R> Gh, Bh;        // midpoint grad v, F_{n-1/2}^{-1}
+  R Jh;                 // (J_{n-1} + J_n) / 2
+  R w[2];               // u_n - u_{n-1}
+  R M[2];               // Gh Bh w
   // products shared by every direction of the linearisation
-  double invJ, invJ2;   // 1 / J, 1 / J^2
-  double Bw[2], Av[2];  // Bh w, A v
-  M2 GhBh, GA, AC, GtC, CGt;   // Gh Bh, G A, A C, G^T C, C G^T
+  R invJ, invJ2;        // 1 / J, 1 / J^2
+  R Bw[2], Av[2];       // Bh w, A v
+  M2T<R> GhBh, GA, AC, GtC, CGt;   // Gh Bh, G A, A C, G^T C, C G^T
 };
+using QpDerived = QpDerivedT<double>;
 
-__device__ inline void derive(const QpIn& q, QpDerived& d) {
-  d.F = eye2() + q.Hu;
+template <typename R>
+__device__ inline void derive(const QpInT<R>& q, QpDerivedT<R>& d) {
+  d.F = eye2t<R>() + q.Hu;
   d.J = det(d.F);
   d.A = adj(d.F);
   d.C = tp(d.A);
   d.Q = mul(mul(q.G, d.A), d.C) + mul(mul(d.C, tp(q.G)), d.C);
-  d.Fo = eye2() + q.Huo;
+  d.Fo = eye2t<R>() + q.Huo;
   d.Jo = det(d.Fo);
   d.Ao = adj(d.Fo);
   d.Co = tp(d.Ao);
   d.Qo = mul(mul(q.Go, d.Ao), d.Co) + mul(mul(d.Co, tp(q.Go)), d.Co);
-  d.Gh = 0.5 * (q.G + q.Go);
-  M2 Fh = eye2() + 0.5 * (q.Hu + q.Huo);
-  d.Bh = (1.0 / det(Fh)) * adj(Fh);
-  d.Jh = 0.5 * (d.J + d.Jo);
+  d.Gh = R(0.5) * (q.G + q.Go);
+  M2T<R> Fh = eye2t<R>() + R(0.5) * (q.Hu + q.Huo);
+  d.Bh = (R(1.0) / det(Fh)) * adj(Fh);
+  d.Jh = R(0.5) * (d.J + d.Jo);
   d.w[0] = q.u[0] - q.uo[0];
   d.w[1] = q.u[1] - q.uo[1];
   mv(d.Bh, d.w, d.Bw);
   mv(d.Gh, d.Bw, d.M);
-  d.invJ = 1.0 / d.J;
+  d.invJ = R(1.0) / d.J;
   d.invJ2 = d.invJ * d.invJ;
   mv(d.A, q.v, d.Av);
   d.GhBh = mul(d.Gh, d.Bh);
@@ -141,27 +167,27 @@ __device__ inline void qp_flux(const Phys& P, const QpIn& q, const QpDerived& d,
 
 // Directional derivative of qp_flux in the direction (dv, dG, du, dH, dp) of
 // the t_n unknowns: out[c * 3 + a].
-__device__ inline void qp_flux_lin(const Phys& P, const QpIn& q, const QpDerived& d, bool solid, double k,
-                                   double theta, const double* dv, M2 dG, const double* du, M2 dH, double dp,
-                                   double* out) {
-  for (int i = 0; i < 15; ++i) out[i] = 0.0;
-  const double kt = k * theta, kto = k * (1.0 - theta);
+template <typename R>
+__device__ inline void qp_flux_lin(const Phys& P, const QpInT<R>& q, const QpDerivedT<R>& d, bool solid, R k,
+                                   R theta, const R* dv, M2T<R> dG, const R* du, M2T<R> dH, R dp, R* out) {
+  for (int i = 0; i < 15; ++i) out[i] = R(0.0);
+  const R kt = k * theta, kto = k * (R(1.0) - theta);
   if (!solid) {
-    const double rf = P.rho_f, rn = P.rho_f * P.nu_f;
-    const double dJ = trace(mul(d.A, dH));      // d det F = tr(adj(F) dF)
-    const M2 dA = adj(dH);                       // adj is linear in 2D
-    const M2 dC = tp(dA);
+    const R rf = R(P.rho_f), rn = R(P.rho_f * P.nu_f);
+    const R dJ = trace(mul(d.A, dH));           // d det F = tr(adj(F) dF)
+    const M2T<R> dA = adj(dH);                   // adj is linear in 2D
+    const M2T<R> dC = tp(dA);
     // ALE mass / domain convection term with midpoint means:
     // d(Gh Bh w) = dGh Bh w + Gh dBh w + Gh Bh dw, dBh = -Bh dFh Bh, dFh = dH / 2
-    const double dJh = 0.5 * dJ;
-    double t1[2], t2[2], t3[2], t4[2], dM[2];
+    const R dJh = R(0.5) * dJ;
+    R t1[2], t2[2], t3[2], t4[2], dM[2];
     mv(dG, d.Bw, t2);
     mv(dH, d.Bw, t1);
     mv(d.GhBh, t1, t3);
     mv(d.GhBh, du, t4);
-    for (int c = 0; c < 2; ++c) dM[c] = 0.5 * t2[c] - 0.5 * t3[c] + t4[c];
+    for (int c = 0; c < 2; ++c) dM[c] = R(0.5) * t2[c] - R(0.5) * t3[c] + t4[c];
     // convection G A v
-    double dGAv[2], GdAv[2], GAdv[2];
+    R dGAv[2], GdAv[2], GAdv[2];
     mv(dG, d.Av, dGAv);
     mv(dA, q.v, t1);
     mv(q.G, t1, GdAv);
@@ -171,22 +197,22 @@ __device__ inline void qp_flux_lin(const Phys& P, const QpIn& q, const QpDerived
                    kt * rf * (dGAv[c] + GdAv[c] + GAdv[c]);
     }
     // stress (rho nu / J) Q - p C, Q = G A C + C G^T C
-    M2 dQ = mul(dG, d.AC) + mul(mul(q.G, dA), d.C) + mul(d.GA, dC) + mul(dC, d.GtC) +
-            mul(mul(d.C, tp(dG)), d.C) + mul(d.CGt, dC);
-    M2 S = kt * ((rn * d.invJ) * dQ - (rn * dJ * d.invJ2) * d.Q - dp * d.C - q.p * dC) - (kto * dp) * d.Co;
+    M2T<R> dQ = mul(dG, d.AC) + mul(mul(q.G, dA), d.C) + mul(d.GA, dC) + mul(dC, d.GtC) +
+                mul(mul(d.C, tp(dG)), d.C) + mul(d.CGt, dC);
+    M2T<R> S = kt * ((rn * d.invJ) * dQ - (rn * dJ * d.invJ2) * d.Q - dp * d.C - q.p * dC) - (kto * dp) * d.Co;
     out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
-    M2 Hh = kt * dH;
+    M2T<R> Hh = kt * dH;
     out[7] = Hh.a; out[8] = Hh.b; out[10] = Hh.c; out[11] = Hh.d;
     out[12] = k * (trace(mul(dG, d.A)) + trace(mul(q.G, dA)));
   } else {
-    const double mu = P.mu_s, lam = P.lambda_s;
-    M2 E = 0.5 * (mul(tp(d.F), d.F) - eye2());
-    M2 Sig = 2.0 * mu * E + (lam * trace(E)) * eye2();
-    M2 dE = 0.5 * (mul(tp(dH), d.F) + mul(tp(d.F), dH));
-    M2 dSig = 2.0 * mu * dE + (lam * trace(dE)) * eye2();
-    M2 S = kt * (mul(dH, Sig) + mul(d.F, dSig));
+    const R mu = R(P.mu_s), lam = R(P.lambda_s);
+    M2T<R> E = R(0.5) * (mul(tp(d.F), d.F) - eye2t<R>());
+    M2T<R> Sig = R(2.0) * mu * E + (lam * trace(E)) * eye2t<R>();
+    M2T<R> dE = R(0.5) * (mul(tp(dH), d.F) + mul(tp(d.F), dH));
+    M2T<R> dSig = R(2.0) * mu * dE + (lam * trace(dE)) * eye2t<R>();
+    M2T<R> S = kt * (mul(dH, Sig) + mul(d.F, dSig));
     for (int c = 0; c < 2; ++c) {
-      out[c * 3] = P.rho_s * dv[c];
+      out[c * 3] = R(P.rho_s) * dv[c];
       out[6 + c * 3] = du[c] - kt * dv[c];
     }
     out[1] = S.a; out[2] = S.b; out[4] = S.c; out[5] = S.d;
@@ -206,19 +232,21 @@ __device__ inline void edge_flux(const Phys& P, M2 G, M2 Hu, M2 Go, M2 Huo, doub
   out[1] = -k * theta * rn / J * T.c - k * (1.0 - theta) * rn / Jo * To.c;
 }
 
-__device__ inline void edge_flux_lin(const Phys& P, M2 G, M2 Hu, M2 dG, M2 dH, double k, double theta, double* out) {
-  const double rn = P.rho_f * P.nu_f;
-  M2 F = eye2() + Hu;
-  M2 A = adj(F), C = tp(A);
-  double J = det(F);
-  double dJ = trace(mul(A, dH));
-  M2 dC = tp(adj(dH));
-  M2 Gt = tp(G);
-  M2 T = mul(mul(C, Gt), C);
-  M2 dT = mul(mul(dC, Gt), C) + mul(mul(C, tp(dG)), C) + mul(mul(C, Gt), dC);
-  M2 R = (-k * theta * rn) * ((1.0 / J) * dT - (dJ / (J * J)) * T);
-  out[0] = R.a;
-  out[1] = R.c;
+template <typename R>
+__device__ inline void edge_flux_lin(const Phys& P, M2T<R> G, M2T<R> Hu, M2T<R> dG, M2T<R> dH, R k, R theta,
+                                     R* out) {
+  const R rn = R(P.rho_f * P.nu_f);
+  M2T<R> F = eye2t<R>() + Hu;
+  M2T<R> A = adj(F), C = tp(A);
+  R J = det(F);
+  R dJ = trace(mul(A, dH));
+  M2T<R> dC = tp(adj(dH));
+  M2T<R> Gt = tp(G);
+  M2T<R> T = mul(mul(C, Gt), C);
+  M2T<R> dT = mul(mul(dC, Gt), C) + mul(mul(C, tp(dG)), C) + mul(mul(C, Gt), dC);
+  M2T<R> Rv = (-k * theta * rn) * ((R(1.0) / J) * dT - (dJ / (J * J)) * T);
+  out[0] = Rv.a;
+  out[1] = Rv.c;
 }
 
 // Directional derivative of qp_flux with respect to the t_{n-1} state

@@ -1373,23 +1373,25 @@ __global__ void __launch_bounds__(FMA_PROBE_THREADS) k_fma_probe(int iters, doub
 }
 
 // --------------------------------------------------------------------------
-// Element Jacobian with the B^T D B contraction on the tensor cores (FP32
-// element matrices, for the FP32 linear solver and FP32 multigrid levels).
-// The tangent stage is that of k_cell_jacobian (FP64). The contraction
+// Element Jacobian for FP32 element matrices (the FP32 linear solver of
+// precision 1, the FP32 multigrid levels of precision 2), with the tangent in
+// FP32 and the B^T D B contraction on the tensor cores. The matrices only
+// feed the FP32 solver: the Newton residual, and with it J = det F of the
+// discrete equations, stays FP64.
 //   K[(i,ci)][(j,cj)] = sum_{q,a} B_a(i,q) E_q[(ci,a)][(j,cj)]
-// becomes one product D = A B^T per cell with
-//   A[m][kk] = s_a E_q[(ci,a)][(j,cj)],  m = ci*45 + j*5 + cj (225 rows, padded to 256),
+// is one product D = A B^T per cell with
+//   A[m][kk] = s_a E_q[(ci,a)][(j,cj)],  m = ci*45 + j*5 + cj (225 rows, two tiles of 128),
 //   B[i][kk] = reference-cell basis value (a = 0) or s / t derivative (a = 1, 2) of
 //              node i at Gauss point q (9 rows, padded to 16), kk = q*3 + a (27, padded to 32),
-// s_a = 1, 1/hx, 1/hy the reference-to-cell derivative factors, and D[m][i] the entry
-// K[(i,ci)][(j,cj)]. Both operands enter tcgen05.mma (kind::f16, M = 128, N = 16,
-// K = 16) as three BF16 terms (FP32-level accuracy), two M tiles accumulate in
-// 32 FP32 columns of tensor memory. Blocks the material does not couple are
-// exactly zero rows of A; the other blocks of the element matrix (zero, the
-// closed-form stabilisation block) and the outflow-edge term are written as in
-// k_cell_jacobian. When the MMA completion is not seen within the poll limit the
-// element matrix is filled with NaN (the solve then stops with FSI_ENAN) and
-// *status is set.
+// s_a = 1, 1/hx, 1/hy the reference-to-cell derivative factors, E_q = w_q D_q B_q
+// and D[m][i] the entry K[(i,ci)][(j,cj)]. Both operands enter tcgen05.mma
+// (kind::f16, M = 128, N = 16, K = 16) as three BF16 terms (FP32-level
+// accuracy); the two M tiles are built one after the other in one buffer and
+// accumulate in 32 FP32 columns of tensor memory. Blocks the material does
+// not couple are exactly zero rows of A; the closed-form stabilisation block
+// and the outflow-edge term are added as in k_cell_jacobian. When an MMA
+// completion is not seen within the poll limit the element matrix is filled
+// with NaN (the solve then stops with FSI_ENAN) and *status is set.
 // --------------------------------------------------------------------------
 __constant__ float c_phif[9][9];
 __constant__ float c_dpsf[9][9];
@@ -1397,12 +1399,38 @@ __constant__ float c_dptf[9][9];
 __constant__ float c_wqf[9];
 
 constexpr int JTC_NS = 3;                          // BF16 terms per FP32 operand
-constexpr int JTC_A_TERM = 256 * 32 * 2;           // bytes of one A term
+constexpr int JTC_A_TERM = 128 * 32 * 2;           // bytes of one A term of one tile
 constexpr int JTC_B_TERM = 16 * 32 * 2;
 constexpr int JTC_SMEM = JTC_NS * (JTC_A_TERM + JTC_B_TERM) + 2048;   // operands + slack
 static_assert(JAC_THREADS >= 128, "the tensor-memory read-back takes four warps");
 
-__global__ void __launch_bounds__(JAC_THREADS, 2) k_cell_jacobian_tc(DevMesh m, Phys P, const double* __restrict__ U,
+// Shared state of the FP32 tangent stage.
+struct JacTangentShared32 {
+  double sU[45], sUo[45];
+  QpInT<float> sq[9];
+  QpDerivedT<float> sd[9];
+  float sD[9][15][15];      // [q][test slot][trial direction]
+  float sDe[3][2][12];      // outflow edge: [q][momentum comp][trial direction (c<4)]
+  double sAlpha;
+};
+
+__device__ inline QpInT<float> qp_to_float(const QpIn& a) {
+  QpInT<float> b;
+  for (int i = 0; i < 2; ++i) {
+    b.v[i] = (float)a.v[i];
+    b.u[i] = (float)a.u[i];
+    b.vo[i] = (float)a.vo[i];
+    b.uo[i] = (float)a.uo[i];
+  }
+  b.p = (float)a.p;
+  b.G = M2T<float>{(float)a.G.a, (float)a.G.b, (float)a.G.c, (float)a.G.d};
+  b.Hu = M2T<float>{(float)a.Hu.a, (float)a.Hu.b, (float)a.Hu.c, (float)a.Hu.d};
+  b.Go = M2T<float>{(float)a.Go.a, (float)a.Go.b, (float)a.Go.c, (float)a.Go.d};
+  b.Huo = M2T<float>{(float)a.Huo.a, (float)a.Huo.b, (float)a.Huo.c, (float)a.Huo.d};
+  return b;
+}
+
+__global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, Phys P, const double* __restrict__ U,
                                                                     const double* __restrict__ Uold, size_t stride,
                                                                     double k, double theta, double lps_scale,
                                                                     const uint8_t* __restrict__ active,
@@ -1411,93 +1439,152 @@ __global__ void __launch_bounds__(JAC_THREADS, 2) k_cell_jacobian_tc(DevMesh m, 
   const int cell = blockIdx.x;
   if (!active[s]) return;   // uniform over the CTA, before any tensor-memory allocation
   extern __shared__ __align__(1024) unsigned char jtc[];
-  __shared__ JacTangentShared sh;
-  __shared__ float sDf[9][15][15];
+  __shared__ JacTangentShared32 sh;
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
   if (tid == 0) tc::mbar_init(&bar, 1);
-  jac_tangent<false>(m, P, U, Uold, stride, k, theta, lps_scale, s, cell, sh);
   const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
   const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
   const uint8_t cf = m.cell_flags[cell];
   const bool solid = cf & CF_SOLID;
   const bool outflow = !solid && (cf & CF_OUTFLOW);
-  for (int e = tid; e < 9 * 15 * 15; e += JAC_THREADS) (&sDf[0][0][0])[e] = (float)(&sh.sD[0][0][0])[e];
+  // ---- FP32 tangent: the states at the Gauss points (FP64 interpolation, then FP32) ----
+  if (tid < 45) {
+    sh.sU[tid] = U[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+    sh.sUo[tid] = Uold[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+  }
   __syncthreads();
-  unsigned char* sA = jtc;
-  unsigned char* sB = jtc + JTC_NS * JTC_A_TERM;
-  const float fihx = (float)ihx, fihy = (float)ihy, farea = (float)area;
-  // B: 16 rows x 4 chunks of 8 K values; A: 256 rows x 4 chunks
-  for (int item = tid; item < 16 * 4 + 256 * 4; item += JAC_THREADS) {
-    const bool isB = item < 64;
-    const int row = isB ? item / 4 : (item - 64) / 4, c = item % 4;
-    float v[8];
-    if (isB) {
-#pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
-        v[x] = (row < 9 && kk < 27) ? (a == 0 ? c_phif[q][row] : (a == 1 ? c_dpsf[q][row] : c_dptf[q][row])) : 0.f;
-      }
+  if (tid < 9) {
+    QpIn q;
+    eval_qp(sh.sU, sh.sUo, tid, ihx, ihy, q);
+    sh.sq[tid] = qp_to_float(q);
+    derive(sh.sq[tid], sh.sd[tid]);
+  }
+  if (tid == 32 && !solid) sh.sAlpha = lps_scale * lps_weight(P, sh.sUo, hx, hy);
+  __syncthreads();
+  const float fk = (float)k, fth = (float)theta;
+  for (int t = tid; t < 9 * 15; t += JAC_THREADS) {
+    const int q = t / 15, dir = t % 15, cj = dir / 3, b = dir % 3;
+    float dv[2] = {0.f, 0.f}, du[2] = {0.f, 0.f}, dp = 0.f;
+    M2T<float> dG{0.f, 0.f, 0.f, 0.f}, dH{0.f, 0.f, 0.f, 0.f};
+    if (cj < 2) {
+      if (b == 0) dv[cj] = 1.f;
+      else if (cj == 0) { if (b == 1) dG.a = 1.f; else dG.b = 1.f; }
+      else { if (b == 1) dG.c = 1.f; else dG.d = 1.f; }
+    } else if (cj < 4) {
+      const int c = cj - 2;
+      if (b == 0) du[c] = 1.f;
+      else if (c == 0) { if (b == 1) dH.a = 1.f; else dH.b = 1.f; }
+      else { if (b == 1) dH.c = 1.f; else dH.d = 1.f; }
     } else {
-      const int ci = row / 45, j = (row / 5) % 9, cj = row % 5;
-      const bool live = row < 225 && jac_block_nonzero(solid, ci, cj);
-#pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
-        float e = 0.f;
-        if (live && kk < 27) {
-          const float* Dr = &sDf[q][ci * 3 + a][cj * 3];
-          const float sa = a == 0 ? 1.f : (a == 1 ? fihx : fihy);
-          e = sa * c_wqf[q] * farea *
-              (Dr[0] * c_phif[q][j] + Dr[1] * (c_dpsf[q][j] * fihx) + Dr[2] * (c_dptf[q][j] * fihy));
-        }
-        v[x] = e;
+      if (b == 0) dp = 1.f;
+    }
+    float out[15];
+    qp_flux_lin(P, sh.sq[q], sh.sd[q], solid, fk, fth, dv, dG, du, dH, dp, out);
+    for (int r = 0; r < 15; ++r) sh.sD[q][r][dir] = out[r];
+  }
+  if (outflow) {
+    for (int t = tid; t < 3 * 12; t += JAC_THREADS) {
+      const int q = t / 12, dir = t % 12, cj = dir / 3, b = dir % 3;
+      M2 G, Hu;
+      eval_edge_grad(sh.sU, q, ihx, ihy, G, Hu);
+      const M2T<float> Gf{(float)G.a, (float)G.b, (float)G.c, (float)G.d};
+      const M2T<float> Hf{(float)Hu.a, (float)Hu.b, (float)Hu.c, (float)Hu.d};
+      M2T<float> dG{0.f, 0.f, 0.f, 0.f}, dH{0.f, 0.f, 0.f, 0.f};
+      float out[2] = {0.f, 0.f};
+      if (b > 0) {
+        M2T<float>& X = cj < 2 ? dG : dH;
+        const int c = cj % 2;
+        if (c == 0) { if (b == 1) X.a = 1.f; else X.b = 1.f; }
+        else { if (b == 1) X.c = 1.f; else X.d = 1.f; }
+        edge_flux_lin(P, Gf, Hf, dG, dH, fk, fth, out);
       }
-    }
-    uint32_t w[JTC_NS][4];
-#pragma unroll
-    for (int x = 0; x < 8; x += 2) {
-      __nv_bfloat16 t0[JTC_NS], t1[JTC_NS];
-      tc::split_bf16<JTC_NS>(v[x], t0);
-      tc::split_bf16<JTC_NS>(v[x + 1], t1);
-#pragma unroll
-      for (int t = 0; t < JTC_NS; ++t)
-        w[t][x / 2] = (uint32_t)__bfloat16_as_ushort(t0[t]) | ((uint32_t)__bfloat16_as_ushort(t1[t]) << 16);
-    }
-    const uint32_t off = tc::kmajor_offset(row, c * 8, 4);
-#pragma unroll
-    for (int t = 0; t < JTC_NS; ++t) {
-      unsigned char* base = isB ? sB + t * JTC_B_TERM : sA + t * JTC_A_TERM;
-      *reinterpret_cast<uint4*>(base + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      sh.sDe[q][0][dir] = out[0];
+      sh.sDe[q][1][dir] = out[1];
     }
   }
-  tc::fence_async_smem();
-  tc::fence_before_sync();
   __syncthreads();
-  tc::fence_after_sync();
+  // ---- the contraction on the tensor cores ----
+  unsigned char* sA = jtc;                          // one tile: JTC_NS terms of 128 x 32
+  unsigned char* sB = jtc + JTC_NS * JTC_A_TERM;
+  const float fihx = (float)ihx, fihy = (float)ihy, farea = (float)area;
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
-    for (int tile = 0; tile < 2; ++tile) {
+  bool ok = true;
+  for (int tile = 0; tile < 2; ++tile) {
+    // B (first tile only): 16 rows x 4 chunks of 8 K values; A: 128 rows x 4 chunks
+    const int nitems = (tile == 0 ? 64 : 0) + 128 * 4;
+    for (int item = tid; item < nitems; item += JAC_THREADS) {
+      const bool isB = tile == 0 && item < 64;
+      const int local = isB ? item / 4 : (item - (tile == 0 ? 64 : 0)) / 4, c = item % 4;
+      float v[8];
+      if (isB) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
+          v[x] = (local < 9 && kk < 27) ? (a == 0 ? c_phif[q][local] : (a == 1 ? c_dpsf[q][local] : c_dptf[q][local]))
+                                        : 0.f;
+        }
+      } else {
+        const int row = tile * 128 + local;
+        const int ci = row / 45, j = (row / 5) % 9, cj = row % 5;
+        const bool live = row < 225 && jac_block_nonzero(solid, ci, cj);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
+          float e = 0.f;
+          if (live && kk < 27) {
+            const float* Dr = &sh.sD[q][ci * 3 + a][cj * 3];
+            const float sa = a == 0 ? 1.f : (a == 1 ? fihx : fihy);
+            e = sa * c_wqf[q] * farea *
+                (Dr[0] * c_phif[q][j] + Dr[1] * (c_dpsf[q][j] * fihx) + Dr[2] * (c_dptf[q][j] * fihy));
+          }
+          v[x] = e;
+        }
+      }
+      uint32_t w[JTC_NS][4];
+#pragma unroll
+      for (int x = 0; x < 8; x += 2) {
+        __nv_bfloat16 t0[JTC_NS], t1[JTC_NS];
+        tc::split_bf16<JTC_NS>(v[x], t0);
+        tc::split_bf16<JTC_NS>(v[x + 1], t1);
+#pragma unroll
+        for (int t = 0; t < JTC_NS; ++t)
+          w[t][x / 2] = (uint32_t)__bfloat16_as_ushort(t0[t]) | ((uint32_t)__bfloat16_as_ushort(t1[t]) << 16);
+      }
+      const uint32_t off = tc::kmajor_offset(local, c * 8, 4);
+#pragma unroll
+      for (int t = 0; t < JTC_NS; ++t) {
+        unsigned char* base = isB ? sB + t * JTC_B_TERM : sA + t * JTC_A_TERM;
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 16);
       int issued = 0;
       for (int ks = 0; ks < 2; ++ks)
         for (int p = 0; p < tc::SplitPairs<JTC_NS>::count; ++p) {
-          const uint32_t a0 = tc::smem_u32(sA + tc::SplitPairs<JTC_NS>::a(p) * JTC_A_TERM) + tile * 8192 + ks * 256;
+          const uint32_t a0 = tc::smem_u32(sA + tc::SplitPairs<JTC_NS>::a(p) * JTC_A_TERM) + ks * 256;
           const uint32_t b0 = tc::smem_u32(sB + tc::SplitPairs<JTC_NS>::b(p) * JTC_B_TERM) + ks * 256;
           tc::mma_bf16(tmem + tile * 16, tc::smem_desc(a0, 128, 512), tc::smem_desc(b0, 128, 512), idesc,
                        issued++ > 0);
         }
+      tc::mma_commit(&bar);
     }
-    tc::mma_commit(&bar);
+    __syncwarp();
+    // the wait also frees the operand buffer for the next tile
+    bool done = tc::mbar_wait(&bar, tile, tc::kMaxPolls);
+    if (!done) done = tc::mbar_wait(&bar, tile, tc::kMaxPolls);   // the MMAs in flight get a second chance
+    ok = __syncthreads_and(ok && done);                              // one outcome for the whole CTA
+    tc::fence_after_sync();
+    if (!ok) break;
   }
-  __syncwarp();
-  bool ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);
-  if (!ok) ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);   // the MMAs in flight get a second chance
-  ok = __syncthreads_and(ok);                            // one outcome for the whole CTA
   if (!ok && tid == 0) atomicExch(status, 1);
-  tc::fence_after_sync();
   float* out = Ke + ((size_t)s * m.n_cells + cell) * 2025;
   if (warp < 4) {
     for (int tile = 0; tile < 2; ++tile) {
@@ -1508,15 +1595,15 @@ __global__ void __launch_bounds__(JAC_THREADS, 2) k_cell_jacobian_tc(DevMesh m, 
       const int ci = row / 45, j = (row / 5) % 9, cj = row % 5;
       if (!jac_block_nonzero(solid, ci, cj)) continue;
       for (int i = 0; i < 9; ++i) {
-        double v = ok ? (double)d[i] : __longlong_as_double(0x7ff8000000000000ll);
+        float v = ok ? d[i] : __int_as_float(0x7fc00000);
         if (outflow && ci < 2 && cj < 4) {
           for (int q = 0; q < 3; ++q) {
-            const double Bj[3] = {c_phie[q][j], c_dpse[q][j] * ihx, c_dpte[q][j] * ihy};
-            const double* Drow = sh.sDe[q][ci] + cj * 3;
-            v += c_we[q] * hy * c_phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+            const float Bj[3] = {(float)c_phie[q][j], (float)(c_dpse[q][j] * ihx), (float)(c_dpte[q][j] * ihy)};
+            const float* Drow = sh.sDe[q][ci] + cj * 3;
+            v += (float)(c_we[q] * hy * c_phie[q][i]) * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
           }
         }
-        out[(i * 5 + ci) * 45 + j * 5 + cj] = (float)v;
+        out[(i * 5 + ci) * 45 + j * 5 + cj] = v;
       }
     }
   }

@@ -60,12 +60,15 @@ def test_newton_iteration_limit_reports_enewton():
 
 
 def test_gmres_iteration_limit_reports_egmres():
+    """Linear solves stopped at their iteration limit still correct the Newton
+    iterate; when Newton then fails, the slice reports FSI_EGMRES (the cause)."""
     from paper_1907_01252_gb300 import fsi
     ctx = ctx_for(S=1, gmres_maxit=2, newton_maxit=3)
     U = torch.zeros((1, ctx.n_dofs), dtype=torch.float64, device=DEV)
     with pytest.raises(fsi.FsiError) as e:
         ctx.fsi_theta_step(U, [0.0], W.k_coarse, 1.0)
-    assert e.value.code in (fsi.FSI_EGMRES, fsi.FSI_ENEWTON)
+    assert e.value.code == fsi.FSI_EGMRES
+    assert e.value.slice_status == [fsi.FSI_EGMRES]
 
 
 def test_bad_sizes_are_rejected():

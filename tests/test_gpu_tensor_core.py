@@ -59,10 +59,11 @@ def test_split_terms_reach_fp32_accuracy(nsplit, tol):
 
 
 def test_tensor_core_element_jacobian_matches_the_fp64_jacobian():
-    """The FP32 Jacobian with the element contraction on the tensor cores (three
-    BF16 terms per operand) against the FP64 Jacobian, row by row, as close as
-    the FP32 contraction on the CUDA cores; a mesh with odd segment counts,
-    solid cells and outflow cells, two slices at different states."""
+    """The FP32 Jacobian with the FP32 tangent and the element contraction on
+    the tensor cores (three BF16 terms per operand) against the FP64 Jacobian,
+    row by row, within 1e-5 of the row's largest entry (the CUDA-core variant,
+    FP64 tangent and FP32 contraction, within 2e-6); a mesh with odd segment
+    counts, solid cells and outflow cells, two slices at different states."""
     from paper_1907_01252_gb300 import fsi, workloads as wl
     w = wl.Workload("tcj", nx=24, ny=6, T=1.0, n_slices=4, m_fine=4)
     S = 2
@@ -85,7 +86,7 @@ def test_tensor_core_element_jacobian_matches_the_fp64_jacobian():
         sc = scale[brow][:, :, None]
         e_tc = (np.abs(Atc[s] - A64[s]) / sc).max()
         e_cc = (np.abs(Acc[s] - A64[s]) / sc).max()
-        assert e_tc <= 2e-6, (s, e_tc, e_cc)
+        assert e_tc <= 1e-5, (s, e_tc, e_cc)
         assert e_cc <= 2e-6, (s, e_tc, e_cc)
     # the same bits on a second call
     assert np.array_equal(ctx.fsi_jacobian_f32(U, Uo, k, th).cpu().numpy().astype(np.float64), Atc)
