@@ -2,15 +2,19 @@
 workload (83,525 dofs per state, T = 2, 64 slices x 32 fine shifted
 Crank-Nicolson steps, FP64 throughout).
 
-The line follows one continuing Parareal run (Sec. 3). The predictor sweep
+The line follows a continuing Parareal run (Sec. 3). The predictor sweep
 (64 implicit-Euler steps) comes first, untimed; then one step = one Parareal
 iteration (parareal_continue): the fine propagator of every slice not yet exact,
 batched (32 steps of all those slices at once: residual, Jacobian,
 multigrid-FGMRES Newton), then the corrected coarse sweep with the correction.
 The first --warmup iterations are untimed, the next --steps are timed.
-value = fine time-steps advanced per second over the timed iterations. Each
-timed step also copies the iterate in from pinned host memory and back out,
-and the same loop gives the end-to-end figure.
+value = fine time-steps advanced per second over the timed steps. Each timed
+step also copies the iterate in from pinned host memory and back out, and the
+same loop gives the end-to-end figure. On this workload the iterates beyond the
+exact front grow from iteration to iteration until a propagator's solve fails
+(about iteration 23); that step ends the run, a new run starts from the
+predictor, and the failed step stays in the timed total without advancing any
+fine step.
 
 Against the metric's accuracy: the serial fine solution of the whole interval
 is computed first on the same GPU (timed: the serial single-slice figure), and
@@ -418,17 +422,56 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
     # the run: predictor sweep, then W warm-up iterations (the last one finds the dominant kernel)
     U = torch.zeros((N + 1, n), dtype=torch.float64, device=dev)
     _, t_pred = timed(stream, torch, lambda: ctx.parareal_iterate(U, 0, 0.0))
-    iters = []
-    saved = []
+    # One step: the next Parareal iteration of the current run. On this workload the
+    # iterates beyond the exact front grow until a propagator's solve fails; such a
+    # step ends the run, the run is restarted from the predictor, and the failed step
+    # (with the restart) stays in the timed total while advancing nothing.
+    runs = [{"run": 1, "predictor_seconds": t_pred, "ended": None}]
+    steps = []       # every step: warm-up and timed
+    saved = {}       # step index -> iterate after it (successful steps)
     names = fsi.kernel_names()
+    hU = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+
+    def one_step(timed_step, host_copies):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        if host_copies:
+            U.copy_(hU, non_blocking=True)
+        e[1].record(stream)
+        prev_it = steps[-1]["iteration"] if steps and steps[-1]["run"] == runs[-1]["run"] else 0
+        rec = {"run": runs[-1]["run"], "timed": timed_step}
+        try:
+            if runs[-1]["ended"]:
+                raise fsi.FsiError(fsi.FSI_EINVAL, "no run to continue: " + runs[-1]["ended"])
+            _, st = ctx.parareal_continue(U, 1, 0.0)
+            S = N - (st["iterations"] - 1) if st["iterations"] > prev_it else 0   # no iteration runs past N
+            rec.update({"iteration": st["iterations"], "fine_slices": S, "fine_gmres": st["fine"]["gmres_iters"],
+                        "coarse_gmres": st["coarse"]["gmres_iters"], "failed": None})
+        except fsi.FsiError as err:
+            rec.update({"iteration": prev_it + 1, "fine_slices": 0, "failed": {"code": err.code, "message": str(err)}})
+            if not runs[-1]["ended"]:
+                runs[-1]["ended"] = "iteration %d: %s" % (prev_it + 1, err)
+                U[1:].zero_()
+                try:
+                    ctx.parareal_iterate(U, 0, 0.0)   # a new run: the predictor sweep
+                    runs.append({"run": runs[-1]["run"] + 1, "predictor_seconds": None, "ended": None})
+                except fsi.FsiError as err2:
+                    runs.append({"run": runs[-1]["run"] + 1, "predictor_seconds": None,
+                                 "ended": "predictor: %s" % err2})
+        e[2].record(stream)
+        if host_copies:
+            hU.copy_(U, non_blocking=True)
+        e[3].record(stream)
+        if rec["failed"] is None:
+            saved[len(steps)] = U.clone()
+        rec["_ev"] = e
+        steps.append(rec)
+
     for i in range(args.warmup):
         if i == args.warmup - 1:
             fsi.profile_enable(names)
-        S = max(0, N - len(iters))
-        (_, st), ti = timed(stream, torch, lambda: ctx.parareal_continue(U, 1, 0.0))
-        iters.append({"iteration": st["iterations"], "fine_slices": S, "seconds": ti, "timed": False,
-                      "fine_gmres": st["fine"]["gmres_iters"], "coarse_gmres": st["coarse"]["gmres_iters"]})
-        saved.append(U.clone())
+        one_step(False, False)
+        torch.cuda.synchronize()
     shares = {nm: fsi.profile_read(nm)[0] for nm in names}
     if not any(shares.values()):
         shares["k_bsr_spmv"] = 1.0
@@ -442,9 +485,8 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
                                                    fsi.profile_read(nm)[1]), file=sys.stderr)
     fsi.profile_enable([dominant])
 
-    # timed region: K iterations; every step copies the iterate in from pinned host
-    # memory and back out, so the same loop gives the device and the end-to-end time
-    hU = torch.empty((N + 1, n), dtype=torch.float64).pin_memory()
+    # timed region: K steps; every step copies the iterate in from pinned host memory and
+    # back out, so the same loop gives the device and the end-to-end time
     hU.copy_(U)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -452,65 +494,58 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
         dist.barrier()
     torch.cuda.synchronize()
     l0 = fsi.launch_count()
-    ev = []
-    steps_done = []
     for _ in range(args.steps):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        e[0].record(stream)
-        U.copy_(hU, non_blocking=True)
-        e[1].record(stream)
-        _, st = ctx.parareal_continue(U, 1, 0.0)
-        e[2].record(stream)
-        hU.copy_(U, non_blocking=True)
-        e[3].record(stream)
-        saved.append(U.clone())
-        ev.append(e)
-        steps_done.append(st)
+        one_step(True, True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches = fsi.launch_count() - l0
     clk = clocks.stop()
-    dev_s = [e[1].elapsed_time(e[2]) / 1000.0 for e in ev]
-    e2e_s = [e[0].elapsed_time(e[3]) / 1000.0 for e in ev]
-    fine_units = 0
-    prev = iters[-1]["iteration"] if iters else 0
-    for st, ts in zip(steps_done, dev_s):
-        S = N - (st["iterations"] - 1) if st["iterations"] > prev else 0   # no iteration runs past N
-        prev = st["iterations"]
-        fine_units += S * w.m_fine
-        iters.append({"iteration": st["iterations"], "fine_slices": S, "seconds": ts, "timed": True,
-                      "fine_gmres": st["fine"]["gmres_iters"], "coarse_gmres": st["coarse"]["gmres_iters"]})
+    for rec in steps:
+        e = rec.pop("_ev")
+        rec["seconds"] = e[1].elapsed_time(e[2]) / 1000.0
+        rec["e2e_seconds"] = e[0].elapsed_time(e[3]) / 1000.0
+    timed_steps = [r for r in steps if r["timed"]]
+    fine_units = sum(r["fine_slices"] * w.m_fine for r in timed_steps)
     dom_ms, dom_n, dom_flops = fsi.profile_read(dominant)
     dom_bytes = fsi.profile_read_bytes(dominant)
     fsi.profile_enable([])
     fp64_tflops = fp64_peak(torch, fsi, stream)   # right after the timed region, at its clocks
-    ms = 1000.0 * sum(dev_s)
-    ms, value = aggregate(ms, fine_units, dist, dev)
-    e2e_ms, e2e_value = aggregate(1000.0 * sum(e2e_s), fine_units, dist, dev)
+    ms = 1000.0 * sum(r["seconds"] for r in timed_steps)
+    if fine_units:
+        ms, value = aggregate(ms, fine_units, dist, dev)
+        e2e_ms, e2e_value = aggregate(1000.0 * sum(r["e2e_seconds"] for r in timed_steps), fine_units, dist, dev)
+    else:
+        value = e2e_value = None
 
-    # error of every iterate against the serial fine solution
-    t_cum = t_pred
+    # error of every iterate against the serial fine solution; run time within its run
     reached = None
-    for rec, Ui in zip(iters, saved):
-        rec["max_rel_err_vs_serial"] = rel_errors(Ui, Us, N)
-        t_cum += rec["seconds"]
-        rec["run_seconds"] = t_cum
-        if reached is None and max(rec["max_rel_err_vs_serial"].values()) <= 1e-8:
-            reached = rec
-    best = min(iters, key=lambda r: max(r["max_rel_err_vs_serial"].values())) if iters else None
+    t_run = {1: t_pred}
+    for idx, rec in enumerate(steps):
+        t_run[rec["run"]] = t_run.get(rec["run"], 0.0) + rec["seconds"]
+        rec["run_seconds"] = t_run[rec["run"]]
+        if idx in saved:
+            rec["max_rel_err_vs_serial"] = rel_errors(saved[idx], Us, N)
+            if reached is None and max(rec["max_rel_err_vs_serial"].values()) <= 1e-8:
+                reached = rec
+    ok_steps = [r for r in steps if "max_rel_err_vs_serial" in r]
+    best = min(ok_steps, key=lambda r: max(r["max_rel_err_vs_serial"].values())) if ok_steps else None
     at_tol = {"tolerance": 1e-8, "reached": reached is not None,
-              "iterations_run": len(iters),
+              "iterations_run": len(ok_steps),
               "iteration_reached": reached["iteration"] if reached else None,
               "run_seconds_to_reach": reached["run_seconds"] if reached else None,
               "fine_steps_per_s_at_1e-8": (N * w.m_fine / reached["run_seconds"]) if reached else None,
               "smallest_error": best["max_rel_err_vs_serial"] if best else None,
               "smallest_error_iteration": best["iteration"] if best else None,
               "exact_at_iteration": N,
+              "runs": runs,
               "note": "an iterate is exact (the serial fine solution) at k = N (Sec. 4.1); boundaries "
-                      "1..k are exact after iteration k"}
-    last_saved = saved[-1] if saved else U
-    del saved[1:]
+                      "1..k are exact after iteration k; a run ends when a propagator's solve fails on its "
+                      "iterates (run_seconds include the run's predictor)"}
+    first_ok = saved[min(saved)] if saved and 0 in saved else None
+    last_saved = saved[max(saved)] if saved else U
+    saved = {}
+
 
     # the dominant kernel's roofline over the timed region, and one isolated launch of it
     roof = {"kernel": dominant, "share_of_kernel_time_last_warmup": shares[dominant] / total_ms if total_ms else None}
@@ -560,8 +595,8 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
     # precision variants (config 3): the predictor and one iteration from the same start,
     # against the FP64 iterate after iteration 1 and the exact first boundary
     variants = []
-    if not args.no_precision_variant and args.warmup >= 1:
-        U1_64 = saved[0]
+    if not args.no_precision_variant and first_ok is not None:
+        U1_64 = first_ok
         tip = wl.tip_node(w)
         desc = {1: "FP32 linear solver (FGMRES, multigrid, Vanka, operator) inside the FP64 Newton loop (Newton "
                    "tolerance 1e-11); FP64 residual, J = det F, Parareal correction",
@@ -578,7 +613,7 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
             b1 = rel_errors(Uv[:2].contiguous(), Us[:2].contiguous(), 1)
             variants.append({"precision": prec, "what": desc[prec], "step": "predictor + iteration 1",
                              "seconds": tv, "fine_steps_per_s": N * w.m_fine / tv,
-                             "fp64_seconds_same_work": t_pred + iters[0]["seconds"],
+                             "fp64_seconds_same_work": t_pred + steps[0]["seconds"],
                              "max_rel_err_vs_fp64_iterate": err, "boundary1_rel_err_vs_fp64_serial": b1,
                              "newton_fine": sv["fine"], "newton_coarse": sv["coarse"]})
             ctxv.close()
@@ -599,13 +634,16 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
              "note": "model speed-up with one processor per slice and K iterations"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms / max(len(timed_steps), 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "steps_completed": sum(1 for r in timed_steps if r["failed"] is None),
                 "config": {"workload": w.name, "unit": "parareal", "n_dofs": n, "n_slices": N,
                            "m_fine": w.m_fine, "m_coarse": w.m_coarse, "mg_levels": ctx.n_levels,
-                           "step": "one Parareal iteration of one continuing run (parareal_continue): batched "
-                                   "fine solves of every slice not yet exact, then the corrected coarse sweep; "
-                                   "value = fine time-steps advanced per second over the timed iterations",
+                           "step": "one Parareal iteration of a continuing run (parareal_continue): batched "
+                                   "fine solves of every slice not yet exact, then the corrected coarse sweep. A "
+                                   "step whose solve fails on the run's iterates ends the run and starts a new one "
+                                   "(predictor sweep); it stays in the timed total and advances no fine step. "
+                                   "value = fine time-steps advanced per second over all timed steps",
                            "l2": "inputs larger than L2 (3.4 GB of Jacobian values per batch)",
                            "overrides": overrides(args),
                            "solver": {"newton_tol": w.newton_tol, "newton_eta": w.newton_eta,
@@ -616,7 +654,7 @@ def bench_parareal(args, torch, fsi, wl, dev, dist, rank, world):
                            "serial_gpu_fine_steps_per_s": N * w.m_fine / t_serial,
                            "batched_iterations_vs_serial_steps_per_s": value / (N * w.m_fine / t_serial),
                            "predictor_seconds": t_pred,
-                           "iterations": iters,
+                           "iterations": steps,
                            "paper_speedup_model": model,
                            "converged_small_workload": small},
                 "roofline": roof, "cpu_baseline": cpu,

@@ -686,19 +686,26 @@ int upload_tables_once() {
   CK(cudaMemcpyToSymbol(c_we, gw, sizeof(gw)));
   CK(cudaMemcpyToSymbol(c_lps_ss, kss, sizeof(kss)));
   CK(cudaMemcpyToSymbol(c_lps_tt, ktt, sizeof(ktt)));
-  float phif[9][9], dpsf[9][9], dptf[9][9], wqf[9];
+  TabF tf;
   for (int q = 0; q < 9; ++q) {
-    wqf[q] = (float)wq[q];
+    tf.wq[q] = (float)wq[q];
     for (int l = 0; l < 9; ++l) {
-      phif[q][l] = (float)phi[q][l];
-      dpsf[q][l] = (float)dps[q][l];
-      dptf[q][l] = (float)dpt[q][l];
+      tf.phi[q][l] = (float)phi[q][l];
+      tf.dps[q][l] = (float)dps[q][l];
+      tf.dpt[q][l] = (float)dpt[q][l];
+      tf.lss[q][l] = (float)kss[q][l];
+      tf.ltt[q][l] = (float)ktt[q][l];
     }
   }
-  CK(cudaMemcpyToSymbol(c_phif, phif, sizeof(phif)));
-  CK(cudaMemcpyToSymbol(c_dpsf, dpsf, sizeof(dpsf)));
-  CK(cudaMemcpyToSymbol(c_dptf, dptf, sizeof(dptf)));
-  CK(cudaMemcpyToSymbol(c_wqf, wqf, sizeof(wqf)));
+  for (int q = 0; q < 3; ++q) {
+    tf.we[q] = (float)gw[q];
+    for (int l = 0; l < 9; ++l) {
+      tf.phie[q][l] = (float)phie[q][l];
+      tf.dpse[q][l] = (float)dpse[q][l];
+      tf.dpte[q][l] = (float)dpte[q][l];
+    }
+  }
+  CK(cudaMemcpyToSymbol(g_tabf, &tf, sizeof(tf)));
   return FSI_OK;
 }
 
@@ -1172,16 +1179,23 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
   // gmiss: an FGMRES solve of the slice stopped at its iteration limit. Its correction is
   // still applied (inexact Newton); the slice fails only if Newton then fails (FSI_EGMRES)
   std::vector<uint8_t> gmiss(S, 0);
+  // slices whose last solve stopped at its limit: their multigrid hierarchy is rebuilt at the
+  // current iterate before the next solve (the other slices keep theirs, so the batch stays bitwise solo)
+  std::vector<uint8_t> rebuild(S, 0);
   const bool trace = trace_newton();
   std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
+  bool fresh = false;   // R and nr already hold the residual at Uit of every active slice
   for (int it = 0;; ++it) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
-    TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-    TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
-    CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (!fresh) {
+      TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+      TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
+      CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    fresh = false;
     bool any = false;
     for (int s = 0; s < S; ++s) {
       if (!act[s]) continue;
@@ -1224,6 +1238,16 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
     // FP64 throughout, or the FP32 linear solver inside the FP64 Newton loop
     // (FP32 cannot reach FP64 tolerances: its relative tolerance is >= 1e-6)
     int rc;
+    if (std::any_of(rebuild.begin(), rebuild.end(), [](uint8_t v) { return v != 0; })) {
+      std::vector<uint8_t> mask(S);
+      for (int s = 0; s < S; ++s) mask[s] = act[s] && rebuild[s];
+      CK(cudaMemcpyAsync(c->active2, mask.data(), S, cudaMemcpyHostToDevice, st));
+      c->n_act = g_nact = count_active(mask);
+      if (c->prm.precision == 0) TRY(mg_setup<double>(c, S, c->Uit, c->Uold, k, theta, c->active2, st));
+      else TRY(mg_setup<float>(c, S, c->Uit, c->Uold, k, theta, c->active2, st));
+      c->n_act = g_nact = count_active(act);
+      std::fill(rebuild.begin(), rebuild.end(), 0);
+    }
     if (c->prm.precision == 1)        // all-FP32 linear solver (inner tolerance >= 1e-6)
       rc = newton_correction<float>(c, S, k, theta, it, reuse, hierarchy_valid, std::max(rtol_now, 1e-6),
                                     stats, st, target.data());
@@ -1243,6 +1267,7 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
       const int code = (int)c->slice_code.size() == S ? c->slice_code[s] : 0;
       if (act[s] && code == FSI_EGMRES) {
         gmiss[s] = 1;
+        rebuild[s] = 1;
         if (trace) std::fprintf(stderr, "[fsi trace] 2D slice %d t=%.6g Newton it %d: FGMRES at its limit\n", s,
                                 t_old[s] + k, it);
       } else if (act[s] && !why[s] && code) {
@@ -1250,6 +1275,46 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
       }
     }
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed: " + g_err);
+    // Backtracking: a slice whose full Newton step increased the residual takes half the
+    // step, up to 6 times (the correction is still in the finest level's x). A step that
+    // does not increase the residual is taken as it is, so converging steps are unchanged.
+    // The last residual computed for each slice is the one at its final iterate: the next
+    // Newton iteration starts from it.
+    std::vector<double> lam(S, 1.0), nb(S);
+    std::vector<uint8_t> cand = act;   // the slices whose residual is checked in this round
+    for (int bt = 0;; ++bt) {
+      CK(cudaMemcpyAsync(c->active, cand.data(), S, cudaMemcpyHostToDevice, st));
+      c->n_act = g_nact = count_active(cand);
+      if (!c->n_act) break;
+      TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+      TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
+      CK(cudaMemcpyAsync(nb.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<uint8_t> back(S, 0);
+      bool anyb = false;
+      for (int s = 0; s < S; ++s) {
+        if (!cand[s]) continue;
+        if (bt < 6 && std::isfinite(nr[s]) && !(nb[s] <= nr[s])) back[s] = anyb = true;
+        else nr[s] = nb[s];
+      }
+      if (!anyb) break;
+      double half = 0.0;
+      for (int s = 0; s < S; ++s)
+        if (back[s]) {
+          half = 0.5 * lam[s];   // every backtracking slice is at the same stage
+          lam[s] *= 0.5;
+          if (trace) std::fprintf(stderr, "[fsi trace] 2D slice %d Newton it %d: step scaled to %g\n", s, it, lam[s]);
+        }
+      cand = back;
+      CK(cudaMemcpyAsync(c->active, back.data(), S, cudaMemcpyHostToDevice, st));
+      c->n_act = g_nact = count_active(back);
+      if (c->prm.precision == 1)
+        LAUNCH(KI_AXPBY, (k_axpby<float, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -half, reinterpret_cast<const float*>(L.x), n, 1.0, c->active, c->Uit, n);
+      else
+        LAUNCH(KI_AXPBY, (k_axpby<double, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -half, reinterpret_cast<const double*>(L.x), n, 1.0, c->active, c->Uit, n);
+      TRY(launch_check());
+    }
+    fresh = true;
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (stats) {

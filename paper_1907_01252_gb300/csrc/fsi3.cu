@@ -1124,14 +1124,19 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
   const bool trace = std::getenv("FSI_TRACE_NEWTON") != nullptr;
   std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
+  bool fresh = false;   // R and nr already hold the residual at Uit of every active slice
   for (int it = 0;; ++it) {
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-    TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-    TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hr, st));
+    if (!fresh) {
+      TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+      TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hr, st));
+      for (int s = 0; s < S; ++s)
+        if (act[s]) nr[s] = std::sqrt(hr[(size_t)s * 64]);
+    }
+    fresh = false;
     bool any = false;
     for (int s = 0; s < S; ++s) {
       if (!act[s]) continue;
-      nr[s] = std::sqrt(hr[(size_t)s * 64]);
       if (!std::isfinite(nr[s])) {
         status = why[s] = FSI_ENAN;
         act[s] = 0;
@@ -1204,6 +1209,39 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, 1.0, c->xk, n, 1.0, c->active, c->Uit, n);
     TRY3(launched3());
+    // Backtracking: a slice whose full Newton step increased the residual takes half the
+    // step, up to 6 times (xk still holds the correction). A step that does not increase the
+    // residual is taken as it is, so converging steps are unchanged. The last residual
+    // computed for each slice is the one at its final iterate: the next Newton iteration
+    // starts from it.
+    std::vector<double> lam(S, 1.0), hb;
+    std::vector<uint8_t> cand = act;   // the slices whose residual is checked in this round
+    for (int bt = 0;; ++bt) {
+      if (!std::any_of(cand.begin(), cand.end(), [](uint8_t v) { return v != 0; })) break;
+      CK3(cudaMemcpyAsync(c->active, cand.data(), S, cudaMemcpyHostToDevice, st));
+      TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+      TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hb, st));
+      std::vector<uint8_t> back(S, 0);
+      bool anyb = false;
+      for (int s = 0; s < S; ++s) {
+        if (!cand[s]) continue;
+        const double nb = std::sqrt(hb[(size_t)s * 64]);
+        if (bt < 6 && std::isfinite(nr[s]) && !(nb <= nr[s])) back[s] = anyb = true;
+        else nr[s] = nb;
+      }
+      if (!anyb) break;
+      cand = back;
+      CK3(cudaMemcpyAsync(c->active, back.data(), S, cudaMemcpyHostToDevice, st));
+      double half = 0.0;
+      for (int s = 0; s < S; ++s)
+        if (back[s]) half = 0.5 * lam[s], lam[s] *= 0.5;   // every backtracking slice is at the same stage
+      P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, -half, c->xk, n, 1.0, c->active, c->Uit, n);
+      TRY3(launched3());
+      if (trace)
+        for (int s = 0; s < S; ++s)
+          if (back[s]) std::fprintf(stderr, "[fsi trace] 3D slice %d Newton it %d: step scaled to %g\n", s, it, lam[s]);
+    }
+    fresh = true;
   }
   CK3(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (stats) {

@@ -1393,10 +1393,61 @@ __global__ void __launch_bounds__(FMA_PROBE_THREADS) k_fma_probe(int iters, doub
 // completion is not seen within the poll limit the element matrix is filled
 // with NaN (the solve then stops with FSI_ENAN) and *status is set.
 // --------------------------------------------------------------------------
-__constant__ float c_phif[9][9];
-__constant__ float c_dpsf[9][9];
-__constant__ float c_dptf[9][9];
-__constant__ float c_wqf[9];
+// FP32 copies of the reference-element tables for the FP32 tangent. They sit in global memory and each CTA
+// stages them in shared memory: the contraction reads them with a per-thread basis index, which constant
+// memory would serialise (one constant-cache access per distinct address in a warp).
+struct TabF {
+  float phi[9][9], dps[9][9], dpt[9][9];   // [Gauss point][basis function]
+  float wq[9];
+  float phie[3][9], dpse[3][9], dpte[3][9];
+  float we[3];
+  float lss[9][9], ltt[9][9];               // the stabilisation integrals
+};
+__device__ TabF g_tabf;
+
+// FP32 counterparts of eval_qp and lps_weight for the FP32 tangent.
+__device__ inline void eval_qp_f32(const TabF& T, const float* Ue, const float* Uo, int q, float ihx, float ihy,
+                                   QpInT<float>& s) {
+  float val[5] = {0, 0, 0, 0, 0}, gx[5] = {0, 0, 0, 0, 0}, gy[5] = {0, 0, 0, 0, 0};
+  float valo[4] = {0, 0, 0, 0}, gxo[4] = {0, 0, 0, 0}, gyo[4] = {0, 0, 0, 0};
+  for (int l = 0; l < 9; ++l) {
+    const float ph = T.phi[q][l], ps = T.dps[q][l] * ihx, pt = T.dpt[q][l] * ihy;
+    for (int c = 0; c < 5; ++c) {
+      val[c] += ph * Ue[l * 5 + c];
+      gx[c] += ps * Ue[l * 5 + c];
+      gy[c] += pt * Ue[l * 5 + c];
+    }
+    for (int c = 0; c < 4; ++c) {
+      valo[c] += ph * Uo[l * 5 + c];
+      gxo[c] += ps * Uo[l * 5 + c];
+      gyo[c] += pt * Uo[l * 5 + c];
+    }
+  }
+  s.v[0] = val[0]; s.v[1] = val[1]; s.u[0] = val[2]; s.u[1] = val[3]; s.p = val[4];
+  s.G = M2T<float>{gx[0], gy[0], gx[1], gy[1]};
+  s.Hu = M2T<float>{gx[2], gy[2], gx[3], gy[3]};
+  s.vo[0] = valo[0]; s.vo[1] = valo[1]; s.uo[0] = valo[2]; s.uo[1] = valo[3];
+  s.Go = M2T<float>{gxo[0], gyo[0], gxo[1], gyo[1]};
+  s.Huo = M2T<float>{gxo[2], gyo[2], gxo[3], gyo[3]};
+}
+
+__device__ inline float lps_weight_f32(const TabF& T, const Phys& P, const float* Uo, float hx, float hy) {
+  float mx = 0.f, my = 0.f, ws = 0.f;
+  for (int q = 0; q < 9; ++q) {
+    float vx = 0.f, vy = 0.f;
+    for (int l = 0; l < 9; ++l) {
+      vx += T.phi[q][l] * Uo[l * 5 + 0];
+      vy += T.phi[q][l] * Uo[l * 5 + 1];
+    }
+    mx += T.wq[q] * vx;
+    my += T.wq[q] * vy;
+    ws += T.wq[q];
+  }
+  mx /= ws;
+  my /= ws;
+  const float h = sqrtf(hx * hx + hy * hy), rf = (float)P.rho_f;
+  return (float)P.alpha0 * h * h / (rf * (float)P.nu_f + rf * sqrtf(mx * mx + my * my) * h);
+}
 
 constexpr int JTC_NS = 3;                          // BF16 terms per FP32 operand
 constexpr int JTC_A_TERM = 128 * 32 * 2;           // bytes of one A term of one tile
@@ -1406,29 +1457,13 @@ static_assert(JAC_THREADS >= 128, "the tensor-memory read-back takes four warps"
 
 // Shared state of the FP32 tangent stage.
 struct JacTangentShared32 {
-  double sU[45], sUo[45];
+  float sU[45], sUo[45];
   QpInT<float> sq[9];
   QpDerivedT<float> sd[9];
   float sD[9][15][15];      // [q][test slot][trial direction]
   float sDe[3][2][12];      // outflow edge: [q][momentum comp][trial direction (c<4)]
-  double sAlpha;
+  float sAlpha;
 };
-
-__device__ inline QpInT<float> qp_to_float(const QpIn& a) {
-  QpInT<float> b;
-  for (int i = 0; i < 2; ++i) {
-    b.v[i] = (float)a.v[i];
-    b.u[i] = (float)a.u[i];
-    b.vo[i] = (float)a.vo[i];
-    b.uo[i] = (float)a.uo[i];
-  }
-  b.p = (float)a.p;
-  b.G = M2T<float>{(float)a.G.a, (float)a.G.b, (float)a.G.c, (float)a.G.d};
-  b.Hu = M2T<float>{(float)a.Hu.a, (float)a.Hu.b, (float)a.Hu.c, (float)a.Hu.d};
-  b.Go = M2T<float>{(float)a.Go.a, (float)a.Go.b, (float)a.Go.c, (float)a.Go.d};
-  b.Huo = M2T<float>{(float)a.Huo.a, (float)a.Huo.b, (float)a.Huo.c, (float)a.Huo.d};
-  return b;
-}
 
 __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, Phys P, const double* __restrict__ U,
                                                                     const double* __restrict__ Uold, size_t stride,
@@ -1440,29 +1475,30 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
   if (!active[s]) return;   // uniform over the CTA, before any tensor-memory allocation
   extern __shared__ __align__(1024) unsigned char jtc[];
   __shared__ JacTangentShared32 sh;
+  __shared__ TabF T;
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
   if (tid == 0) tc::mbar_init(&bar, 1);
-  const double hx = m.cell_h[cell * 2], hy = m.cell_h[cell * 2 + 1];
-  const double ihx = 1.0 / hx, ihy = 1.0 / hy, area = hx * hy;
+  const float hx = (float)m.cell_h[cell * 2], hy = (float)m.cell_h[cell * 2 + 1];
+  const float fihx = 1.f / hx, fihy = 1.f / hy, farea = hx * hy;
   const uint8_t cf = m.cell_flags[cell];
   const bool solid = cf & CF_SOLID;
   const bool outflow = !solid && (cf & CF_OUTFLOW);
-  // ---- FP32 tangent: the states at the Gauss points (FP64 interpolation, then FP32) ----
+  // ---- FP32 tangent: the cell's states in FP32, then the Gauss-point quantities ----
   if (tid < 45) {
-    sh.sU[tid] = U[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
-    sh.sUo[tid] = Uold[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+    sh.sU[tid] = (float)U[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
+    sh.sUo[tid] = (float)Uold[s * stride + (size_t)m.cell_nodes[cell * 9 + tid / 5] * 5 + tid % 5];
   }
+  for (int i = tid; i < (int)(sizeof(TabF) / sizeof(float)); i += JAC_THREADS)
+    reinterpret_cast<float*>(&T)[i] = reinterpret_cast<const float*>(&g_tabf)[i];
   __syncthreads();
   if (tid < 9) {
-    QpIn q;
-    eval_qp(sh.sU, sh.sUo, tid, ihx, ihy, q);
-    sh.sq[tid] = qp_to_float(q);
+    eval_qp_f32(T, sh.sU, sh.sUo, tid, fihx, fihy, sh.sq[tid]);
     derive(sh.sq[tid], sh.sd[tid]);
   }
-  if (tid == 32 && !solid) sh.sAlpha = lps_scale * lps_weight(P, sh.sUo, hx, hy);
+  if (tid == 32 && !solid) sh.sAlpha = (float)lps_scale * lps_weight_f32(T, P, sh.sUo, hx, hy);
   __syncthreads();
   const float fk = (float)k, fth = (float)theta;
   for (int t = tid; t < 9 * 15; t += JAC_THREADS) {
@@ -1488,10 +1524,16 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
   if (outflow) {
     for (int t = tid; t < 3 * 12; t += JAC_THREADS) {
       const int q = t / 12, dir = t % 12, cj = dir / 3, b = dir % 3;
-      M2 G, Hu;
-      eval_edge_grad(sh.sU, q, ihx, ihy, G, Hu);
-      const M2T<float> Gf{(float)G.a, (float)G.b, (float)G.c, (float)G.d};
-      const M2T<float> Hf{(float)Hu.a, (float)Hu.b, (float)Hu.c, (float)Hu.d};
+      float gx[4] = {0.f, 0.f, 0.f, 0.f}, gy[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int l = 0; l < 9; ++l) {
+        const float ps = T.dpse[q][l] * fihx, pt = T.dpte[q][l] * fihy;
+        for (int cc = 0; cc < 4; ++cc) {
+          gx[cc] += ps * sh.sU[l * 5 + cc];
+          gy[cc] += pt * sh.sU[l * 5 + cc];
+        }
+      }
+      const M2T<float> Gf{gx[0], gy[0], gx[1], gy[1]};
+      const M2T<float> Hf{gx[2], gy[2], gx[3], gy[3]};
       M2T<float> dG{0.f, 0.f, 0.f, 0.f}, dH{0.f, 0.f, 0.f, 0.f};
       float out[2] = {0.f, 0.f};
       if (b > 0) {
@@ -1509,7 +1551,6 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
   // ---- the contraction on the tensor cores ----
   unsigned char* sA = jtc;                          // one tile: JTC_NS terms of 128 x 32
   unsigned char* sB = jtc + JTC_NS * JTC_A_TERM;
-  const float fihx = (float)ihx, fihy = (float)ihy, farea = (float)area;
   const uint32_t tmem = tmem_base;
   bool ok = true;
   for (int tile = 0; tile < 2; ++tile) {
@@ -1523,7 +1564,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
           const int kk = c * 8 + x, q = kk / 3, a = kk % 3;
-          v[x] = (local < 9 && kk < 27) ? (a == 0 ? c_phif[q][local] : (a == 1 ? c_dpsf[q][local] : c_dptf[q][local]))
+          v[x] = (local < 9 && kk < 27) ? (a == 0 ? T.phi[q][local] : (a == 1 ? T.dps[q][local] : T.dpt[q][local]))
                                         : 0.f;
         }
       } else {
@@ -1537,8 +1578,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
           if (live && kk < 27) {
             const float* Dr = &sh.sD[q][ci * 3 + a][cj * 3];
             const float sa = a == 0 ? 1.f : (a == 1 ? fihx : fihy);
-            e = sa * c_wqf[q] * farea *
-                (Dr[0] * c_phif[q][j] + Dr[1] * (c_dpsf[q][j] * fihx) + Dr[2] * (c_dptf[q][j] * fihy));
+            e = sa * T.wq[q] * farea *
+                (Dr[0] * T.phi[q][j] + Dr[1] * (T.dps[q][j] * fihx) + Dr[2] * (T.dpt[q][j] * fihy));
           }
           v[x] = e;
         }
@@ -1598,9 +1639,9 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
         float v = ok ? d[i] : __int_as_float(0x7fc00000);
         if (outflow && ci < 2 && cj < 4) {
           for (int q = 0; q < 3; ++q) {
-            const float Bj[3] = {(float)c_phie[q][j], (float)(c_dpse[q][j] * ihx), (float)(c_dpte[q][j] * ihy)};
+            const float Bj[3] = {T.phie[q][j], T.dpse[q][j] * fihx, T.dpte[q][j] * fihy};
             const float* Drow = sh.sDe[q][ci] + cj * 3;
-            v += (float)(c_we[q] * hy * c_phie[q][i]) * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
+            v += T.we[q] * hy * T.phie[q][i] * (Drow[0] * Bj[0] + Drow[1] * Bj[1] + Drow[2] * Bj[2]);
           }
         }
         out[(i * 5 + ci) * 45 + j * 5 + cj] = v;
@@ -1612,9 +1653,10 @@ __global__ void __launch_bounds__(JAC_THREADS, 4) k_cell_jacobian_tc(DevMesh m, 
     const int row = e / 45, col = e % 45;
     const int i = row / 5, ci = row % 5, j = col / 5, cj = col % 5;
     if (jac_block_nonzero(solid, ci, cj)) continue;
-    double v = 0.0;
-    if (!solid && ci == 4 && cj == 4) v = k * sh.sAlpha * (hy * ihx * c_lps_ss[i][j] + hx * ihy * c_lps_tt[i][j]);
-    out[e] = (float)v;
+    float v = 0.f;
+    if (!solid && ci == 4 && cj == 4)
+      v = fk * sh.sAlpha * (hy * fihx * T.lss[i][j] + hx * fihy * T.ltt[i][j]);
+    out[e] = v;
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -79,3 +79,36 @@ def test_adjoint_gradient_matches_oracle_and_finite_differences():
     Jt.backward()
     assert Jt.item() == pytest.approx(J, rel=1e-14)
     assert np.allclose(params.grad.numpy(), g, rtol=1e-14, atol=0)
+
+
+def test_adjoint_gradient_on_the_16x4_workload_matches_finite_differences():
+    """Beyond the toy mesh: the 16 x 4 workload's mesh and fine step (k = 1/128),
+    from a developed state (an oracle implicit-Euler step from rest to t = 0.25,
+    the inflow at full strength), 32 fine steps in two checkpointed slices; the
+    gradient against central differences of the GPU functional at h = 1e-4
+    relative, with every Newton system solved to 1e-12 and exact linear solves
+    (a difference quotient needs forward solves converged to round-off)."""
+    from paper_1907_01252_gb300 import fsi
+    import dataclasses
+    w = dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-12)
+    mesh = of.mesh_for(w, wl.X_BREAKS, wl.Y_BREAKS, wl.SOLID_BOX)
+    model = of.FSIModel(mesh, w.material, newton_tol=1e-12)
+    U_dev = model.step(np.zeros((mesh.n_nodes, 5)), 0.15, 0.1, 1.0)
+    k = w.k_fine
+    M = 2 * w.m_fine
+    ctx = fsi.Context(w, max_batch=1, newton_eta=0.0)
+    U0 = torch.tensor(U_dev.ravel(), device=DEV)
+    J, g, _ = ctx.fsi_adjoint(U0, 0.25, M)
+    assert J > 0.0
+    m = w.material
+    base = [m.mu_s, m.lambda_s, m.vbar]
+    for i in range(3):
+        vals = []
+        for sgn in (1, -1):
+            p = list(base)
+            p[i] += sgn * 1e-4 * base[i]
+            ctx.fsi_set_material(*p)
+            vals.append(ctx.fsi_adjoint(U0, 0.25, M)[0])
+        ctx.fsi_set_material(*base)
+        fd = (vals[0] - vals[1]) / (2e-4 * base[i])
+        assert abs(g[i] - fd) <= 1e-6 * abs(fd), (i, g[i], fd)
