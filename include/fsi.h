@@ -235,6 +235,18 @@ int fsi_bsr_pattern(const fsi_ctx* ctx, int* rowptr, int* colidx);
  * x, y device [S][n_dofs]. Errors: FSI_EINVAL. */
 int fsi_bsr_spmv(fsi_ctx* ctx, int S, const double* vals, const double* x,
                  double* y, void* stream);
+/* The same product with FP32 values and vectors (the FP32 linear solver's
+ * operator), one warp per node row: vals device [S][nnzb][25], x, y device
+ * [S][n_dofs], all float. Errors: FSI_EINVAL. */
+int fsi_bsr_spmv_f32(fsi_ctx* ctx, int S, const float* vals, const float* x,
+                     float* y, void* stream);
+/* The FP64 product as the float-float option computes it: vals and x split
+ * into float pairs hi + lo (a context scratch buffer), every row summed with
+ * compensated FP32 arithmetic, y in FP64 (about 2^-48 of sum |a x| per row).
+ * Shapes as fsi_bsr_spmv. Errors: FSI_EINVAL, also when the context was set
+ * up without ff_operator. */
+int fsi_bsr_spmv_ff(fsi_ctx* ctx, int S, const double* vals, const double* x,
+                    double* y, void* stream);
 
 /* One theta step for S slices: Newton's method (exact Jacobian, no damping;
  * Sec. 1 and 4 solve each step's nonlinear system by Newton) with FGMRES

@@ -775,7 +775,11 @@ int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act
   if (sizeof(T) == sizeof(double) && L.Aff && L.aff_of == (const void*)A) {
     // the FP64 operator as float pairs: x to float pairs, then the compensated FP32 product
     LAUNCH_WB(3.0 * (double)L.n * g_nact, 16.0 * (double)L.n * g_nact, KI_TO_FF, k_to_ff, (dim3(nblk(L.n, 256), S)), 256, 0, st, L.n, reinterpret_cast<const double*>(x), L.n, act, L.xff, L.n);
-    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV_FF, (k_bsr_spmv_ff<RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, L.Aff, L.xff, reinterpret_cast<const double*>(b), L.n, act, reinterpret_cast<double*>(y), rows, nrows);
+    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV_FF, (k_bsr_spmv_w<float2, double, RES>), (dim3(nblk(nrows, SPW_THREADS / 32), S)), SPW_THREADS, 0, st, L.dm, L.Aff, L.xff, reinterpret_cast<const double*>(b), L.n, act, reinterpret_cast<double*>(y), rows, nrows);
+    return launch_check();
+  }
+  if (sizeof(T) == sizeof(float)) {   // FP32: one warp per row, the blocks read in order
+    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv_w<float, float, RES>), (dim3(nblk(nrows, SPW_THREADS / 32), S)), SPW_THREADS, 0, st, L.dm, reinterpret_cast<const float*>(A), reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(b), L.n, act, reinterpret_cast<float*>(y), rows, nrows);
     return launch_check();
   }
   LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
@@ -1185,17 +1189,13 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
   const bool trace = trace_newton();
   std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
-  bool fresh = false;   // R and nr already hold the residual at Uit of every active slice
   for (int it = 0;; ++it) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
-    if (!fresh) {
-      TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-      TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
-      CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-    }
-    fresh = false;
+    TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+    TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
+    CK(cudaMemcpyAsync(nr.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     bool any = false;
     for (int s = 0; s < S; ++s) {
       if (!act[s]) continue;
@@ -1275,46 +1275,6 @@ int theta_step(fsi_ctx* c, int S, const double* U_old, const double* t_old, doub
       }
     }
     if (rc != FSI_OK && rc != FSI_EGMRES) return fail(rc, "linear solve failed: " + g_err);
-    // Backtracking: a slice whose full Newton step increased the residual takes half the
-    // step, up to 6 times (the correction is still in the finest level's x). A step that
-    // does not increase the residual is taken as it is, so converging steps are unchanged.
-    // The last residual computed for each slice is the one at its final iterate: the next
-    // Newton iteration starts from it.
-    std::vector<double> lam(S, 1.0), nb(S);
-    std::vector<uint8_t> cand = act;   // the slices whose residual is checked in this round
-    for (int bt = 0;; ++bt) {
-      CK(cudaMemcpyAsync(c->active, cand.data(), S, cudaMemcpyHostToDevice, st));
-      c->n_act = g_nact = count_active(cand);
-      if (!c->n_act) break;
-      TRY(residual(c, L, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-      TRY(dots<double>(c, S, n, 1, c->R, 0, n, c->R, n, c->active, c->scal, 1, true, st));
-      CK(cudaMemcpyAsync(nb.data(), c->scal, S * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      std::vector<uint8_t> back(S, 0);
-      bool anyb = false;
-      for (int s = 0; s < S; ++s) {
-        if (!cand[s]) continue;
-        if (bt < 6 && std::isfinite(nr[s]) && !(nb[s] <= nr[s])) back[s] = anyb = true;
-        else nr[s] = nb[s];
-      }
-      if (!anyb) break;
-      double half = 0.0;
-      for (int s = 0; s < S; ++s)
-        if (back[s]) {
-          half = 0.5 * lam[s];   // every backtracking slice is at the same stage
-          lam[s] *= 0.5;
-          if (trace) std::fprintf(stderr, "[fsi trace] 2D slice %d Newton it %d: step scaled to %g\n", s, it, lam[s]);
-        }
-      cand = back;
-      CK(cudaMemcpyAsync(c->active, back.data(), S, cudaMemcpyHostToDevice, st));
-      c->n_act = g_nact = count_active(back);
-      if (c->prm.precision == 1)
-        LAUNCH(KI_AXPBY, (k_axpby<float, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -half, reinterpret_cast<const float*>(L.x), n, 1.0, c->active, c->Uit, n);
-      else
-        LAUNCH(KI_AXPBY, (k_axpby<double, double>), (dim3(nblk(n, 256), S)), 256, 0, st, (int)n, -half, reinterpret_cast<const double*>(L.x), n, 1.0, c->active, c->Uit, n);
-      TRY(launch_check());
-    }
-    fresh = true;
   }
   CK(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (stats) {
@@ -2090,6 +2050,36 @@ int fsi_bsr_spmv(fsi_ctx* c, int S, const double* vals, const double* x, double*
   c->n_act = g_nact = count_active(act);
   TRY((spmv<double, false>(c->lev[0], S, vals, x, nullptr, c->active, y, st)));
   return FSI_OK;
+}
+
+int fsi_bsr_spmv_f32(fsi_ctx* c, int S, const float* vals, const float* x, float* y, void* stream) {
+  if (!c || !vals || !x || !y) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
+  TRY((spmv<float, false>(c->lev[0], S, vals, x, nullptr, c->active, y, st)));
+  return FSI_OK;
+}
+
+int fsi_bsr_spmv_ff(fsi_ctx* c, int S, const double* vals, const double* x, double* y, void* stream) {
+  if (!c || !vals || !x || !y) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  Level& L = c->lev[0];
+  if (!L.Aff) return fail(FSI_EINVAL, "the context was set up without ff_operator");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
+  // the operator's float pairs, as a Jacobian assembly leaves them (they then belong to vals)
+  const size_t cnt = (size_t)L.h.nnzb * 25;
+  LAUNCH_WB(3.0 * cnt * c->n_act, 16.0 * cnt * c->n_act, KI_TO_FF, k_to_ff, (dim3(nblk(cnt, 256), S)), 256, 0, st, cnt, vals, cnt, c->active, L.Aff, cnt);
+  TRY(launch_check());
+  L.aff_of = vals;
+  const int rc = spmv<double, false>(L, S, vals, x, nullptr, c->active, y, st);
+  L.aff_of = nullptr;   // the pairs are not the context's operator
+  return rc;
 }
 
 // Resets the statistics of a call, keeping the caller's per-slice array

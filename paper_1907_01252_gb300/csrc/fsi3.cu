@@ -614,6 +614,7 @@ struct fsi3_ctx {
   int red_blocks = 0;
   bool mg32 = false;                 // multigrid in FP32 (precision 2)
   bool hierarchy_built = false;
+  double* sub[2] = {nullptr, nullptr};   // states of the half-step fallback, one buffer per depth
 };
 
 namespace {
@@ -1101,7 +1102,8 @@ int fgmres3(fsi3_ctx* c, int S, const double* b, double* x, std::vector<uint8_t>
 // Theta step, propagators, Parareal
 // ---------------------------------------------------------------------------
 int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, double k, double theta, double* U_new,
-                fsi_stats* stats, cudaStream_t st, int reuse, bool hierarchy_valid) {
+                fsi_stats* stats, cudaStream_t st, int reuse, bool hierarchy_valid,
+                std::vector<int>* why_out = nullptr) {
   if (S < 1 || S > c->S) return fail3(FSI_EINVAL, "batch size outside 1..max_batch");
   const size_t n = c->n;
   std::vector<double> tn(S);
@@ -1124,19 +1126,14 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
   const bool trace = std::getenv("FSI_TRACE_NEWTON") != nullptr;
   std::vector<std::vector<double>> hist(trace ? S : 0);
   int status = FSI_OK;
-  bool fresh = false;   // R and nr already hold the residual at Uit of every active slice
   for (int it = 0;; ++it) {
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
-    if (!fresh) {
-      TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-      TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hr, st));
-      for (int s = 0; s < S; ++s)
-        if (act[s]) nr[s] = std::sqrt(hr[(size_t)s * 64]);
-    }
-    fresh = false;
+    TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
+    TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hr, st));
     bool any = false;
     for (int s = 0; s < S; ++s) {
       if (!act[s]) continue;
+      nr[s] = std::sqrt(hr[(size_t)s * 64]);
       if (!std::isfinite(nr[s])) {
         status = why[s] = FSI_ENAN;
         act[s] = 0;
@@ -1209,41 +1206,9 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
     CK3(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, 1.0, c->xk, n, 1.0, c->active, c->Uit, n);
     TRY3(launched3());
-    // Backtracking: a slice whose full Newton step increased the residual takes half the
-    // step, up to 6 times (xk still holds the correction). A step that does not increase the
-    // residual is taken as it is, so converging steps are unchanged. The last residual
-    // computed for each slice is the one at its final iterate: the next Newton iteration
-    // starts from it.
-    std::vector<double> lam(S, 1.0), hb;
-    std::vector<uint8_t> cand = act;   // the slices whose residual is checked in this round
-    for (int bt = 0;; ++bt) {
-      if (!std::any_of(cand.begin(), cand.end(), [](uint8_t v) { return v != 0; })) break;
-      CK3(cudaMemcpyAsync(c->active, cand.data(), S, cudaMemcpyHostToDevice, st));
-      TRY3(residual3(c, S, c->Uit, c->Uold, k, theta, c->active, c->R, st));
-      TRY3(dots3(c, S, 1, c->R, 0, n, c->R, c->active, hb, st));
-      std::vector<uint8_t> back(S, 0);
-      bool anyb = false;
-      for (int s = 0; s < S; ++s) {
-        if (!cand[s]) continue;
-        const double nb = std::sqrt(hb[(size_t)s * 64]);
-        if (bt < 6 && std::isfinite(nr[s]) && !(nb <= nr[s])) back[s] = anyb = true;
-        else nr[s] = nb;
-      }
-      if (!anyb) break;
-      cand = back;
-      CK3(cudaMemcpyAsync(c->active, back.data(), S, cudaMemcpyHostToDevice, st));
-      double half = 0.0;
-      for (int s = 0; s < S; ++s)
-        if (back[s]) half = 0.5 * lam[s], lam[s] *= 0.5;   // every backtracking slice is at the same stage
-      P3(KI3_AXPBY, (k3_axpby<double, double>), (dim3(nb3(n, 256), S)), 256, 0, st, (int)n, -half, c->xk, n, 1.0, c->active, c->Uit, n);
-      TRY3(launched3());
-      if (trace)
-        for (int s = 0; s < S; ++s)
-          if (back[s]) std::fprintf(stderr, "[fsi trace] 3D slice %d Newton it %d: step scaled to %g\n", s, it, lam[s]);
-    }
-    fresh = true;
   }
   CK3(cudaMemcpyAsync(U_new, c->Uit, S * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (why_out) *why_out = why;
   if (stats) {
     for (int s = 0; s < S; ++s) {
       stats->newton_iters += nit[s];
@@ -1260,11 +1225,75 @@ int theta_step3(fsi3_ctx* c, int S, const double* U_old, const double* t_old, do
   return FSI_OK;
 }
 
+// Fallback of the propagators. The slices of a batch whose step failed in Newton's method
+// or in FGMRES (not by a NaN or a singular element) take it again from the same state as
+// two steps of half the length (fine: shifted Crank-Nicolson with theta = 1/2 + theta0 k/2;
+// coarse: implicit Euler), each with the same fallback, halving at most kSubstepDepth times.
+// Steps that converge are unchanged; a slice's fallback depends on its own state only. The
+// step after a fallback rebuilds the multigrid hierarchy of the whole batch.
+constexpr int kSubstepDepth = 2;
+
+int step3_with_fallback(fsi3_ctx* c, int S, const double* src, const double* t, double k, bool fine, double* dst,
+                        fsi_stats* stats, cudaStream_t st, int reuse, bool hierarchy_valid, int depth = 0) {
+  const size_t n = c->n;
+  const double theta = fine ? 0.5 + c->prm.theta0 * k : 1.0;
+  std::vector<int> saved;   // the caller's per-slice statuses before the step
+  if (stats && stats->slice_status)
+    saved.assign(stats->slice_status, stats->slice_status + std::min(S, stats->slice_status_len));
+  std::vector<int> why;
+  const int rc = theta_step3(c, S, src, t, k, theta, dst, stats, st, reuse, hierarchy_valid, &why);
+  if (rc == FSI_OK || depth >= kSubstepDepth || (int)why.size() != S) return rc;
+  std::vector<int> redo;
+  for (int s = 0; s < S; ++s) {
+    if (why[s] == FSI_ENEWTON || why[s] == FSI_EGMRES) redo.push_back(s);
+    else if (why[s] != FSI_OK) return rc;   // a NaN or a singular element stands
+  }
+  if (redo.empty()) return rc;
+  if (!c->sub[depth]) TRY3(dal3(c->owned, &c->sub[depth], (size_t)c->S * n));
+  double* buf = c->sub[depth];
+  const int R = (int)redo.size();
+  std::vector<double> tr(R);
+  for (int i = 0; i < R; ++i) {   // the step's input is still in Uold (src may alias dst)
+    CK3(cudaMemcpyAsync(buf + (size_t)i * n, c->Uold + (size_t)redo[i] * n, n * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st));
+    tr[i] = t[redo[i]];
+  }
+  if (std::getenv("FSI_TRACE_NEWTON"))
+    std::fprintf(stderr, "[fsi trace] 3D: %d slice(s) of the batch retry t=%.6g as two steps of k=%.6g\n", R,
+                 t[redo[0]] + k, 0.5 * k);
+  fsi_stats sub{};
+  if (stats) {
+    sub = *stats;
+    sub.slice_status = nullptr;
+    sub.slice_status_len = 0;
+  }
+  for (int h = 0; h < 2; ++h) {
+    const int rc2 = step3_with_fallback(c, R, buf, tr.data(), 0.5 * k, fine, buf, stats ? &sub : nullptr, st, reuse,
+                                        false, depth + 1);
+    if (stats) {
+      stats->newton_iters = sub.newton_iters;
+      stats->gmres_iters = sub.gmres_iters;
+      stats->max_newton = std::max(stats->max_newton, sub.max_newton);
+      stats->max_gmres = std::max(stats->max_gmres, sub.max_gmres);
+    }
+    c->hierarchy_built = false;   // the hierarchy now belongs to the sub-batch
+    if (rc2 != FSI_OK) return rc;  // the first failure stands
+    for (double& x : tr) x += 0.5 * k;
+  }
+  for (int i = 0; i < R; ++i)
+    CK3(cudaMemcpyAsync(dst + (size_t)redo[i] * n, buf + (size_t)i * n, n * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    stats->status = FSI_OK;
+    for (size_t s = 0; s < saved.size(); ++s) stats->slice_status[s] = saved[s];
+  }
+  return FSI_OK;
+}
+
 int propagate3(fsi3_ctx* c, int S, const double* U0, const double* t0, double* U1, bool fine, fsi_stats* stats,
                cudaStream_t st) {
   const int m = fine ? c->prm.m_fine : c->prm.m_coarse;
   const double k = c->prm.T / c->prm.n_slices / m;
-  const double theta = fine ? 0.5 + c->prm.theta0 * k : 1.0;
   const int every = std::max(1, c->prm.mg_rebuild_every);
   for (int s0 = 0; s0 < S; s0 += c->S) {
     const int b = std::min(c->S, S - s0);
@@ -1273,7 +1302,7 @@ int propagate3(fsi3_ctx* c, int S, const double* U0, const double* t0, double* U
     double* dst = U1 + (size_t)s0 * c->n;
     for (int j = 0; j < m; ++j) {
       const int reuse = fine ? c->prm.mg_reuse : std::min(c->prm.mg_reuse, 1);
-      TRY3(theta_step3(c, b, src, t.data(), k, theta, dst, stats, st, reuse, fine && j % every != 0));
+      TRY3(step3_with_fallback(c, b, src, t.data(), k, fine, dst, stats, st, reuse, fine && j % every != 0));
       for (double& x : t) x += k;
       src = dst;
     }

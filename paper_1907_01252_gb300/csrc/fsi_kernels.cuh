@@ -1711,3 +1711,69 @@ __global__ void k_bsr_spmv_ff(DevMesh m, const float2* __restrict__ A, const flo
   const double r = fsiff::result(acc);
   y[o] = RESIDUAL ? bvec[o] - r : r;
 }
+
+// --------------------------------------------------------------------------
+// Warp-per-row block product for 4- and 8-byte values (the FP32 operator, and the
+// FP64 operator as float pairs). A warp takes one node row; lane 5c + e (25 of the
+// 32 lanes) multiplies entry (c, e) of every 5 x 5 block of the row with x_j[e].
+// Consecutive lanes so read each block as 25 consecutive values, the whole row
+// streams through in order, and the five partial sums of a row component are
+// combined by warp shuffles (e0 += e2, e1 += e3, e0 += e1, e0 += e4).
+// --------------------------------------------------------------------------
+constexpr int SPW_THREADS = 256;   // 8 rows per CTA
+
+template <typename V> struct SpwAcc;
+template <> struct SpwAcc<float> {
+  float a = 0.f;
+  __device__ void add(float v, float x) { a = fmaf(v, x, a); }
+  __device__ void take(int delta, bool use) {
+    const float o = __shfl_down_sync(0xffffffffu, a, delta);
+    if (use) a += o;
+  }
+  __device__ float value() const { return a; }
+};
+template <> struct SpwAcc<float2> {
+  fsiff::ffacc a;
+  __device__ void add(float2 v, float2 x) { fsiff::fma_ff(a, fsiff::ff{v.x, v.y}, fsiff::ff{x.x, x.y}); }
+  __device__ void take(int delta, bool use) {
+    fsiff::ffacc o;
+    o.s = __shfl_down_sync(0xffffffffu, a.s, delta);
+    o.c = __shfl_down_sync(0xffffffffu, a.c, delta);
+    o.cc = __shfl_down_sync(0xffffffffu, a.cc, delta);
+    if (use) fsiff::merge(a, o);
+  }
+  __device__ double value() const { return fsiff::result(a); }
+};
+
+// y = A x (or b - A x) for the rows listed; V the stored value type, Y the vector type of b and y.
+template <typename V, typename Y, bool RESIDUAL>
+__global__ void __launch_bounds__(SPW_THREADS) k_bsr_spmv_w(DevMesh m, const V* __restrict__ A,
+                                                            const V* __restrict__ x, const Y* __restrict__ bvec,
+                                                            size_t stride, const uint8_t* __restrict__ active,
+                                                            Y* __restrict__ y, const int* __restrict__ rows,
+                                                            int nrows) {
+  const int s = blockIdx.y;
+  const int w = blockIdx.x * (SPW_THREADS / 32) + (threadIdx.x >> 5);
+  if (!active[s] || w >= nrows) return;   // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < 25;
+  const int c = lane / 5, e = lane % 5;
+  const int i = rows[w];
+  const V* As = A + (size_t)s * m.nnzb * 25 + (on ? lane : 0);
+  const V* xs = x + s * stride + e;
+  SpwAcc<V> acc;
+  const int b0 = m.rowptr[i], b1 = m.rowptr[i + 1];
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b) {
+    const int col = m.colidx[b];
+    if (on) acc.add(As[(size_t)b * 25], xs[(size_t)col * 5]);
+  }
+  acc.take(2, e < 2);
+  acc.take(1, e == 0);
+  acc.take(4, e == 0);
+  if (on && e == 0) {
+    const size_t o = s * stride + (size_t)i * 5 + c;
+    const Y r = (Y)acc.value();
+    y[o] = RESIDUAL ? bvec[o] - r : r;
+  }
+}

@@ -96,6 +96,8 @@ SIGNATURES = {
     "fsi_set_material": (_I, [_VP, _D, _D, _D]),
     "fsi_adjoint": (_I, [_VP, _VP, _D, _I, C.POINTER(_D), C.POINTER(_D), C.POINTER(fsi_stats), _VP]),
     "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "fsi_bsr_spmv_f32": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "fsi_bsr_spmv_ff": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "fsi_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
@@ -384,6 +386,20 @@ class Context:
         import torch
         y = torch.empty_like(x) if y is None else y
         _check(self.lib.fsi_bsr_spmv(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def fsi_bsr_spmv_f32(self, vals, x, y=None):
+        """y = A x with FP32 values and vectors (the FP32 operator's product)."""
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(self.lib.fsi_bsr_spmv_f32(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def fsi_bsr_spmv_ff(self, vals, x, y=None):
+        """y = A x for FP64 vals and x through the float-pair product (ff_operator contexts)."""
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(self.lib.fsi_bsr_spmv_ff(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
         return y
 
     def _propagator_call(self, fn, S, *args):

@@ -106,6 +106,40 @@ def test_spmv_matches_oracle_matrix():
         assert np.abs(y[s] - ref).max() <= 1e-12 * (abs(A) @ abs(x[s].ravel())).max()
 
 
+def test_spmv_f32_and_float_pair_products():
+    """The warp-per-row products against the FP64 product of the same values: FP32 values
+    and vectors within the FP32 summation bound (28 terms deep per row component: 25 blocks
+    at most per lane, then three merges), float pairs within 2^-44 of sum |a x| per row.
+    36 x 10 cells: 1,533 rows (a ragged last CTA of 5 rows), 3 slices; one slice alone
+    gives the same bits."""
+    import scipy.sparse as sp
+    w = wl.Workload("spmv_w", nx=36, ny=10, T=1.0, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    S = 3
+    U = np.stack([wl.random_state(mesh.n_nodes, 700 + s) for s in range(S)])
+    x = np.stack([wl.random_state(mesh.n_nodes, 800 + s) for s in range(S)])
+    ctx = ctx_for(w, S, ff_operator=1)
+    vals = ctx.fsi_jacobian(to_dev(U), to_dev(U), 1e-2, 0.6)
+    rowptr, colidx = ctx.fsi_bsr_pattern()
+    xd = to_dev(x)
+    y_ff = ctx.fsi_bsr_spmv_ff(vals, xd).cpu().numpy()
+    v32, x32 = vals.float(), xd.float()
+    y_32 = ctx.fsi_bsr_spmv_f32(v32, x32).cpu().numpy()
+    v32h, x32h = v32.double().cpu().numpy(), x32.double().cpu().numpy()
+    vh = vals.cpu().numpy()
+    n = mesh.n_dofs
+    for s in range(S):
+        A = sp.bsr_matrix((vh[s], colidx, rowptr), shape=(n, n))
+        ref, mag = A @ x[s].ravel(), abs(A) @ abs(x[s].ravel())
+        assert np.all(np.abs(y_ff[s] - ref) <= 2.0 ** -44 * mag)
+        A32 = sp.bsr_matrix((v32h[s], colidx, rowptr), shape=(n, n))
+        ref32, mag32 = A32 @ x32h[s], abs(A32) @ abs(x32h[s])
+        assert np.all(np.abs(y_32[s].astype(np.float64) - ref32) <= 28 * 2.0 ** -24 * mag32 + 1e-38)
+    one_ff = ctx.fsi_bsr_spmv_ff(vals[1:2].contiguous(), xd[1:2].contiguous()).cpu().numpy()
+    one_32 = ctx.fsi_bsr_spmv_f32(v32[1:2].contiguous(), x32[1:2].contiguous()).cpu().numpy()
+    assert np.array_equal(one_ff[0], y_ff[1]) and np.array_equal(one_32[0], y_32[1])
+
+
 def developed_states(w, mesh, steps, k):
     model = of.FSIModel(mesh, w.material)
     U = np.zeros((mesh.n_nodes, 5))
@@ -205,10 +239,13 @@ def test_fine_and_coarse_propagators_match_oracle():
 # its 128 fine steps per iteration two solutions that each meet the Newton
 # stopping test at 1e-10 drift apart by about that much in the pressure, so
 # both sides solve that workload's Newton systems to 1e-11 (just above the
-# residual's round-off floor of about 1.5e-12 relative): the comparison then
-# sees the arithmetic, not where two stopping tests fall.
+# residual's round-off floor of about 1.5e-12 relative), and the GPU solves
+# every Newton correction to the FGMRES tolerance (no inexact forcing), as the
+# oracle's direct solver does: both then take the same Newton iterates, and the
+# comparison sees the arithmetic, not where two stopping tests fall.
 @pytest.mark.parametrize("w", [wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4),
-                               dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-11)],
+                               dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-11, gmres_rtol_first=0.0,
+                                                   newton_eta=0.0)],
                          ids=["short", "fsi2d_q2_16x4_T1_8x16"])
 def test_parareal_matches_oracle_iterates_and_reaches_serial(w):
     mesh = oracle_mesh(w)
