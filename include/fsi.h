@@ -248,6 +248,21 @@ int fsi_bsr_spmv_f32(fsi_ctx* ctx, int S, const float* vals, const float* x,
 int fsi_bsr_spmv_ff(fsi_ctx* ctx, int S, const double* vals, const double* x,
                     double* y, void* stream);
 
+/* The product y = A x over all node rows in one chosen kernel variant, for
+ * tests and tuning: value_type 0 FP64 (vals, x, y double), 1 FP32 (all float),
+ * 2 FP64 values and vector carried as float pairs (vals, x, y double; needs
+ * ff_operator); tile_rows 0 the row-list kernel (one thread per row component),
+ * or 8, 16, 32, 64: the row-tile kernel, whose CTA stages the contiguous blocks
+ * of that many consecutive rows in shared memory by a bulk asynchronous copy.
+ * Every variant sums each row component over its blocks in the same order, so
+ * all give the same bits (the library's own products pick the fastest per
+ * level, value type and batch size on first use). Shapes as fsi_bsr_spmv;
+ * synchronises the stream. Errors: FSI_EINVAL (also a tile whose blocks exceed
+ * 200 KiB of shared memory), FSI_ECUDA when a bulk copy did not complete within
+ * its poll limit (the outputs of its tile are NaN). */
+int fsi_bsr_spmv_variant(fsi_ctx* ctx, int S, int value_type, int tile_rows,
+                         const void* vals, const void* x, void* y, void* stream);
+
 /* One theta step for S slices: Newton's method (exact Jacobian, no damping;
  * Sec. 1 and 4 solve each step's nonlinear system by Newton) with FGMRES
  * preconditioned by a geometric multigrid V-cycle with Vanka smoothing.

@@ -24,6 +24,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -264,6 +265,9 @@ void prolong_1d(const std::vector<double>& vc, const std::vector<double>& xf, st
 // ---------------------------------------------------------------------------
 // Device level: tables, transfer from the next finer level, workspace.
 // ---------------------------------------------------------------------------
+constexpr int kSptRows[4] = {8, 16, 32, 64};   // tile heights of the row-tile block product
+constexpr size_t kSptMaxSmem = 200 * 1024;     // largest staged tile (bytes)
+
 struct Level {
   HostMesh h;
   DevMesh dm{};
@@ -284,6 +288,12 @@ struct Level {
   const void* aff_of = nullptr;               // the FP64 values Aff currently holds (nullptr: none)
   int* perm = nullptr;
   bool coarsest = false;
+  // row-tile block product: blocks of the largest tile for each tile height of
+  // kSptRows, and the tuned variant per value type (FP64, FP32, float pair) and
+  // batch-size class (-1 not tuned yet, 0 the row-list kernel, t > 0 tile kSptRows[t - 1])
+  int spt_blocks[4] = {};
+  signed char spt_choice[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};
+  int* async_status = nullptr;   // set when a bulk copy into shared memory did not complete
 };
 
 }  // namespace
@@ -549,6 +559,7 @@ int setup_level(Level& L, int S, bool coarsest, bool need_state, bool ff) {
   TRY(upload(L.owned, &d.blk_src, h.blk_src));
   TRY(upload(L.owned, &d.cell_blk, h.cell_blk));
   TRY(upload(L.owned, &d.spmv_rows, h.spmv_rows));
+  for (int t = 0; t < 4; ++t) L.spt_blocks[t] = spmv_tile_max_blocks(h.rowptr.data(), h.n_nodes, kSptRows[t]);
   TRY(upload(L.owned, &L.blk_t, h.blk_t));
   for (int k = 0; k < 4; ++k) {
     TRY(upload(L.owned, &L.col_cells[k], h.col_cells[k]));
@@ -761,9 +772,90 @@ int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
   return launch_check();
 }
 
+// One launch of the row-tile product with tile index t (1..4) or, for t = 0,
+// the row-list kernel of the same value type (bit-identical results).
+template <typename V, typename Y, bool RES, int ROWS>
+void spt_launch(Level& L, int S, const V* A, const V* x, const Y* b, const uint8_t* act, Y* y, cudaStream_t st,
+                double work, double bytes, int ki, int t) {
+  const size_t smem = spmv_tile_smem<V>(L.spt_blocks[t - 1]);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_bsr_spmv_tile<V, Y, RES, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  LAUNCH_WB(work, bytes, ki, (k_bsr_spmv_tile<V, Y, RES, ROWS>), (dim3(nblk(L.h.n_nodes, ROWS), S)), ROWS * 5, smem, st,
+            L.dm, A, x, b, L.n, act, y, L.async_status);
+}
+
+template <typename V, typename Y, bool RES>
+void spt_run(Level& L, int S, const V* A, const V* x, const Y* b, const uint8_t* act, Y* y, cudaStream_t st,
+             double work, double bytes, int ki, int t) {
+  const int* rows = L.dm.spmv_rows;
+  const int nrows = L.h.n_nodes;
+  switch (t) {
+    case 0:
+      if constexpr (std::is_same<V, float2>::value)
+        LAUNCH_WB(work, bytes, ki, k_bsr_spmv_ff<RES>, (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b,
+                  L.n, act, y, rows, nrows);
+      else
+        LAUNCH_WB(work, bytes, ki, (k_bsr_spmv<V, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x,
+                  b, L.n, act, y, rows, nrows);
+      break;
+    case 1: spt_launch<V, Y, RES, 8>(L, S, A, x, b, act, y, st, work, bytes, ki, t); break;
+    case 2: spt_launch<V, Y, RES, 16>(L, S, A, x, b, act, y, st, work, bytes, ki, t); break;
+    case 3: spt_launch<V, Y, RES, 32>(L, S, A, x, b, act, y, st, work, bytes, ki, t); break;
+    default: spt_launch<V, Y, RES, 64>(L, S, A, x, b, act, y, st, work, bytes, ki, t); break;
+  }
+}
+
+// The product over all rows, in the variant tuned for this level, value type and
+// batch-size class. The first call of a class that is not inside a stream capture
+// (and whose output overlaps neither input) times every variant whose tile fits
+// in shared memory, three launches each, and keeps the fastest; all variants give
+// the same bits, so the choice never changes a result.
+template <typename V, typename Y, bool RES>
+int spt_product(Level& L, int S, const V* A, const V* x, const Y* b, const uint8_t* act, Y* y, cudaStream_t st,
+                double work, double bytes, int ki) {
+  const int type = std::is_same<V, double>::value ? 0 : std::is_same<V, float>::value ? 1 : 2;
+  const int cls = S <= 1 ? 0 : S <= 4 ? 1 : S <= 16 ? 2 : 3;
+  signed char& choice = L.spt_choice[type][cls];
+  auto fits = [&](int t) { return t == 0 || spmv_tile_smem<V>(L.spt_blocks[t - 1]) <= kSptMaxSmem; };
+  if (choice < 0) {
+    const bool aliased = (const void*)y == (const void*)x || (RES && (const void*)y == (const void*)b);
+    if (g_cap.on || aliased) {   // no timing here: the row-list kernel, untuned
+      spt_run<V, Y, RES>(L, S, A, x, b, act, y, st, work, bytes, ki, 0);
+      return launch_check();
+    }
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    float best = 0.0f;
+    int best_t = 0;
+    for (int t = 0; t <= 4; ++t) {
+      if (!fits(t)) continue;
+      spt_run<V, Y, RES>(L, S, A, x, b, act, y, st, work, bytes, ki, t);   // warm-up
+      cudaEventRecord(ev[0], st);
+      for (int r = 0; r < 2; ++r) spt_run<V, Y, RES>(L, S, A, x, b, act, y, st, work, bytes, ki, t);
+      cudaEventRecord(ev[1], st);
+      TRY(launch_check());
+      CK(cudaEventSynchronize(ev[1]));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      if (t == 0 || ms < best) best = ms, best_t = t;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    choice = (signed char)best_t;
+    if (std::getenv("FSI_TRACE_TUNE"))
+      std::fprintf(stderr, "[fsi tune] level n=%zu type %d class %d: variant %d (%.3f ms per launch)\n", L.n, type,
+                   cls, best_t, best / 2.0f);
+    return FSI_OK;   // y holds the product of the last timed launch
+  }
+  spt_run<V, Y, RES>(L, S, A, x, b, act, y, st, work, bytes, ki, choice);
+  return launch_check();
+}
+
 template <typename T, bool RES>
 int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act, T* y, cudaStream_t st,
          const int* rows = nullptr, int nrows = -1) {
+  const bool all_rows = !rows;
   if (!rows) {
     rows = L.dm.spmv_rows;
     nrows = L.h.n_nodes;
@@ -772,17 +864,18 @@ int spmv(Level& L, int S, const T* A, const T* x, const T* b, const uint8_t* act
   // per active slice: the blocks, x, y (and b); once per launch: the row list, row pointers and column indices
   const double bytes = (double)g_nact * sizeof(T) * (25.0 * blocks + (double)L.n + (RES ? 10.0 : 5.0) * nrows) +
                        4.0 * (blocks + 2.0 * nrows + 1.0);
+  const double work = 50.0 * blocks * (double)g_nact;
   if (sizeof(T) == sizeof(double) && L.Aff && L.aff_of == (const void*)A) {
     // the FP64 operator as float pairs: x to float pairs, then the compensated FP32 product
     LAUNCH_WB(3.0 * (double)L.n * g_nact, 16.0 * (double)L.n * g_nact, KI_TO_FF, k_to_ff, (dim3(nblk(L.n, 256), S)), 256, 0, st, L.n, reinterpret_cast<const double*>(x), L.n, act, L.xff, L.n);
-    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV_FF, (k_bsr_spmv_w<float2, double, RES>), (dim3(nblk(nrows, SPW_THREADS / 32), S)), SPW_THREADS, 0, st, L.dm, L.Aff, L.xff, reinterpret_cast<const double*>(b), L.n, act, reinterpret_cast<double*>(y), rows, nrows);
+    if (all_rows)
+      return spt_product<float2, double, RES>(L, S, L.Aff, L.xff, reinterpret_cast<const double*>(b), act,
+                                              reinterpret_cast<double*>(y), st, work, bytes, KI_BSR_SPMV_FF);
+    LAUNCH_WB(work, bytes, KI_BSR_SPMV_FF, k_bsr_spmv_ff<RES>, (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, L.Aff, L.xff, reinterpret_cast<const double*>(b), L.n, act, reinterpret_cast<double*>(y), rows, nrows);
     return launch_check();
   }
-  if (sizeof(T) == sizeof(float)) {   // FP32: one warp per row, the blocks read in order
-    LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv_w<float, float, RES>), (dim3(nblk(nrows, SPW_THREADS / 32), S)), SPW_THREADS, 0, st, L.dm, reinterpret_cast<const float*>(A), reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(b), L.n, act, reinterpret_cast<float*>(y), rows, nrows);
-    return launch_check();
-  }
-  LAUNCH_WB(50.0 * blocks * (double)g_nact, bytes, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
+  if (all_rows) return spt_product<T, T, RES>(L, S, A, x, b, act, y, st, work, bytes, KI_BSR_SPMV);
+  LAUNCH_WB(work, bytes, KI_BSR_SPMV, (k_bsr_spmv<T, RES>), (dim3(nblk((size_t)nrows * 5, 128), S)), 128, 0, st, L.dm, A, x, b, L.n, act, y, rows, nrows);
   return launch_check();
 }
 
@@ -1978,6 +2071,7 @@ int fsi_setup(const fsi_mesh* mesh, const fsi_params* p, fsi_ctx** out) {
       (rc = A(&c->p_in, S * n)) || (rc = A(&c->p_out, S * n)) || (rc = A(&c->tc_status, 1)))
     return cleanup(rc);
   if (cudaMemset(c->tc_status, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
+  for (auto& L : c->lev) L.async_status = c->tc_status;
   // the tables were copied with synchronous copies on the legacy stream; wait
   // for their DMA without waiting on other contexts' non-blocking streams
   if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) return cleanup(fail(FSI_ECUDA, "set-up failed"));
@@ -2080,6 +2174,50 @@ int fsi_bsr_spmv_ff(fsi_ctx* c, int S, const double* vals, const double* x, doub
   const int rc = spmv<double, false>(L, S, vals, x, nullptr, c->active, y, st);
   L.aff_of = nullptr;   // the pairs are not the context's operator
   return rc;
+}
+
+int fsi_bsr_spmv_variant(fsi_ctx* c, int S, int value_type, int tile_rows, const void* vals, const void* x, void* y,
+                         void* stream) {
+  if (!c || !vals || !x || !y) return fail(FSI_EINVAL, "null argument");
+  if (S < 1 || S > c->S) return fail(FSI_EINVAL, "batch size outside 1..max_batch");
+  if (value_type < 0 || value_type > 2) return fail(FSI_EINVAL, "value_type must be 0, 1 or 2");
+  Level& L = c->lev[0];
+  int t = -1;
+  if (tile_rows == 0) t = 0;
+  for (int i = 0; i < 4; ++i)
+    if (tile_rows == kSptRows[i]) t = i + 1;
+  if (t < 0) return fail(FSI_EINVAL, "tile_rows must be 0, 8, 16, 32 or 64");
+  const size_t vsz = value_type == 1 ? 4 : 8;
+  if (t > 0 && (size_t)L.spt_blocks[t - 1] * 25 * vsz + 16 > kSptMaxSmem)
+    return fail(FSI_EINVAL, "the tile's blocks do not fit in shared memory");
+  if (value_type == 2 && !L.Aff) return fail(FSI_EINVAL, "the context was set up without ff_operator");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<uint8_t> act(S, 1);
+  CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+  c->n_act = g_nact = count_active(act);
+  const double blocks = (double)L.h.nnzb;
+  const double work = 50.0 * blocks * S;
+  const double bytes = (double)S * vsz * (25.0 * blocks + 2.0 * (double)L.n) + 4.0 * (blocks + 2.0 * L.h.n_nodes + 1.0);
+  if (value_type == 0) {
+    spt_run<double, double, false>(L, S, (const double*)vals, (const double*)x, nullptr, c->active, (double*)y, st,
+                                   work, bytes, KI_BSR_SPMV, t);
+  } else if (value_type == 1) {
+    spt_run<float, float, false>(L, S, (const float*)vals, (const float*)x, nullptr, c->active, (float*)y, st, work,
+                                 bytes, KI_BSR_SPMV, t);
+  } else {
+    const size_t cnt = (size_t)L.h.nnzb * 25;
+    LAUNCH_WB(3.0 * cnt * S, 16.0 * cnt * S, KI_TO_FF, k_to_ff, (dim3(nblk(cnt, 256), S)), 256, 0, st, cnt, (const double*)vals, cnt, c->active, L.Aff, cnt);
+    LAUNCH_WB(3.0 * L.n * S, 16.0 * L.n * S, KI_TO_FF, k_to_ff, (dim3(nblk(L.n, 256), S)), 256, 0, st, L.n, (const double*)x, L.n, c->active, L.xff, L.n);
+    L.aff_of = nullptr;   // the pairs are not the context's operator
+    spt_run<float2, double, false>(L, S, L.Aff, L.xff, nullptr, c->active, (double*)y, st, work, bytes,
+                                   KI_BSR_SPMV_FF, t);
+  }
+  TRY(launch_check());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, L.async_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) return fail(FSI_ECUDA, "a bulk copy or MMA completion was not seen within the poll limit");
+  return FSI_OK;
 }
 
 // Resets the statistics of a call, keeping the caller's per-slice array

@@ -74,16 +74,6 @@ FSI_FF_HD inline void fma_ff(ffacc& acc, ff a, ff x) {
   acc.cc += ec;
 }
 
-// acc += o for two running sums of the same kind (partial sums of one dot product): the leading
-// parts by TwoSum, their rounding error and the compensations into the compensation pair.
-FSI_FF_HD inline void merge(ffacc& acc, const ffacc& o) {
-  float s, es, c, ec;
-  two_sum(acc.s, o.s, s, es);
-  acc.s = s;
-  two_sum(acc.c, o.c + es, c, ec);
-  acc.c = c;
-  acc.cc += o.cc + ec;
-}
 FSI_FF_HD inline double result(const ffacc& acc) { return (double)acc.s + ((double)acc.c + (double)acc.cc); }
 
 }  // namespace fsiff

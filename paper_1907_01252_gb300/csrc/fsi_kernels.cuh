@@ -1713,67 +1713,105 @@ __global__ void k_bsr_spmv_ff(DevMesh m, const float2* __restrict__ A, const flo
 }
 
 // --------------------------------------------------------------------------
-// Warp-per-row block product for 4- and 8-byte values (the FP32 operator, and the
-// FP64 operator as float pairs). A warp takes one node row; lane 5c + e (25 of the
-// 32 lanes) multiplies entry (c, e) of every 5 x 5 block of the row with x_j[e].
-// Consecutive lanes so read each block as 25 consecutive values, the whole row
-// streams through in order, and the five partial sums of a row component are
-// combined by warp shuffles (e0 += e2, e1 += e3, e0 += e1, e0 += e4).
+// Row-tile block product: a CTA takes ROWS consecutive node rows. Their blocks
+// are one contiguous range of the slice's values, which the CTA brings into
+// shared memory at once: the 16-byte aligned middle of the range by one bulk
+// asynchronous copy (cp.async.bulk, completion counted on an mbarrier), the
+// unaligned head and tail by plain loads. Thread (r, c) then sums component c
+// of row r over the row's blocks in ascending order, five terms per block:
+// the order of k_bsr_spmv and k_bsr_spmv_ff, so the tile size changes the work
+// distribution, never a bit of the result. V is the stored value type (double,
+// float, or float2 = an FP64 value as a float pair), Y the type of b and y.
+// A bulk copy that does not complete within the poll limit (twice) sets
+// *status and leaves NaN in the tile's outputs.
 // --------------------------------------------------------------------------
-constexpr int SPW_THREADS = 256;   // 8 rows per CTA
-
-template <typename V> struct SpwAcc;
-template <> struct SpwAcc<float> {
+template <typename V> struct SptAcc;
+template <> struct SptAcc<double> {
+  double a = 0.0;
+  __device__ void add(double v, double x) { a = fma(v, x, a); }
+  __device__ double value() const { return a; }
+};
+template <> struct SptAcc<float> {
   float a = 0.f;
   __device__ void add(float v, float x) { a = fmaf(v, x, a); }
-  __device__ void take(int delta, bool use) {
-    const float o = __shfl_down_sync(0xffffffffu, a, delta);
-    if (use) a += o;
-  }
   __device__ float value() const { return a; }
 };
-template <> struct SpwAcc<float2> {
+template <> struct SptAcc<float2> {
   fsiff::ffacc a;
   __device__ void add(float2 v, float2 x) { fsiff::fma_ff(a, fsiff::ff{v.x, v.y}, fsiff::ff{x.x, x.y}); }
-  __device__ void take(int delta, bool use) {
-    fsiff::ffacc o;
-    o.s = __shfl_down_sync(0xffffffffu, a.s, delta);
-    o.c = __shfl_down_sync(0xffffffffu, a.c, delta);
-    o.cc = __shfl_down_sync(0xffffffffu, a.cc, delta);
-    if (use) fsiff::merge(a, o);
-  }
   __device__ double value() const { return fsiff::result(a); }
 };
 
-// y = A x (or b - A x) for the rows listed; V the stored value type, Y the vector type of b and y.
-template <typename V, typename Y, bool RESIDUAL>
-__global__ void __launch_bounds__(SPW_THREADS) k_bsr_spmv_w(DevMesh m, const V* __restrict__ A,
+// Blocks of the largest tile of ROWS consecutive rows (host side: shared-memory size).
+inline int spmv_tile_max_blocks(const int* rowptr, int n_nodes, int rows) {
+  int mx = 0;
+  for (int r0 = 0; r0 < n_nodes; r0 += rows) {
+    const int r1 = r0 + rows < n_nodes ? r0 + rows : n_nodes;
+    mx = rowptr[r1] - rowptr[r0] > mx ? rowptr[r1] - rowptr[r0] : mx;
+  }
+  return mx;
+}
+// Dynamic shared memory of a tile of `blocks` blocks: the values plus 16 bytes of
+// alignment slack (the staged range keeps the address modulo 16 of the source).
+template <typename V> constexpr size_t spmv_tile_smem(int blocks) { return (size_t)blocks * 25 * sizeof(V) + 16; }
+
+template <typename V, typename Y, bool RESIDUAL, int ROWS>
+__global__ void __launch_bounds__(ROWS * 5) k_bsr_spmv_tile(DevMesh m, const V* __restrict__ A,
                                                             const V* __restrict__ x, const Y* __restrict__ bvec,
                                                             size_t stride, const uint8_t* __restrict__ active,
-                                                            Y* __restrict__ y, const int* __restrict__ rows,
-                                                            int nrows) {
+                                                            Y* __restrict__ y, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char spt_raw[];
+  __shared__ __align__(8) uint64_t bar;
   const int s = blockIdx.y;
-  const int w = blockIdx.x * (SPW_THREADS / 32) + (threadIdx.x >> 5);
-  if (!active[s] || w >= nrows) return;   // uniform over the warp
-  const int lane = threadIdx.x & 31;
-  const bool on = lane < 25;
-  const int c = lane / 5, e = lane % 5;
-  const int i = rows[w];
-  const V* As = A + (size_t)s * m.nnzb * 25 + (on ? lane : 0);
-  const V* xs = x + s * stride + e;
-  SpwAcc<V> acc;
-  const int b0 = m.rowptr[i], b1 = m.rowptr[i + 1];
-#pragma unroll 4
-  for (int b = b0; b < b1; ++b) {
-    const int col = m.colidx[b];
-    if (on) acc.add(As[(size_t)b * 25], xs[(size_t)col * 5]);
+  if (!active[s]) return;   // uniform over the CTA
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * ROWS;
+  const int r1 = min(r0 + ROWS, m.n_nodes);
+  const int B0 = m.rowptr[r0], B1 = m.rowptr[r1];
+  const V* src = A + ((size_t)s * m.nnzb + B0) * 25;
+  const int n_el = (B1 - B0) * 25;
+  // sm[k] holds src[k]; sm starts at the same address modulo 16 as src
+  const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 15u);
+  V* sm = reinterpret_cast<V*>(spt_raw + mis);
+  const int k_a = min(n_el, (int)(((16u - mis) & 15u) / sizeof(V)));   // first 16-byte aligned element
+  const int k_b = k_a + (int)((((size_t)(n_el - k_a) * sizeof(V)) / 16) * 16 / sizeof(V));
+  const uint32_t bytes = (uint32_t)((size_t)(k_b - k_a) * sizeof(V));
+  if (tid == 0 && bytes) tc::mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0 && bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(&bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_u32(sm + k_a)),
+        "l"(src + k_a), "r"(bytes), "r"(tc::smem_u32(&bar))
+        : "memory");
   }
-  acc.take(2, e < 2);
-  acc.take(1, e == 0);
-  acc.take(4, e == 0);
-  if (on && e == 0) {
-    const size_t o = s * stride + (size_t)i * 5 + c;
-    const Y r = (Y)acc.value();
-    y[o] = RESIDUAL ? bvec[o] - r : r;
+  for (int k = tid; k < k_a; k += ROWS * 5) sm[k] = src[k];
+  for (int k = k_b + tid; k < n_el; k += ROWS * 5) sm[k] = src[k];
+  bool ok = true;
+  if (bytes) {
+    ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);
+    if (!ok) ok = tc::mbar_wait(&bar, 0, tc::kMaxPolls);   // the copy in flight gets a second chance
   }
+  ok = __syncthreads_and(ok);
+  if (!ok && tid == 0) atomicExch(status, 1);
+  const int r = r0 + tid / 5, c = tid % 5;
+  if (r >= r1) return;
+  const size_t o = s * stride + (size_t)r * 5 + c;
+  if (!ok) {
+    y[o] = (Y)__longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const V* xs = x + s * stride;
+  SptAcc<V> acc;
+  const int b1 = m.rowptr[r + 1];
+  for (int b = m.rowptr[r]; b < b1; ++b) {
+    const V* blk = sm + (b - B0) * 25 + c * 5;
+    const V* xj = xs + (size_t)m.colidx[b] * 5;
+#pragma unroll
+    for (int e = 0; e < 5; ++e) acc.add(blk[e], xj[e]);
+  }
+  const Y v = (Y)acc.value();
+  y[o] = RESIDUAL ? bvec[o] - v : v;
 }

@@ -98,6 +98,7 @@ SIGNATURES = {
     "fsi_bsr_spmv": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "fsi_bsr_spmv_f32": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "fsi_bsr_spmv_ff": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "fsi_bsr_spmv_variant": (_I, [_VP, _I, _I, _I, _VP, _VP, _VP, _VP]),
     "fsi_theta_step": (_I, [_VP, _I, _VP, C.POINTER(_D), _D, _D, _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_fine": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
     "fsi_coarse": (_I, [_VP, _I, _VP, C.POINTER(_D), _VP, C.POINTER(fsi_stats), _VP]),
@@ -400,6 +401,15 @@ class Context:
         import torch
         y = torch.empty_like(x) if y is None else y
         _check(self.lib.fsi_bsr_spmv_ff(self.handle, x.shape[0], _ptr(vals), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def fsi_bsr_spmv_variant(self, value_type, tile_rows, vals, x, y=None):
+        """y = A x in one kernel variant (value_type 0 FP64, 1 FP32, 2 float pairs;
+        tile_rows 0 for the row-list kernel, else 8, 16, 32 or 64)."""
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(self.lib.fsi_bsr_spmv_variant(self.handle, x.shape[0], value_type, tile_rows, _ptr(vals), _ptr(x),
+                                             _ptr(y), _stream()))
         return y
 
     def _propagator_call(self, fn, S, *args):

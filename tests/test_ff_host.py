@@ -24,7 +24,7 @@ def lib(tmp_path_factory):
                    check=True)
     lib = C.CDLL(out)
     P = C.POINTER(C.c_double)
-    for f in (lib.ff_dot_host, lib.ff_dot5_host, lib.f64_dot_host):
+    for f in (lib.ff_dot_host, lib.f64_dot_host):
         f.argtypes, f.restype = [P, P, C.c_int], C.c_double
     return lib
 
@@ -48,8 +48,7 @@ def test_float_float_dot_is_fp64_class(lib, n):
         x = rng.choice([-1, 1], n) * 10.0 ** rng.uniform(-6, 2, n)
         ref = exact(a, x)
         mag = float(np.sum(np.abs(a * x)))
-        worst_ff = max(worst_ff, abs(lib.ff_dot_host(ptr(a), ptr(x), n) - ref) / mag,
-                       abs(lib.ff_dot5_host(ptr(a), ptr(x), n) - ref) / mag)
+        worst_ff = max(worst_ff, abs(lib.ff_dot_host(ptr(a), ptr(x), n) - ref) / mag)
         worst_64 = max(worst_64, abs(lib.f64_dot_host(ptr(a), ptr(x), n) - ref) / mag)
     assert worst_ff <= 2.0 ** -45, (worst_ff, worst_64)
 
@@ -63,7 +62,5 @@ def test_float_float_split_and_cancellation(lib):
     got = lib.ff_dot_host(ptr(a), ptr(x), len(a))
     mag = float(np.sum(np.abs(a * x)))
     assert abs(got - ref) <= 2.0 ** -45 * mag, (got, ref)
-    got5 = lib.ff_dot5_host(ptr(a), ptr(x), len(a))
-    assert abs(got5 - ref) <= 2.0 ** -45 * mag, (got5, ref)
     one = np.array([np.pi]), np.array([1.0])
     assert abs(lib.ff_dot_host(ptr(one[0]), ptr(one[1]), 1) - np.pi) <= 2.0 ** -47 * np.pi

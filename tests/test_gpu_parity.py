@@ -107,11 +107,10 @@ def test_spmv_matches_oracle_matrix():
 
 
 def test_spmv_f32_and_float_pair_products():
-    """The warp-per-row products against the FP64 product of the same values: FP32 values
-    and vectors within the FP32 summation bound (28 terms deep per row component: 25 blocks
-    at most per lane, then three merges), float pairs within 2^-44 of sum |a x| per row.
-    36 x 10 cells: 1,533 rows (a ragged last CTA of 5 rows), 3 slices; one slice alone
-    gives the same bits."""
+    """The FP32 and float-pair products against the FP64 product of the same values: FP32
+    values and vectors within the bound of a sequential FP32 sum (125 terms at most per row
+    component: 25 blocks of 5), float pairs within 2^-44 of sum |a x| per row. 36 x 10
+    cells: 1,533 rows, 3 slices; one slice alone gives the same bits."""
     import scipy.sparse as sp
     w = wl.Workload("spmv_w", nx=36, ny=10, T=1.0, n_slices=4, m_fine=4)
     mesh = oracle_mesh(w)
@@ -134,10 +133,48 @@ def test_spmv_f32_and_float_pair_products():
         assert np.all(np.abs(y_ff[s] - ref) <= 2.0 ** -44 * mag)
         A32 = sp.bsr_matrix((v32h[s], colidx, rowptr), shape=(n, n))
         ref32, mag32 = A32 @ x32h[s], abs(A32) @ abs(x32h[s])
-        assert np.all(np.abs(y_32[s].astype(np.float64) - ref32) <= 28 * 2.0 ** -24 * mag32 + 1e-38)
+        assert np.all(np.abs(y_32[s].astype(np.float64) - ref32) <= 125 * 2.0 ** -24 * mag32 + 1e-38)
     one_ff = ctx.fsi_bsr_spmv_ff(vals[1:2].contiguous(), xd[1:2].contiguous()).cpu().numpy()
     one_32 = ctx.fsi_bsr_spmv_f32(v32[1:2].contiguous(), x32[1:2].contiguous()).cpu().numpy()
     assert np.array_equal(one_ff[0], y_ff[1]) and np.array_equal(one_32[0], y_32[1])
+
+
+def test_spmv_tile_variants_give_the_same_bits():
+    """Every kernel variant of the block product (the row-list kernel and the
+    row-tile kernel with 8, 16, 32 and 64 rows per CTA, staged by a bulk copy)
+    sums each row component in the same order: identical bits for FP64, FP32
+    and float-pair values. 36 x 10 cells: 1,533 node rows, so the last tile is
+    ragged for every height; 3 slices. The FP64 product also matches the
+    oracle's matrix."""
+    import scipy.sparse as sp
+    from paper_1907_01252_gb300 import fsi
+    w = wl.Workload("spmv_t", nx=36, ny=10, T=1.0, n_slices=4, m_fine=4)
+    mesh = oracle_mesh(w)
+    S = 3
+    U = np.stack([wl.random_state(mesh.n_nodes, 710 + s) for s in range(S)])
+    x = np.stack([wl.random_state(mesh.n_nodes, 810 + s) for s in range(S)])
+    ctx = ctx_for(w, S, ff_operator=1)
+    vals = ctx.fsi_jacobian(to_dev(U), to_dev(U), 1e-2, 0.6)
+    xd = to_dev(x)
+    for vt, (v, xx) in enumerate(((vals, xd), (vals.float(), xd.float()), (vals, xd))):
+        ref = ctx.fsi_bsr_spmv_variant(vt, 0, v, xx).cpu()
+        assert torch.isfinite(ref).all()
+        for rows in (8, 16, 32, 64):
+            try:
+                got = ctx.fsi_bsr_spmv_variant(vt, rows, v, xx).cpu()
+            except fsi.FsiError as err:   # a tile of 64 rows of 8-byte blocks exceeds shared memory
+                assert vt != 1 and rows == 64 and "shared memory" in str(err), (vt, rows, err)
+                continue
+            assert torch.equal(got, ref), (vt, rows)
+        if vt == 0:
+            rowptr, colidx = ctx.fsi_bsr_pattern()
+            vh, n = vals.cpu().numpy(), mesh.n_dofs
+            for s in range(S):
+                A = sp.bsr_matrix((vh[s], colidx, rowptr), shape=(n, n))
+                assert np.abs(ref[s].numpy() - A @ x[s].ravel()).max() <= 1e-12 * (abs(A) @ abs(x[s].ravel())).max()
+    # the library's own products (tuned variant) give the same bits as well
+    assert torch.equal(ctx.fsi_bsr_spmv(vals, xd).cpu(), ctx.fsi_bsr_spmv_variant(0, 0, vals, xd).cpu())
+    assert torch.equal(ctx.fsi_bsr_spmv_ff(vals, xd).cpu(), ctx.fsi_bsr_spmv_variant(2, 0, vals, xd).cpu())
 
 
 def developed_states(w, mesh, steps, k):
@@ -241,8 +278,17 @@ def test_fine_and_coarse_propagators_match_oracle():
 # both sides solve that workload's Newton systems to 1e-11 (just above the
 # residual's round-off floor of about 1.5e-12 relative), and the GPU solves
 # every Newton correction to the FGMRES tolerance (no inexact forcing), as the
-# oracle's direct solver does: both then take the same Newton iterates, and the
-# comparison sees the arithmetic, not where two stopping tests fall.
+# oracle's direct solver does.
+#
+# The bar. Eq. (parareal:iteration) makes the iterate at boundary n+1 a sum of
+# three propagator results, F(U_n^i) + C(U_n^(i+1)) - C(U_n^i), and on the 16 x 4
+# workload (coarse step K = 1/8) the three terms' pressures add up to as much as
+# 15x the pressure of the sum (boundary 2 after iteration 2, in the oracle; about
+# 3x where the terms do not cancel). The propagators agree with the oracle's to a
+# few 1e-12 on the oracle's own inputs, and a sum carries its terms' errors, so
+# the iterate after iteration 2 is held to 1e-10 of the size of the terms it is
+# summed from, per field: |U - U_ref| <= 1e-10 (|F| + |C_new| + |C_old|). The
+# serial limit (k = N) has no such sum and keeps the plain 1e-10 of |U| per field.
 @pytest.mark.parametrize("w", [wl.Workload("pr", nx=16, ny=4, T=0.4, n_slices=4, m_fine=4),
                                dataclasses.replace(wl.SMALL_16x4, newton_tol=1e-11, gmres_rtol_first=0.0,
                                                    newton_eta=0.0)],
@@ -251,20 +297,36 @@ def test_parareal_matches_oracle_iterates_and_reaches_serial(w):
     mesh = oracle_mesh(w)
     model = of.FSIModel(mesh, w.material, newton_tol=w.newton_tol)
     dt = w.T / w.n_slices
-    fine = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine)
-    coarse = lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, 1, theta=1.0)
+    N = w.n_slices
+    calls = {"F": [], "C": []}   # every propagator result, in call order
+
+    def fine(U, n):
+        calls["F"].append(model.propagate(U, n * dt, (n + 1) * dt, w.m_fine))
+        return calls["F"][-1]
+
+    def coarse(U, n):
+        calls["C"].append(model.propagate(U, n * dt, (n + 1) * dt, 1, theta=1.0))
+        return calls["C"][-1]
+
     U0 = np.zeros((mesh.n_nodes, 5))
-    hist = opr.parareal(U0, w.n_slices, coarse, fine, 2)
-    ser = opr.serial(U0, w.n_slices, fine)
-    ctx = ctx_for(w, w.n_slices)
-    for iters, ref in ((2, hist[2]), (w.n_slices, ser)):
-        U = torch.zeros((w.n_slices + 1, mesh.n_dofs), dtype=torch.float64, device=DEV)
+    hist = opr.parareal(U0, N, coarse, fine, 2)
+    # call order: predictor sweep (N coarse), then per iteration N fine and N coarse
+    F2, C1, C2 = calls["F"][N:2 * N], calls["C"][N:2 * N], calls["C"][2 * N:3 * N]
+    ser = opr.serial(U0, N, lambda U, n: model.propagate(U, n * dt, (n + 1) * dt, w.m_fine))
+    ctx = ctx_for(w, N)
+    for iters, ref in ((2, hist[2]), (N, ser)):
+        U = torch.zeros((N + 1, mesh.n_dofs), dtype=torch.float64, device=DEV)
         U, st = ctx.parareal_iterate(U, iters, 0.0)
-        got = U.cpu().numpy().reshape(w.n_slices + 1, -1, 5)
+        got = U.cpu().numpy().reshape(N + 1, -1, 5)
         assert st["iterations"] == iters
-        for n in range(1, w.n_slices + 1):
-            errs = rel_field_errors(got[n], ref[n])
-            assert max(errs.values()) <= 1e-10, (iters, n, errs)
+        for n in range(1, N + 1):
+            for name, sl in FIELDS.items():
+                err = np.linalg.norm(got[n][..., sl] - ref[n][..., sl])
+                if iters == 2:
+                    bar = 1e-10 * sum(np.linalg.norm(t[n - 1][..., sl]) for t in (F2, C1, C2))
+                else:
+                    bar = 1e-10 * np.linalg.norm(ref[n][..., sl])
+                assert err <= bar, (iters, n, name, err, bar)
 
 
 @pytest.mark.parametrize("chunk", [1, 3])
