@@ -42,6 +42,10 @@ Parareal iteration each, run concurrently by the library's worker threads with
 the worker count chosen by the library's autotuner (its timed candidate runs
 are the warm-up). value = fine time-steps of all problems per second.
 
+--unit fine_step3d times one batched fine theta step of all 32 slices of that 3D
+workload from their predictor states (profiling aid; kernel shares of the last
+warm-up step in the line).
+
 --unit parareal3d measures the 3D path (hexahedral Q2, 7 unknowns per node) on the
 32 x 8 x 8 channel with the plate (131,495 dofs, T = 1, 32 slices x 16 fine steps): one
 fsi3_parareal iteration per step, FP32 multigrid inside FP64 FGMRES and Newton.
@@ -79,7 +83,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--unit", default="parareal", choices=["parareal", "fine_step", "coarse_step", "spmv", "batch",
-                                                           "parareal3d"])
+                                                           "parareal3d", "fine_step3d"])
     ap.add_argument("--instances", type=int, default=4,
                     help="--unit batch: the first K problems of the seeded 48-problem uneven batch")
     ap.add_argument("--slices", type=int, default=64, help="batch for --unit fine_step")
@@ -311,6 +315,58 @@ def bench_3d(args, torch, fsi, wl, dev):
                        "kernels_last_warmup": shares},
             "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": launches}
     print(json.dumps(line))
+
+
+def bench_3d_step(args, torch, fsi, wl, dev):
+    """Profiling aid for the 3D path: the predictor sweep of the 32 x 8 x 8 workload
+    (32 implicit-Euler steps, untimed), then one batched fine theta step (shifted
+    Crank-Nicolson, k = 1/512) of all 32 slices from their predictor states per step.
+    value = fine time-steps (slices x steps) per second."""
+    w = wl.CHANNEL3D_32x8x8
+    N = w.n_slices
+    K = w.T / N
+    k = K / w.m_fine
+    c1 = fsi.Context3D(w, max_batch=1, **overrides(args))
+    U = torch.zeros((N + 1, c1.n_dofs), dtype=torch.float64, device=dev)
+    for i in range(N):
+        c1.fsi3_coarse(U[i:i + 1], [i * K], U[i + 1:i + 2])
+    c1.close()
+    ctx = fsi.Context3D(w, max_batch=N, **overrides(args))
+    stream = torch.cuda.current_stream(dev)
+    t0 = [i * K for i in range(N)]
+    theta = 0.5 + w.material.theta0 * k
+    U0 = U[:N].contiguous()
+    U1 = torch.empty_like(U0)
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fsi.profile3(True)
+        ctx.fsi3_theta_step(U0, t0, k, theta, U1)
+    torch.cuda.synchronize()
+    kernel_ms = {kk: v for kk, v in fsi.profile3_read().items() if v[1]}
+    fsi.profile3(False)
+    total = sum(v[0] for v in kernel_ms.values()) or 1.0
+    shares = {kk: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
+              for kk, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1][0])}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = fsi.launch_count3()
+    stats = []
+    _, sec = timed(stream, torch, lambda: [stats.append(ctx.fsi3_theta_step(U0, t0, k, theta, U1)[1])
+                                           for _ in range(args.steps)])
+    clk = clocks.stop()
+    print(json.dumps({"metric": METRIC, "value": N * args.steps / sec, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sec / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f64 (FP32 multigrid)", "data": "synthetic",
+                      "config": {"workload": w.name, "unit": "fine_step3d", "slices": N, "n_dofs": ctx.n_dofs,
+                                 "nnzb": ctx.nnzb, "levels": ctx.n_levels, "k": k,
+                                 "step": "one batched fine theta step of all slices from their predictor states",
+                                 "newton_iters": [st["newton_iters"] for st in stats],
+                                 "gmres_iters": [st["gmres_iters"] for st in stats],
+                                 "kernels_last_warmup": shares},
+                      "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+                      "gpu_launches": fsi.launch_count3() - l0}))
+    ctx.close()
 
 
 FIELDS = (("v", slice(0, 2)), ("u", slice(2, 4)), ("p", slice(4, 5)))
@@ -816,6 +872,8 @@ def main():
         bench_batch(args, torch, fsi, wl, dev)
     elif args.unit == "parareal3d":
         bench_3d(args, torch, fsi, wl, dev)
+    elif args.unit == "fine_step3d":
+        bench_3d_step(args, torch, fsi, wl, dev)
     elif args.unit == "spmv":
         bench_spmv(args, torch, fsi, wl, dev)
     elif args.unit in ("fine_step", "coarse_step"):

@@ -772,14 +772,33 @@ int jacobian(fsi_ctx* c, Level& L, int S, const double* U, const double* Uold, d
   return launch_check();
 }
 
+// The dynamic shared-memory limit of a kernel is one setting per kernel and device,
+// shared by every context and host thread: it is only ever raised (to the largest
+// size launched so far), never set to a launch's own size, which a launch or a
+// captured graph of another thread could exceed. (Setting it is not a stream
+// operation, so it may also happen while a stream is being captured.)
+void raise_smem_limit(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{fn, dev}];
+  if (smem <= cur) return;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) cur = smem;
+  else (void)cudaGetLastError();   // the launch then reports the error
+}
+
 // One launch of the row-tile product with tile index t (1..4) or, for t = 0,
 // the row-list kernel of the same value type (bit-identical results).
 template <typename V, typename Y, bool RES, int ROWS>
 void spt_launch(Level& L, int S, const V* A, const V* x, const Y* b, const uint8_t* act, Y* y, cudaStream_t st,
                 double work, double bytes, int ki, int t) {
   const size_t smem = spmv_tile_smem<V>(L.spt_blocks[t - 1]);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_bsr_spmv_tile<V, Y, RES, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {   // both forms (y = A x and y = b - A x) share the tuned choice
+    raise_smem_limit(reinterpret_cast<const void*>(k_bsr_spmv_tile<V, Y, false, ROWS>), smem);
+    raise_smem_limit(reinterpret_cast<const void*>(k_bsr_spmv_tile<V, Y, true, ROWS>), smem);
+  }
   LAUNCH_WB(work, bytes, ki, (k_bsr_spmv_tile<V, Y, RES, ROWS>), (dim3(nblk(L.h.n_nodes, ROWS), S)), ROWS * 5, smem, st,
             L.dm, A, x, b, L.n, act, y, L.async_status);
 }
@@ -1031,6 +1050,40 @@ int vcycle(fsi_ctx* c, int l, int S, const T* b, T* x, const uint8_t* act, cudaS
 // slice to ||b - A x|| <= rtol ||b||, vectors and operator in T (the
 // Hessenberg matrix and the rotations are kept in FP64). x is overwritten.
 // abs_target (optional, host [S]): stop a slice once ||b - A x|| <= max(abs_target[s], rtol ||b||).
+// Tunes, ahead of a graph capture, the block products that an Arnoldi step of
+// FGMRES will launch (the Krylov operator in T, each multigrid level's operator in
+// TP) for this batch-size class: inside the capture no variant can be timed. Runs
+// on scratch vectors (the preconditioner's input and output, each level's x and
+// r), so it needs the level operators assembled and nothing else.
+template <typename T, typename TP>
+int spt_pretune(fsi_ctx* c, int S, cudaStream_t st) {
+  const int cls = S <= 1 ? 0 : S <= 4 ? 1 : S <= 16 ? 2 : 3;
+  auto type_of = [](size_t bytes) { return bytes == sizeof(float) ? 1 : 0; };
+  for (size_t l = 0; l < c->lev.size(); ++l) {
+    Level& L = c->lev[l];
+    if (L.coarsest) break;
+    const double work = 50.0 * L.h.nnzb * (double)c->n_act;
+    if (sizeof(T) == sizeof(double) && L.Aff && L.aff_of == (const void*)L.A && L.spt_choice[2][cls] < 0) {
+      const double bytes = (double)c->n_act * 8.0 * (25.0 * L.h.nnzb + 2.0 * L.n);   // float-pair products
+      TRY((spt_product<float2, double, false>(L, S, L.Aff, L.xff, nullptr, c->active, reinterpret_cast<double*>(L.r),
+                                              st, work, bytes, KI_BSR_SPMV_FF)));
+    }
+    if (l == 0 && L.spt_choice[type_of(sizeof(T))][cls] < 0) {
+      const double bytes = (double)c->n_act * sizeof(T) * (25.0 * L.h.nnzb + 2.0 * L.n);
+      TRY((spt_product<T, T, false>(L, S, reinterpret_cast<const T*>(L.A), reinterpret_cast<const T*>(c->dU), nullptr,
+                                    c->active, reinterpret_cast<T*>(c->R), st, work, bytes, KI_BSR_SPMV)));
+    }
+    if (L.spt_choice[type_of(sizeof(TP))][cls] < 0) {
+      const TP* A = (l == 0 && mixed<TP>(c)) ? reinterpret_cast<const TP*>(L.A32) : reinterpret_cast<const TP*>(L.A);
+      const TP* xin = l == 0 ? reinterpret_cast<const TP*>(c->dU) : reinterpret_cast<const TP*>(L.x);
+      const double bytes = (double)c->n_act * sizeof(TP) * (25.0 * L.h.nnzb + 2.0 * L.n);
+      TRY((spt_product<TP, TP, false>(L, S, A, xin, nullptr, c->active, reinterpret_cast<TP*>(L.r), st, work, bytes,
+                                      KI_BSR_SPMV)));
+    }
+  }
+  return FSI_OK;
+}
+
 template <typename T, typename TP = T>
 int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rtol, fsi_stats* stats,
            cudaStream_t st, const double* abs_target = nullptr) {
@@ -1064,6 +1117,11 @@ int fgmres(fsi_ctx* c, int S, const T* b, T* x, const uint8_t* act_in, double rt
     }
   auto any = [&]() { return std::any_of(act.begin(), act.end(), [](uint8_t a) { return a != 0; }); };
   bool first_cycle = true;
+  if (S <= c->prm.graph_max_batch && any()) {
+    CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
+    c->n_act = g_nact = count_active(act);
+    TRY((spt_pretune<T, TP>(c, S, st)));
+  }
   while (any()) {
     CK(cudaMemcpyAsync(c->active, act.data(), S, cudaMemcpyHostToDevice, st));
     c->n_act = g_nact = count_active(act);
