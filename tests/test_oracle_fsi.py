@@ -361,3 +361,21 @@ def test_shifted_crank_nicolson_is_second_order():
     assert np.all(r > 1.9) and np.all(r < 2.15), r
     r = rates(channel_mesh(8, 2, solid=True), (16, 32, 64), 512, slice(2, 4))
     assert np.all(r > 1.9) and np.all(r < 2.2), r
+
+
+def test_implicit_euler_coarse_step_is_first_order_towards_the_fine_solution():
+    """The coarse propagator is the same step equation at theta = 1 (Sec. 3: implicit
+    Euler, with the n-1/2 means of the ALE mass term kept). It must converge to the
+    solution of the fine scheme at first order: theta = 1 steps of decreasing size
+    against a shifted Crank-Nicolson run with many steps (second order, so its own
+    error is negligible). A wrong weight between the old and new terms at theta = 1
+    would change the limit or the order."""
+    T = 0.08
+    for mesh, comp, ms in ((channel_mesh(8, 2, solid=False), slice(0, 2), (8, 16, 32)),
+                           (channel_mesh(8, 2, solid=True), slice(2, 4), (16, 32, 64))):
+        model = of.FSIModel(mesh, MAT, newton_tol=1e-13)
+        U0 = np.zeros((mesh.n_nodes, 5))
+        ref = model.propagate(U0, 0.0, T, 512)
+        errs = [np.linalg.norm((model.propagate(U0, 0.0, T, m, theta=1.0) - ref)[:, comp]) for m in ms]
+        r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert np.all(r > 0.85) and np.all(r < 1.2), (r, errs)
